@@ -1,0 +1,205 @@
+/*
+ * megaparticles.h -- C ABI of the GB300 (sm_103a) implementation of the
+ * MegaParticles hot path: Koide, Oishi, Yokozuka, Banno, "MegaParticles:
+ * Range-based 6-DoF Monte Carlo Localization with GPU-Accelerated Stein
+ * Particle Filter", ICRA 2024 (arXiv 2404.16370).
+ *
+ * One filter step (mp_step) runs, on the context's CUDA stream and entirely in
+ * this library's kernels:
+ *   prediction                 Sec. III-B, Eq. 1
+ *   scan Gaussians             Sec. III-C, GICP point model
+ *   neighbour list update      Sec. III-C, Eq. 9-10, Algorithm 1
+ *   likelihood + Gauss-Newton  Sec. III-C, Eq. 2-4 (NNF lookup)
+ *   particle state update      Sec. III-C, Eq. 4-8 (GN step, SVGD)
+ *   posterior propagation      Sec. III-D, Eq. 11 (+ representative state)
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers may be host or device memory; the library asks the CUDA runtime
+ *    (cudaPointerGetAttributes) and copies accordingly. Device pointers must
+ *    belong to the device that was current at mp_init_map.
+ *  - Ownership: the context owns all device state. Inputs are copied before the
+ *    call returns (or enqueued on the context stream, for device pointers: the
+ *    caller keeps them alive until the stream reaches that point). Outputs go
+ *    to caller-allocated buffers.
+ *  - Synchronisation: mp_init_map, mp_init_particles and the getters
+ *    synchronise the context stream; mp_step and mp_run_stages only enqueue.
+ *  - Errors: every call returns MP_OK (0) or a negative code; a message is kept
+ *    in the context (mp_last_error). No exception crosses the ABI. After
+ *    MP_ECUDA the context should be destroyed.
+ *  - Poses are float32[7] = (qx, qy, qz, qw, tx, ty, tz), sensor-to-map, unit
+ *    quaternion (Hamilton). Twists are (omega, v), rotation first (the order
+ *    of W^K in Eq. 7).
+ *  - Sizes: n_particles <= 2^26; the NNF grid holds < 2^31 voxels; scans hold
+ *    at most params.max_scan points.
+ */
+#ifndef MEGAPARTICLES_H
+#define MEGAPARTICLES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MP_OK 0
+#define MP_EINVAL (-1)    /* bad argument, size or state                      */
+#define MP_ENOMEM (-2)    /* device allocation failed                         */
+#define MP_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed      */
+#define MP_ETIMEOUT (-4)  /* a bounded device-side wait gave up               */
+#define MP_ENOTINIT (-5)  /* particles not initialised                        */
+
+typedef struct mp_ctx mp_ctx;
+
+/* Filter constants. Printed in the paper: nnf_res (Sec. III-C: 0.1 m indoor,
+ * 0.2 m outdoor), sigma_r = 5 rad^-1 and sigma_t = 2.5 m^-1 (Eq. 7), K (Sec.
+ * III-C, e.g. 20), post_iters (Sec. III-D, e.g. 10). The others are readings
+ * of what the paper leaves open: r_max (NNF search radius), c_max (per-point
+ * cost truncation), alpha and lsh_sigma (Eq. 10), lambda/eps (GN damping),
+ * eps_cov/r_cov/cov_k/cov_min (GICP covariances), C (bucket window),
+ * n_buckets_log2 (N^B = 2^n_buckets_log2). */
+typedef struct mp_params {
+    float nnf_res, r_max, c_max;
+    float sigma_r, sigma_t;
+    float alpha, lsh_sigma;
+    float lambda, eps;
+    float eps_cov, r_cov;
+    int32_t K, C;
+    int32_t cov_k, cov_min;
+    int32_t post_iters;
+    int32_t n_buckets_log2;
+    int32_t max_scan;
+    uint64_t seed;
+} mp_params;
+
+#define MP_PRESET_BOX_ROOM 0   /* 0.1 m NNF, r_max 1 m, K = C = 16           */
+#define MP_PRESET_OUTDOOR 1    /* 0.2 m NNF, r_max 2 m, K = C = 32           */
+
+/* Fill *p with the defaults of a preset. n_particles sets n_buckets_log2 =
+ * ceil(log2(n_particles)). Returns MP_EINVAL for an unknown preset. */
+int mp_default_params(mp_params* p, int preset, int64_t n_particles);
+
+/* Map preprocessing (Sec. III-A map M; Sec. III-C point Gaussians and the
+ * nearest neighbour field m^nnf). xyz: n_map x 3 float32 map points. Computes
+ * each point's GICP normal from its cov_k nearest points within r_cov (fewer
+ * than cov_min: the point is unused), then the NNF: for every voxel of the map
+ * box padded by r_max, the nearest valid map point to the voxel centre within
+ * r_max (-1 if none). cuda_stream: a cudaStream_t the context will use for all
+ * its work (NULL = legacy default stream). On success *ctx owns the device
+ * memory. Errors: MP_EINVAL (NULL/empty input, bad params, grid too large),
+ * MP_ENOMEM, MP_ECUDA; *ctx is NULL on error. */
+int mp_init_map(mp_ctx** ctx, const float* xyz, int64_t n_map, const mp_params* p, void* cuda_stream);
+
+/* Particle set X_t (Sec. III-A), uniform prior, neighbour lists = {self}.
+ * With poses_or_null (n x 7 float32) the poses are copied; otherwise each
+ * particle is drawn on the device from Philox(seed): x, y, z, roll, pitch, yaw
+ * uniform in [lo, hi] (R = Rz(yaw) Ry(pitch) Rx(roll)), or a uniform SO(3)
+ * rotation when all three angle ranges span >= 2 pi (Sec. IV-A, full SO(3)).
+ * log_prior_or_null: n float64 log prior weights (state import); NULL =
+ * uniform. Resets the step counter. Errors: MP_EINVAL, MP_ENOMEM, MP_ECUDA. */
+int mp_init_particles(mp_ctx* ctx, int64_t n_particles, const float lo[6], const float hi[6],
+                      const float* poses_or_null, const double* log_prior_or_null);
+
+/* One filter step on one scan P_t (n_scan x 3 float32, sensor frame).
+ * odom_T: row-major 4x4 float64 relative motion dT_t (NULL = identity);
+ * odom_cov: 6x6 float64 covariance Sigma^dT of the tangent noise (rotation
+ * first; NULL = no noise). n_scan = 0 is a blackout step: prediction, the
+ * neighbour list update and the posterior smoothing run with a zero
+ * log-likelihood; likelihood and SVGD are skipped. Enqueued on the context
+ * stream; advances the step counter. Errors: MP_EINVAL (n_scan > max_scan,
+ * NULL scan with n_scan > 0), MP_ENOTINIT, MP_ECUDA. */
+int mp_step(mp_ctx* ctx, const float* scan_xyz, int32_t n_scan, const double odom_T[16],
+            const double odom_cov[36]);
+
+/* Posterior after the last step (Sec. III-D): poses_out (n x 7 float32),
+ * prob_out (n float64, sums to 1), best_pose (7 float32: the particle with the
+ * highest posterior, smallest index on ties) and best_prob. Any output may be
+ * NULL. Synchronises the stream; reports MP_ETIMEOUT if a device-side wait gave
+ * up during the step. */
+int mp_get_posterior(mp_ctx* ctx, float* poses_out, double* prob_out, float best_pose[7], double* best_prob);
+
+/* Frees every resource of the context (NULL is accepted). */
+int mp_destroy(mp_ctx* ctx);
+
+/* Message of the last error of ctx ("" if none; a static string if ctx is NULL). */
+const char* mp_last_error(const mp_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Stage-level access (the same kernels mp_step runs; used for parity tests,
+ * profiling and state import/export).
+ * ------------------------------------------------------------------------- */
+#define MP_STAGE_PREDICT 0x001u      /* Eq. 1                                   */
+#define MP_STAGE_SCAN 0x002u         /* scan Gaussians + compaction             */
+#define MP_STAGE_LSH 0x004u          /* Eq. 9-10 keys (draws T^LSH, delta^LSH)  */
+#define MP_STAGE_SORT 0x008u         /* Algorithm 1 distribute: stable sort     */
+#define MP_STAGE_MERGE 0x010u        /* Algorithm 1 gather + list refinement    */
+#define MP_STAGE_LIKELIHOOD 0x020u   /* Eq. 2-4 sums                            */
+#define MP_STAGE_SOLVE 0x040u        /* psi = GN step                           */
+#define MP_STAGE_SVGD 0x080u         /* Eq. 5-6                                 */
+#define MP_STAGE_POSTERIOR 0x100u    /* Eq. 11 + argmax                         */
+#define MP_STAGE_ALL 0x1FFu
+
+/* Upload a scan / odometry for the current step without running anything.
+ * Same argument rules as mp_step. */
+int mp_set_scan(mp_ctx* ctx, const float* scan_xyz, int32_t n_scan);
+int mp_set_odometry(mp_ctx* ctx, const double odom_T[16], const double odom_cov[36]);
+
+/* Run the selected stages, in the order of the step, at the current step
+ * index (which is not advanced). Enqueued only. */
+int mp_run_stages(mp_ctx* ctx, uint32_t stage_mask);
+
+/* Step index used by the random draws of the next stage run (mp_step advances
+ * it by one). */
+int mp_set_step_index(mp_ctx* ctx, uint64_t step);
+
+/* Buffers readable (and, where noted, writable) as flat arrays, in particle
+ * order unless noted. count = number of elements of the stated type. */
+#define MP_BUF_POSES 1         /* n x 7 float32          rw                     */
+#define MP_BUF_LOG_PRIOR 2     /* n float64               rw                     */
+#define MP_BUF_KEYS 3          /* n uint32 LSH keys        r                     */
+#define MP_BUF_BUCKETS 4       /* n uint32 key mod N^B     r                     */
+#define MP_BUF_SORTED_IDS 5    /* n int32 stable order     rw                    */
+#define MP_BUF_SEGMENTS 6      /* n x 2 int32 [lo, hi) of each particle's bucket in the sorted order  r */
+#define MP_BUF_NBR_IDS 7       /* n x K int32, -1 padded   rw (current lists)     */
+#define MP_BUF_NBR_K 8         /* n x K float32 k_ij       rw                     */
+#define MP_BUF_NBR_D 9         /* n x K x 6 float32 d_ij   rw                     */
+#define MP_BUF_GN 10           /* n x 29 float32: H (21, upper rows), b (6), log-lik, inliers  r */
+#define MP_BUF_PSI 11          /* n x 6 float32 GN steps   rw                     */
+#define MP_BUF_POST 12         /* n float64 posterior      r                      */
+#define MP_BUF_POST_INIT 13    /* n float64 initial posterior (before Eq. 11)  r  */
+#define MP_BUF_LOGLIK 14       /* n float32 log-likelihood rw                     */
+#define MP_BUF_SCAN_NORMALS 15 /* n_scan x 3 float32       r                      */
+#define MP_BUF_SCAN_VALID 16   /* n_scan uint8             r                      */
+#define MP_BUF_MAP_NORMALS 17  /* n_map x 3 float32        r                      */
+#define MP_BUF_MAP_VALID 18    /* n_map uint8              r                      */
+#define MP_BUF_LSH 19          /* 13 float64: T^LSH q (4), t (3), delta (6)  r    */
+#define MP_BUF_PHI 20          /* n x 6 float32 SVGD update r                     */
+
+/* Element count of a buffer (0 if not allocated). */
+int mp_buffer_size(mp_ctx* ctx, int which, int64_t* count);
+/* Copy a buffer out (synchronises the stream). count must equal its size. */
+int mp_get_buffer(mp_ctx* ctx, int which, void* dst, int64_t count);
+/* Overwrite a writable buffer (synchronises the stream). */
+int mp_set_buffer(mp_ctx* ctx, int which, const void* src, int64_t count);
+
+/* NNF values of m voxels (m x 3 int32 integer coordinates; outside the grid:
+ * -1). Synchronises. */
+int mp_nnf_query(mp_ctx* ctx, const int32_t* vox, int64_t m, int32_t* out);
+
+/* NNF grid geometry: origin o, dims n, inv_res = 1/res and off = -(o*inv_res)
+ * (FP32), such that a point q has voxel floor(fma(q, inv_res, off)); n_valid =
+ * number of map points with a covariance. */
+int mp_map_info(mp_ctx* ctx, float origin[3], int32_t dims[3], float* inv_res, float off[3], int64_t* n_valid);
+
+/* Per-stage device times (CUDA events on the context stream) of the last
+ * mp_step / mp_run_stages, in stage-bit order (9 floats, ms; 0 for stages not
+ * run). Timing must be enabled first; enabling adds event records only. */
+int mp_set_timing(mp_ctx* ctx, int enable);
+int mp_stage_times(mp_ctx* ctx, float ms_out[9]);
+
+/* Number of kernels this context has launched so far. */
+int mp_kernel_launches(mp_ctx* ctx, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MEGAPARTICLES_H */

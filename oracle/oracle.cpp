@@ -193,14 +193,26 @@ void V_of(const double w[3], double V[9], bool inverse) {
   double S[9], S2[9];
   skew(w, S);
   matmul3(S, S, S2);
+  // Evaluated without cancellation: A = 2 sin^2(th/2) / th^2,
+  // B = (th - sin th) / th^3 and C = (1 - (th/2) cot(th/2)) / th^2, with their
+  // Taylor series below th = 1e-2.
   double a, b;
   if (!inverse) {
-    if (th < 1e-5) { a = 0.5 - th2 / 24.0; b = 1.0 / 6.0 - th2 / 120.0; }
-    else { a = (1.0 - std::cos(th)) / th2; b = (th - std::sin(th)) / (th2 * th); }
+    if (th < 1e-2) {
+      a = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+      b = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    } else {
+      double sh = std::sin(0.5 * th);
+      a = 2.0 * sh * sh / th2;
+      b = (th - std::sin(th)) / (th2 * th);
+    }
   } else {
     a = -0.5;
-    if (th < 1e-5) b = 1.0 / 12.0 + th2 / 720.0;
-    else b = (1.0 - th * std::sin(th) / (2.0 * (1.0 - std::cos(th)))) / th2;
+    if (th < 1e-2) b = 1.0 / 12.0 + th2 / 720.0 + th2 * th2 / 30240.0;
+    else {
+      double h = 0.5 * th;
+      b = (1.0 - h * std::cos(h) / std::sin(h)) / th2;
+    }
   }
   for (int i = 0; i < 9; ++i) V[i] = a * S[i] + b * S2[i];
   V[0] += 1; V[4] += 1; V[8] += 1;

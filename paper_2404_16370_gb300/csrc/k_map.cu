@@ -1,0 +1,477 @@
+// Map and scan preprocessing (Sec. III-C):
+//  * GICP point Gaussians: each point's normal from its cov_k nearest points
+//    within r_cov (decided by the exact FP32 distance sequence, ties to the
+//    smaller index); Sigma = I - (1 - eps_cov) n n^T is carried as n.
+//  * the nearest neighbour field m^nnf: per voxel, the nearest valid map point
+//    to the voxel centre within r_max (-1 if none).
+//  * per-step scan Gaussians and the compaction of the valid scan points into
+//    the 32-byte records the likelihood kernel streams through shared memory.
+#include "mp_internal.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace {
+
+// Uniform cell grid of side h over a point set (exact candidate filter: every
+// point within distance h of a query lies in the 27 cells around it).
+struct CellGridDev {
+    float og[3], inv_h;
+    int dims[3];
+    int64_t ncell;
+    uint32_t* start = nullptr;   // ncell + 1
+    int32_t* items = nullptr;    // points, grouped by cell
+};
+
+__device__ __forceinline__ void cell_coords(const CellGridDev& g, float x, float y, float z, int c[3]) {
+    float p[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int v = (int)floorf((p[a] - g.og[a]) * g.inv_h);
+        c[a] = min(max(v, -1), g.dims[a]);
+    }
+}
+
+__global__ void k_cell_count(const float4* __restrict__ pts, const uint8_t* __restrict__ valid, int64_t n,
+                             CellGridDev g, int32_t* __restrict__ cell_of, uint32_t* __restrict__ count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (valid && !valid[i]) { cell_of[i] = -1; return; }
+    float4 p = pts[i];
+    int c[3];
+    cell_coords(g, p.x, p.y, p.z, c);
+    c[0] = min(max(c[0], 0), g.dims[0] - 1);
+    c[1] = min(max(c[1], 0), g.dims[1] - 1);
+    c[2] = min(max(c[2], 0), g.dims[2] - 1);
+    int64_t ci = ((int64_t)c[2] * g.dims[1] + c[1]) * g.dims[0] + c[0];
+    cell_of[i] = (int32_t)ci;
+    atomicAdd(&count[ci], 1u);
+}
+
+__global__ void k_cell_fill(const int32_t* __restrict__ cell_of, int64_t n, const uint32_t* __restrict__ start,
+                            uint32_t* __restrict__ fill, int32_t* __restrict__ items) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = cell_of[i];
+    if (c < 0) return;
+    uint32_t pos = atomicAdd(&fill[c], 1u);
+    items[start[c] + pos] = (int32_t)i;
+}
+
+// Sorted insertion of (d, j) into the MP_COVK smallest pairs seen so far.
+__device__ __forceinline__ void topk_insert(float (&D)[MP_COVK], int (&J)[MP_COVK], float d, int j) {
+#pragma unroll
+    for (int s = 0; s < MP_COVK; ++s) {
+        bool lt = (d < D[s]) || (d == D[s] && j < J[s]);
+        float td = D[s];
+        int tj = J[s];
+        D[s] = lt ? d : td;
+        J[s] = lt ? j : tj;
+        d = lt ? td : d;
+        j = lt ? tj : j;
+    }
+}
+
+// Normal of a 3x3 covariance (FP64): smallest eigenvalue by the closed-form
+// trigonometric solution of the characteristic cubic (Smith, CACM 1961),
+// refined once by the Rayleigh quotient of its eigenvector; the eigenvector
+// is the largest cross product of two rows of (C - lambda I). Sign: the
+// largest-magnitude component positive (first index on ties).
+__device__ void normal_of_cov(const double C[6], float n_out[3]) {
+    // C = (xx, xy, xz, yy, yz, zz)
+    double a00 = C[0], a01 = C[1], a02 = C[2], a11 = C[3], a12 = C[4], a22 = C[5];
+    double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    double q = (a00 + a11 + a22) / 3.0;
+    double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
+    double lam;
+    if (p2 <= 0.0) {
+        lam = q;
+    } else {
+        double p = sqrt(p2 / 6.0);
+        double ip = 1.0 / p;
+        double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+        double det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02);
+        double r = fmin(1.0, fmax(-1.0, 0.5 * det));
+        double phi = acos(r) / 3.0;
+        lam = q + 2.0 * p * cos(phi + 2.0943951023931954923);   // + 2 pi / 3: the smallest root
+    }
+    double v[3] = {0, 0, 1};
+    for (int it = 0; it < 2; ++it) {
+        double r0[3] = {a00 - lam, a01, a02}, r1[3] = {a01, a11 - lam, a12}, r2[3] = {a02, a12, a22 - lam};
+        double c[3][3];
+        c[0][0] = r0[1] * r1[2] - r0[2] * r1[1]; c[0][1] = r0[2] * r1[0] - r0[0] * r1[2]; c[0][2] = r0[0] * r1[1] - r0[1] * r1[0];
+        c[1][0] = r0[1] * r2[2] - r0[2] * r2[1]; c[1][1] = r0[2] * r2[0] - r0[0] * r2[2]; c[1][2] = r0[0] * r2[1] - r0[1] * r2[0];
+        c[2][0] = r1[1] * r2[2] - r1[2] * r2[1]; c[2][1] = r1[2] * r2[0] - r1[0] * r2[2]; c[2][2] = r1[0] * r2[1] - r1[1] * r2[0];
+        double nn[3];
+        int best = 0;
+        for (int k = 0; k < 3; ++k) nn[k] = c[k][0] * c[k][0] + c[k][1] * c[k][1] + c[k][2] * c[k][2];
+        if (nn[1] > nn[best]) best = 1;
+        if (nn[2] > nn[best]) best = 2;
+        if (!(nn[best] > 0.0)) break;   // (near) repeated smallest eigenvalue: keep v
+        double s = 1.0 / sqrt(nn[best]);
+        v[0] = c[best][0] * s; v[1] = c[best][1] * s; v[2] = c[best][2] * s;
+        // Rayleigh quotient of the current vector refines lambda
+        double Av0 = a00 * v[0] + a01 * v[1] + a02 * v[2];
+        double Av1 = a01 * v[0] + a11 * v[1] + a12 * v[2];
+        double Av2 = a02 * v[0] + a12 * v[1] + a22 * v[2];
+        lam = v[0] * Av0 + v[1] * Av1 + v[2] * Av2;
+    }
+    int big = 0;
+    if (fabs(v[1]) > fabs(v[big])) big = 1;
+    if (fabs(v[2]) > fabs(v[big])) big = 2;
+    double sg = v[big] < 0 ? -1.0 : 1.0;
+    n_out[0] = (float)(sg * v[0]);
+    n_out[1] = (float)(sg * v[1]);
+    n_out[2] = (float)(sg * v[2]);
+}
+
+// FP64 sample covariance of the first m neighbours and the resulting normal.
+__device__ void neighbourhood_normal(const float4* __restrict__ pts, const int (&J)[MP_COVK], int m, float n_out[3]) {
+    double mx = 0, my = 0, mz = 0;
+    for (int s = 0; s < m; ++s) {
+        float4 p = pts[J[s]];
+        mx += p.x; my += p.y; mz += p.z;
+    }
+    mx /= m; my /= m; mz /= m;
+    double C[6] = {0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < m; ++s) {
+        float4 p = pts[J[s]];
+        double dx = p.x - mx, dy = p.y - my, dz = p.z - mz;
+        C[0] += dx * dx; C[1] += dx * dy; C[2] += dx * dz;
+        C[3] += dy * dy; C[4] += dy * dz; C[5] += dz * dz;
+    }
+    for (int a = 0; a < 6; ++a) C[a] /= m;
+    normal_of_cov(C, n_out);
+}
+
+// Map points: neighbourhoods through the cell grid.
+__global__ void k_map_normals(const float4* __restrict__ pts, int64_t n, CellGridDev g, float r2, int k, int kmin,
+                              float* __restrict__ normals, uint8_t* __restrict__ valid) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 pi = pts[i];
+    float D[MP_COVK];
+    int J[MP_COVK];
+#pragma unroll
+    for (int s = 0; s < MP_COVK; ++s) { D[s] = INFINITY; J[s] = 0x7fffffff; }
+    int cnt = 0;
+    int c[3];
+    cell_coords(g, pi.x, pi.y, pi.z, c);
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
+                if (x < 0 || y < 0 || z < 0 || x >= g.dims[0] || y >= g.dims[1] || z >= g.dims[2]) continue;
+                int64_t ci = ((int64_t)z * g.dims[1] + y) * g.dims[0] + x;
+                for (uint32_t e = g.start[ci]; e < g.start[ci + 1]; ++e) {
+                    int j = g.items[e];
+                    float4 pj = pts[j];
+                    float d2 = dist2_exact(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z);
+                    if (d2 <= r2) {
+                        cnt++;
+                        topk_insert(D, J, d2, j);
+                    }
+                }
+            }
+    int m = min(cnt, k);
+    if (m < kmin) {
+        valid[i] = 0;
+        normals[3 * i] = normals[3 * i + 1] = normals[3 * i + 2] = 0.f;
+        return;
+    }
+    float nv[3];
+    neighbourhood_normal(pts, J, m, nv);
+    normals[3 * i] = nv[0]; normals[3 * i + 1] = nv[1]; normals[3 * i + 2] = nv[2];
+    valid[i] = 1;
+}
+
+// Scan points: brute force over the whole scan, staged through shared memory.
+#define SCAN_TILE 1024
+__global__ void __launch_bounds__(256) k_scan_normals(const float* __restrict__ raw, int n, float r2, int k, int kmin,
+                                                      float4* __restrict__ tmp_pts, float* __restrict__ normals,
+                                                      uint8_t* __restrict__ valid) {
+    __shared__ float sx[SCAN_TILE], sy[SCAN_TILE], sz[SCAN_TILE];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float px = 0, py = 0, pz = 0;
+    if (i < n) { px = raw[3 * i]; py = raw[3 * i + 1]; pz = raw[3 * i + 2]; }
+    float D[MP_COVK];
+    int J[MP_COVK];
+#pragma unroll
+    for (int s = 0; s < MP_COVK; ++s) { D[s] = INFINITY; J[s] = 0x7fffffff; }
+    int cnt = 0;
+    for (int base = 0; base < n; base += SCAN_TILE) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < SCAN_TILE && base + t < n; t += blockDim.x) {
+            sx[t] = raw[3 * (base + t)]; sy[t] = raw[3 * (base + t) + 1]; sz[t] = raw[3 * (base + t) + 2];
+        }
+        __syncthreads();
+        int m = min(SCAN_TILE, n - base);
+        if (i < n) {
+            for (int t = 0; t < m; ++t) {
+                float d2 = dist2_exact(px, py, pz, sx[t], sy[t], sz[t]);
+                if (d2 <= r2) {
+                    cnt++;
+                    topk_insert(D, J, d2, base + t);
+                }
+            }
+        }
+    }
+    if (i >= n) return;
+    int m = min(cnt, k);
+    if (m < kmin) {
+        valid[i] = 0;
+        normals[3 * i] = normals[3 * i + 1] = normals[3 * i + 2] = 0.f;
+        return;
+    }
+    float nv[3];
+    neighbourhood_normal(tmp_pts, J, m, nv);
+    normals[3 * i] = nv[0]; normals[3 * i + 1] = nv[1]; normals[3 * i + 2] = nv[2];
+    valid[i] = 1;
+}
+
+__global__ void k_scan_to_float4(const float* __restrict__ raw, int n, float4* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float4(raw[3 * i], raw[3 * i + 1], raw[3 * i + 2], 0.f);
+}
+
+// Order-preserving compaction of the valid scan points into 32-byte records.
+__global__ void __launch_bounds__(1024) k_scan_compact(const float* __restrict__ raw, const float* __restrict__ normals,
+                                                       const uint8_t* __restrict__ valid, int n,
+                                                       float4* __restrict__ out, int32_t* __restrict__ nvalid) {
+    __shared__ int warp_tot[32];
+    __shared__ int base_s;
+    if (threadIdx.x == 0) base_s = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int start = 0; start < n; start += blockDim.x) {
+        int i = start + threadIdx.x;
+        int f = (i < n && valid[i]) ? 1 : 0;
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        int in_warp = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[w] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            if (k < w) off += warp_tot[k];
+            tot += warp_tot[k];
+        }
+        int base = base_s;
+        if (f) {
+            int o = base + off + in_warp;
+            out[2 * o] = make_float4(raw[3 * i], raw[3 * i + 1], raw[3 * i + 2], normals[3 * i]);
+            out[2 * o + 1] = make_float4(normals[3 * i + 1], normals[3 * i + 2], 0.f, 0.f);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base_s = base + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *nvalid = base_s;
+}
+
+// NNF: nearest valid map point to each voxel centre within r_max.
+__global__ void k_nnf_build(const float4* __restrict__ pts, CellGridDev g, int nx, int ny, int64_t nvox, float ox,
+                            float oy, float oz, float res, float r2, int32_t* __restrict__ nnf) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nvox) return;
+    int vx = (int)(idx % nx);
+    int64_t r = idx / nx;
+    int vy = (int)(r % ny);
+    int vz = (int)(r / ny);
+    float cx = __fadd_rn(ox, __fmul_rn(__fadd_rn((float)vx, 0.5f), res));
+    float cy = __fadd_rn(oy, __fmul_rn(__fadd_rn((float)vy, 0.5f), res));
+    float cz = __fadd_rn(oz, __fmul_rn(__fadd_rn((float)vz, 0.5f), res));
+    int c[3];
+    cell_coords(g, cx, cy, cz, c);
+    int best = -1;
+    float bd = INFINITY;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
+                if (x < 0 || y < 0 || z < 0 || x >= g.dims[0] || y >= g.dims[1] || z >= g.dims[2]) continue;
+                int64_t ci = ((int64_t)z * g.dims[1] + y) * g.dims[0] + x;
+                for (uint32_t e = g.start[ci]; e < g.start[ci + 1]; ++e) {
+                    int j = g.items[e];
+                    float4 p = pts[j];
+                    float d2 = dist2_exact(cx, cy, cz, p.x, p.y, p.z);
+                    if (d2 <= r2 && (d2 < bd || (d2 == bd && j < best))) { bd = d2; best = j; }
+                }
+            }
+    nnf[idx] = best;
+}
+
+__global__ void k_map_records(const float4* __restrict__ pts, const float* __restrict__ normals, int64_t n,
+                              float4* __restrict__ rec) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 p = pts[i];
+    rec[2 * i] = make_float4(p.x, p.y, p.z, normals[3 * i]);
+    rec[2 * i + 1] = make_float4(normals[3 * i + 1], normals[3 * i + 2], 0.f, 0.f);
+}
+
+__global__ void k_nnf_query(const int32_t* __restrict__ nnf, int nx, int ny, int nz, const int32_t* __restrict__ vox,
+                            int64_t m, int32_t* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int x = vox[3 * i], y = vox[3 * i + 1], z = vox[3 * i + 2];
+    bool in = x >= 0 && y >= 0 && z >= 0 && x < nx && y < ny && z < nz;
+    out[i] = in ? nnf[((int64_t)z * ny + y) * nx + x] : -1;
+}
+
+__global__ void k_pts_from_xyz(const float* __restrict__ xyz, int64_t n, float4* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.f);
+}
+
+// Builds the cell grid of the (valid) points with cell side h over [lo, hi].
+int build_cells(mp_ctx* c, const float4* pts, const uint8_t* valid, int64_t n, float h, const float lo[3],
+                const float hi[3], CellGridDev& g, int32_t** cell_of_out) {
+    g.inv_h = 1.0f / h;
+    g.ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        g.og[a] = lo[a] - h;
+        g.dims[a] = (int)std::floor((hi[a] - g.og[a]) / h) + 2;
+        g.ncell *= g.dims[a];
+    }
+    if (g.ncell > (int64_t)1 << 30) return mp_fail(c, MP_EINVAL, "cell grid too large (%lld cells)", (long long)g.ncell);
+    int32_t* cell_of = nullptr;
+    uint32_t *count = nullptr, *fill = nullptr;
+    MP_CUDA(c, cudaMalloc(&cell_of, sizeof(int32_t) * (size_t)n));
+    MP_CUDA(c, cudaMalloc(&count, sizeof(uint32_t) * (size_t)(g.ncell + 1)));
+    MP_CUDA(c, cudaMalloc(&fill, sizeof(uint32_t) * (size_t)(g.ncell + 1)));
+    MP_CUDA(c, cudaMalloc(&g.start, sizeof(uint32_t) * (size_t)(g.ncell + 1)));
+    MP_CUDA(c, cudaMalloc(&g.items, sizeof(int32_t) * (size_t)n));
+    MP_CUDA(c, cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)(g.ncell + 1), c->stream));
+    MP_CUDA(c, cudaMemsetAsync(fill, 0, sizeof(uint32_t) * (size_t)(g.ncell + 1), c->stream));
+    k_cell_count<<<grid_for(n, 256), 256, 0, c->stream>>>(pts, valid, n, g, cell_of, count);
+    MP_LAUNCHED(c);
+    int rc = mp_launch_exclusive_scan(c, count, g.start, g.ncell + 1);
+    if (rc) return rc;
+    k_cell_fill<<<grid_for(n, 256), 256, 0, c->stream>>>(cell_of, n, g.start, fill, g.items);
+    MP_LAUNCHED(c);
+    MP_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(count);
+    cudaFree(fill);
+    *cell_of_out = cell_of;
+    return MP_OK;
+}
+
+void free_cells(CellGridDev& g) {
+    cudaFree(g.start);
+    cudaFree(g.items);
+    g.start = nullptr;
+    g.items = nullptr;
+}
+
+}  // namespace
+
+// Map preprocessing: normals, validity, NNF geometry (host, FP32 sequence),
+// NNF grid and records. xyz_dev: n_map x 3 float32 on the device.
+int mp_launch_map_prepare(mp_ctx* c, const float* xyz_dev) {
+    int64_t n = c->n_map;
+    k_pts_from_xyz<<<grid_for(n, 256), 256, 0, c->stream>>>(xyz_dev, n, c->map_pts);
+    MP_LAUNCHED(c);
+    // bounding box of all points (exact FP32 min/max on the host)
+    std::vector<float> h(3 * (size_t)n);
+    MP_CUDA(c, cudaMemcpyAsync(h.data(), xyz_dev, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(c, cudaStreamSynchronize(c->stream));
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            float v = h[3 * i + a];
+            if (!std::isfinite(v)) return mp_fail(c, MP_EINVAL, "map point %lld is not finite", (long long)i);
+            lo[a] = fminf(lo[a], v);
+            hi[a] = fmaxf(hi[a], v);
+        }
+    // normals through a cell grid of side r_cov (+0.1 % margin)
+    CellGridDev g;
+    int32_t* cell_of = nullptr;
+    int rc = build_cells(c, c->map_pts, nullptr, n, c->p.r_cov * 1.001f, lo, hi, g, &cell_of);
+    if (rc) return rc;
+    float r2c = c->p.r_cov * c->p.r_cov;
+    k_map_normals<<<grid_for(n, 128), 128, 0, c->stream>>>(c->map_pts, n, g, r2c, c->p.cov_k, c->p.cov_min,
+                                                            c->map_normals, c->map_valid);
+    MP_LAUNCHED(c);
+    MP_CUDA(c, cudaStreamSynchronize(c->stream));
+    free_cells(g);
+    cudaFree(cell_of);
+    // NNF geometry from the valid points, by the FP32 sequence:
+    // o = lo - r_max; n = floor(((hi + r_max) - o) * inv_res) + 1; off = -(o * inv_res)
+    std::vector<uint8_t> v((size_t)n);
+    MP_CUDA(c, cudaMemcpy(v.data(), c->map_valid, (size_t)n, cudaMemcpyDeviceToHost));
+    float vlo[3] = {INFINITY, INFINITY, INFINITY}, vhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int64_t nv = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!v[i]) continue;
+        nv++;
+        for (int a = 0; a < 3; ++a) {
+            vlo[a] = fminf(vlo[a], h[3 * i + a]);
+            vhi[a] = fmaxf(vhi[a], h[3 * i + a]);
+        }
+    }
+    c->n_map_valid = nv;
+    if (nv == 0) return mp_fail(c, MP_EINVAL, "no map point has %d neighbours within r_cov", c->p.cov_min);
+    volatile float res = c->p.nnf_res, rmax = c->p.r_max;
+    volatile float inv_res = 1.0f / res;
+    c->nnf_inv_res = inv_res;
+    c->nnf_voxels = 1;
+    for (int a = 0; a < 3; ++a) {
+        volatile float o = vlo[a] - rmax;
+        volatile float t1 = vhi[a] + rmax;
+        volatile float t2 = t1 - o;
+        volatile float t3 = t2 * inv_res;
+        volatile float po = o * inv_res;
+        c->nnf_origin[a] = o;
+        c->nnf_dims[a] = (int32_t)std::floor((float)t3) + 1;
+        c->nnf_off[a] = -po;
+        c->nnf_voxels *= c->nnf_dims[a];
+        c->map_lo[a] = vlo[a];
+        c->map_hi[a] = vhi[a];
+    }
+    if (c->nnf_voxels >= ((int64_t)1 << 31))
+        return mp_fail(c, MP_EINVAL, "NNF grid of %lld voxels exceeds 2^31", (long long)c->nnf_voxels);
+    MP_CUDA(c, cudaMalloc(&c->nnf, sizeof(int32_t) * (size_t)c->nnf_voxels));
+    rc = build_cells(c, c->map_pts, c->map_valid, n, c->p.r_max * 1.001f, vlo, vhi, g, &cell_of);
+    if (rc) return rc;
+    float r2 = c->p.r_max * c->p.r_max;
+    k_nnf_build<<<grid_for(c->nnf_voxels, 256), 256, 0, c->stream>>>(
+        c->map_pts, g, c->nnf_dims[0], c->nnf_dims[1], c->nnf_voxels, c->nnf_origin[0], c->nnf_origin[1],
+        c->nnf_origin[2], c->p.nnf_res, r2, c->nnf);
+    MP_LAUNCHED(c);
+    k_map_records<<<grid_for(n, 256), 256, 0, c->stream>>>(c->map_pts, c->map_normals, n, c->map_rec);
+    MP_LAUNCHED(c);
+    MP_CUDA(c, cudaStreamSynchronize(c->stream));
+    free_cells(g);
+    cudaFree(cell_of);
+    return MP_OK;
+}
+
+// Per-step scan Gaussians (brute-force radius kNN in shared-memory tiles) and
+// compaction of the valid points.
+int mp_launch_scan_prepare(mp_ctx* c) {
+    int n = c->n_scan;
+    if (n == 0) {
+        MP_CUDA(c, cudaMemsetAsync(c->scan_nvalid, 0, sizeof(int32_t), c->stream));
+        return MP_OK;
+    }
+    float4* tmp = (float4*)c->gn;   // gn is free during this stage and holds >= 4 * max_scan floats
+    k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(c->scan_raw, n, tmp);
+    MP_LAUNCHED(c);
+    float r2 = c->p.r_cov * c->p.r_cov;
+    k_scan_normals<<<grid_for(n, 256), 256, 0, c->stream>>>(c->scan_raw, n, r2, c->p.cov_k, c->p.cov_min, tmp,
+                                                             c->scan_normals, c->scan_valid);
+    MP_LAUNCHED(c);
+    k_scan_compact<<<1, 1024, 0, c->stream>>>(c->scan_raw, c->scan_normals, c->scan_valid, n, c->scan_pts,
+                                              c->scan_nvalid);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_nnf_query(mp_ctx* c, const int32_t* vox_dev, int64_t m, int32_t* out_dev) {
+    if (m == 0) return MP_OK;
+    k_nnf_query<<<grid_for(m, 256), 256, 0, c->stream>>>(c->nnf, c->nnf_dims[0], c->nnf_dims[1], c->nnf_dims[2],
+                                                         vox_dev, m, out_dev);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}

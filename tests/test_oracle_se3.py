@@ -91,3 +91,13 @@ def test_relative_log_is_log_of_relative_transform(oracle):
         dji = oracle.relative_log(pj, pi)
         if np.linalg.norm(d[:3]) < np.pi - 1e-6:
             assert np.allclose(dji, -d, atol=1e-11)
+
+
+@pytest.mark.parametrize("theta", [1e-6, 1e-4, 1e-3, 5e-3, 1e-2, 2e-2, 0.1])
+def test_log_small_angle_large_translation(oracle, theta):
+    # the translation part of log (V^-1 t) must stay accurate where
+    # 1 - cos(theta) cancels: LSH floors (Eq. 10) depend on it at 1e-9
+    xi = np.array([theta, 0.3 * theta, -0.2 * theta, 100.0, 50.0, -30.0])
+    T = expm(hat(xi))
+    q = Rotation.from_matrix(T[:3, :3]).as_quat()
+    assert np.abs(oracle.se3_log(q, T[:3, 3]) - xi).max() < 1e-12
