@@ -676,9 +676,12 @@ void or_voxel_of(void* h, const float* pose, const float* mu, int32_t v[3], floa
 //   for inliers, J_k = d e_k / d xi = R [ [mu^S_k]x , -I ]  (right
 //   perturbation T exp(xi)), H += J^T Omega J, b += J^T Omega e.
 // amb counts inlier decisions within amb_tol * c_max of the threshold.
+// absum (optional, np x 28): per output entry the sum of the magnitudes of
+// its terms (H 21, b 6, log-likelihood 1), the scale of its rounding error.
 int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const double* scan_n,
                   const uint8_t* scan_valid, i64 ns, double c_max, double eps_cov, double amb_tol,
-                  double* H, double* b, double* loglik, int32_t* n_in, int32_t* amb, int nthreads) {
+                  double* H, double* b, double* loglik, int32_t* n_in, int32_t* amb, double* absum,
+                  int nthreads) {
   Map* M = (Map*)h;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -697,7 +700,7 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
       double R[9];
       quat_to_R(q, R);  // the stored quaternion as given (unit up to FP32 rounding)
       double t[3] = {P[4], P[5], P[6]};
-      double Hl[21] = {0}, bl[6] = {0}, ll = 0;
+      double Hl[21] = {0}, bl[6] = {0}, ll = 0, ab[28] = {0};
       int cnt = 0, namb = 0;
       for (i64 k = 0; k < ns; ++k) {
         if (scan_valid && !scan_valid[k]) continue;
@@ -713,7 +716,7 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
           if (it != memo.end()) m = it->second;
           else { m = nnf_value(*M, v, false); memo.emplace(lin, m); }
         }
-        if (m < 0) { ll -= c_max; continue; }
+        if (m < 0) { ll -= c_max; ab[27] += c_max; continue; }
         double mus[3] = {mu[0], mu[1], mu[2]};
         double qk[3];
         matvec3(R, mus, qk);
@@ -727,13 +730,14 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
         matmul3(R, SS, RS);
         matmul3(RS, Rt, RSRt);
         for (int a = 0; a < 9; ++a) C[a] = SM[a] + RSRt[a];
-        if (!inv3(C, Om)) { ll -= c_max; continue; }
+        if (!inv3(C, Om)) { ll -= c_max; ab[27] += c_max; continue; }
         double Oe[3];
         matvec3(Om, e, Oe);
         double c = e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];
         if (std::fabs(c - c_max) <= amb_tol * c_max) namb++;
-        if (!(c <= c_max)) { ll -= c_max; continue; }
+        if (!(c <= c_max)) { ll -= c_max; ab[27] += c_max; continue; }
         ll -= c;
+        ab[27] += std::fabs(c);
         cnt++;
         // J = R [ [mu]x , -I ]
         double S[9], J0[9], J[3][6];
@@ -749,10 +753,12 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
             double s = 0;
             for (int r = 0; r < 3; ++r) s += J[r][a] * OJ[r][bb];
             Hl[H_IDX[a][bb]] += s;
+            ab[H_IDX[a][bb]] += std::fabs(s);
           }
           double s = 0;
           for (int r = 0; r < 3; ++r) s += J[r][a] * Oe[r];
           bl[a] += s;
+          ab[21 + a] += std::fabs(s);
         }
       }
       for (int a = 0; a < 21; ++a) H[21 * i + a] = Hl[a];
@@ -760,6 +766,7 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
       loglik[i] = ll;
       n_in[i] = cnt;
       if (amb) amb[i] = namb;
+      if (absum) for (int a = 0; a < 28; ++a) absum[28 * i + a] = ab[a];
     }
   }
   return 0;
@@ -950,14 +957,18 @@ void or_bucket_sort(const u32* buckets, i64 np, int32_t* sorted_ids, int32_t* ra
 // (relative) of each other.
 void or_neighbor_merge(const float* poses, i64 np, const int32_t* old_ids, int K, int C,
                        const int32_t* sorted_ids, const int32_t* rank, const int32_t* seg_lo,
-                       const int32_t* seg_hi, double sr, double st, double tie_tol, int32_t* ids,
-                       double* kk, double* dd, int32_t* flags, int nthreads) {
+                       const int32_t* seg_hi, double sr, double st, double tie_tol, const int32_t* subset,
+                       i64 n_subset, int32_t* ids, double* kk, double* dd, int32_t* flags, int nthreads) {
+  // subset (optional): compute only these particles; output row r belongs to
+  // particle subset[r].
   double W[6] = {sr, sr, sr, st, st, st};
+  i64 n_out = subset ? n_subset : np;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 64)
 #endif
-  for (i64 i = 0; i < np; ++i) {
+  for (i64 row = 0; row < n_out; ++row) {
+    i64 i = subset ? (i64)subset[row] : row;
     std::vector<int32_t> cand;
     if (old_ids)
       for (int a = 0; a < K; ++a) {
@@ -995,12 +1006,12 @@ void or_neighbor_merge(const float* poses, i64 np, const int32_t* old_ids, int K
       double a = ev[keep - 1].s, bb = ev[keep].s;
       if (bb - a <= tie_tol * std::max(bb, 1e-300)) fl = 1;
     }
-    if (flags) flags[i] = fl;
-    ids[i * K] = (int32_t)i;
-    kk[i * K] = 1.0;
-    for (int a = 0; a < 6; ++a) dd[(i * K) * 6 + a] = 0;
+    if (flags) flags[row] = fl;
+    ids[row * K] = (int32_t)i;
+    kk[row * K] = 1.0;
+    for (int a = 0; a < 6; ++a) dd[(row * K) * 6 + a] = 0;
     for (int slot = 1; slot < K; ++slot) {
-      i64 o = i * K + slot;
+      i64 o = row * K + slot;
       if (slot - 1 < keep) {
         const E& x = ev[slot - 1];
         ids[o] = x.j;

@@ -76,13 +76,13 @@ def _declare(L):
     L.or_map_geometry.argtypes = [_P, _P, _P, _P, _P]
     L.or_map_nnf.argtypes = [_P, _P, _I64, _P, _INT, _INT]
     L.or_voxel_of.argtypes = [_P, _P, _P, _P, _P]
-    L.or_likelihood.argtypes = [_P, _P, _I64, _P, _P, _P, _I64, _D, _D, _D, _P, _P, _P, _P, _P, _INT]
+    L.or_likelihood.argtypes = [_P, _P, _I64, _P, _P, _P, _I64, _D, _D, _D, _P, _P, _P, _P, _P, _P, _INT]
     L.or_likelihood_pairs.argtypes = [_P, _P, _P, _P, _P, _I64, _D, _D, _P, _P, _P, _P, _P, _P]
     L.or_gn_solve.argtypes = [_P, _P, _P, _I64, _D, _D, _P, _P]
     L.or_lsh_draw.argtypes = [_U64, _U64, _P, _P, _D, _P, _P, _P]
     L.or_lsh_keys.argtypes = [_P, _I64, _P, _P, _P, _D, _D, _D, _INT, _P, _P, _P, _P]
     L.or_bucket_sort.argtypes = [_P, _I64, _P, _P, _P, _P]
-    L.or_neighbor_merge.argtypes = [_P, _I64, _P, _INT, _INT, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P, _INT]
+    L.or_neighbor_merge.argtypes = [_P, _I64, _P, _INT, _INT, _P, _P, _P, _P, _D, _D, _D, _P, _I64, _P, _P, _P, _P, _INT]
     L.or_svgd.argtypes = [_P, _I64, _P, _P, _P, _INT, _P, _D, _D, _P, _P]
     L.or_posterior.argtypes = [_P, _P, _I64, _P, _P, _INT, _INT, _P, _P, _P]
     L.or_cholesky6.argtypes = [_P, _P]
@@ -232,15 +232,17 @@ class OracleMap:
 
 
 def likelihood(m: OracleMap, poses, scan, scan_n, scan_valid, params: Params, amb_tol=1e-3, nthreads=0):
+    """H (n,21), b (n,6), loglik, n_in, amb (ambiguous inlier decisions) and
+    absum (n,28): the sum of term magnitudes of each output entry."""
     poses = _c(poses, np.float32).reshape(-1, 7)
     scan = _c(scan, np.float32).reshape(-1, 3)
     npart = len(poses)
     H = np.zeros((npart, 21)); b = np.zeros((npart, 6)); ll = np.zeros(npart)
-    n_in = np.zeros(npart, np.int32); amb = np.zeros(npart, np.int32)
+    n_in = np.zeros(npart, np.int32); amb = np.zeros(npart, np.int32); absum = np.zeros((npart, 28))
     lib().or_likelihood(m.h, _p(poses), npart, _p(scan), _p(_c(scan_n, np.float64)),
                         _p(_c(scan_valid, np.uint8)), len(scan), params.c_max, params.eps_cov, amb_tol,
-                        _p(H), _p(b), _p(ll), _p(n_in), _p(amb), nthreads)
-    return dict(H=H, b=b, loglik=ll, n_in=n_in, amb=amb)
+                        _p(H), _p(b), _p(ll), _p(n_in), _p(amb), _p(absum), nthreads)
+    return dict(H=H, b=b, loglik=ll, n_in=n_in, amb=amb, absum=absum)
 
 
 def likelihood_pairs(m: OracleMap, pose, scan, scan_n, scan_valid, params: Params):
@@ -298,14 +300,18 @@ def bucket_sort(buckets):
     return dict(sorted_ids=sid, rank=rank, seg_lo=lo, seg_hi=hi)
 
 
-def neighbor_merge(poses, old_ids, sorting, params: Params, tie_tol=3e-5, nthreads=0):
+def neighbor_merge(poses, old_ids, sorting, params: Params, tie_tol=3e-5, nthreads=0, subset=None):
+    """New lists of all particles, or of `subset` (rows follow subset)."""
     poses = _c(poses, np.float32).reshape(-1, 7)
     npart, K = len(poses), params.K
-    ids = np.zeros((npart, K), np.int32); kk = np.zeros((npart, K)); dd = np.zeros((npart, K, 6))
-    flags = np.zeros(npart, np.int32)
+    sub = None if subset is None else _c(subset, np.int32)
+    nout = npart if sub is None else len(sub)
+    ids = np.zeros((nout, K), np.int32); kk = np.zeros((nout, K)); dd = np.zeros((nout, K, 6))
+    flags = np.zeros(nout, np.int32)
     lib().or_neighbor_merge(_p(poses), npart, _p(None if old_ids is None else _c(old_ids, np.int32)), K, params.C,
-                            _p(sorting["sorted_ids"]), _p(sorting["rank"]), _p(sorting["seg_lo"]),
-                            _p(sorting["seg_hi"]), params.sigma_r, params.sigma_t, tie_tol,
+                            _p(_c(sorting["sorted_ids"], np.int32)), _p(_c(sorting["rank"], np.int32)),
+                            _p(_c(sorting["seg_lo"], np.int32)), _p(_c(sorting["seg_hi"], np.int32)),
+                            params.sigma_r, params.sigma_t, tie_tol, _p(sub), 0 if sub is None else len(sub),
                             _p(ids), _p(kk), _p(dd), _p(flags), nthreads)
     return dict(ids=ids, k=kk, d=dd, flags=flags)
 
@@ -395,8 +401,12 @@ class OracleFilter:
         if odom_cov is None:
             odom_cov = np.zeros((6, 6))
         s = self.step_index
-        # prediction (Sec. III-B, Eq. 1)
-        pred, delta = predict(self.poses, odom_T, odom_cov, P.seed, s, want_delta=True)
+        # prediction (Sec. III-B, Eq. 1); with no motion and no noise it is the
+        # identity and the stored FP32 poses are kept as they are
+        if np.array_equal(np.asarray(odom_T, np.float64), np.eye(4)) and not np.any(odom_cov):
+            pred = self.poses.astype(np.float64)
+        else:
+            pred, _ = predict(self.poses, odom_T, odom_cov, P.seed, s)
         poses = pred.astype(np.float32)
         out["pred_poses"] = pred
         out["poses_in"] = poses

@@ -455,7 +455,7 @@ int mp_launch_scan_prepare(mp_ctx* c) {
         MP_CUDA(c, cudaMemsetAsync(c->scan_nvalid, 0, sizeof(int32_t), c->stream));
         return MP_OK;
     }
-    float4* tmp = (float4*)c->gn;   // gn is free during this stage and holds >= 4 * max_scan floats
+    float4* tmp = c->scan_tmp4;
     k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(c->scan_raw, n, tmp);
     MP_LAUNCHED(c);
     float r2 = c->p.r_cov * c->p.r_cov;

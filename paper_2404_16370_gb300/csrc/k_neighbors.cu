@@ -1,0 +1,462 @@
+// Neighbour list update (Sec. III-C, "LSH-based iterative neighbor particle
+// search"; Eq. 9, 10; Algorithm 1):
+//  * k_lsh_keys   zeta = alpha W^K log(T_LSH^-1 T_i) + delta (FP64), key =
+//                 XOR_a floor(zeta_a) * P_a (mod 2^32), bucket = key mod N^B.
+//  * radix sort   stable LSD sort of (bucket, id): the distribute loop.
+//  * k_merge      one warp per particle: candidates = previous list + a window
+//                 of its bucket, d_ij = log(T_i^-1 T_j), s_ij = sum W d^2
+//                 (Eq. 7, 8 as printed), keep self + the K-1 smallest (s, j):
+//                 the gather loop with the iterative refinement of the lists.
+// Also the generic exclusive scan used by the sort and the cell grids.
+#include "mp_internal.cuh"
+
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// exclusive scan (uint32), 4096 elements per block
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_scan_block(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                     int64_t n, uint32_t* __restrict__ block_sums) {
+    __shared__ uint32_t warp_tot[32];
+    int64_t base = (int64_t)blockIdx.x * 4096 + 4 * threadIdx.x;
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
+    uint32_t s0 = v[0], s1 = s0 + v[1], s2 = s1 + v[2], tot = s2 + v[3];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        warp_tot[lane] = x;   // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t excl = inc - tot + (w > 0 ? warp_tot[w - 1] : 0u);
+    uint32_t r[4] = {excl, excl + s0, excl + s1, excl + s2};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < n) out[base + k] = r[k];
+    if (threadIdx.x == 1023 && block_sums) block_sums[blockIdx.x] = warp_tot[31];
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, int64_t n, const uint32_t* __restrict__ offs) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] += offs[i / 4096];
+}
+
+int scan_rec(mp_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp) {
+    int64_t nb = (n + 4095) / 4096;
+    k_scan_block<<<(unsigned)nb, 1024, 0, c->stream>>>(in, out, n, tmp);
+    MP_LAUNCHED(c);
+    if (nb > 1) {
+        int rc = scan_rec(c, tmp, tmp, nb, tmp + nb);
+        if (rc) return rc;
+        k_scan_add<<<grid_for(n, 256), 256, 0, c->stream>>>(out, n, tmp);
+        MP_LAUNCHED(c);
+    }
+    return MP_OK;
+}
+
+size_t scan_tmp_need(int64_t n) {
+    size_t need = 0;
+    while (n > 1) {
+        n = (n + 4095) / 4096;
+        need += (size_t)n;
+    }
+    return need + 1;
+}
+
+// ---------------------------------------------------------------------------
+// LSH keys (FP64)
+// ---------------------------------------------------------------------------
+struct LshArgs {
+    double q[4];       // T_LSH^-1 rotation
+    double t[3];       // T_LSH^-1 translation
+    double delta[6];
+    double scale[6];   // alpha * W^K diagonal
+    uint32_t mask;
+};
+
+__device__ __forceinline__ void log_se3_d(double qx, double qy, double qz, double qw, const double t[3], double xi[6]) {
+    if (qw < 0) { qx = -qx; qy = -qy; qz = -qz; qw = -qw; }
+    double s2 = qx * qx + qy * qy + qz * qz;
+    double f;
+    if (s2 < 1e-20) f = 2.0 / qw * (1.0 - s2 / (3.0 * qw * qw));
+    else {
+        double s = sqrt(s2);
+        f = 2.0 * atan2(s, qw) / s;
+    }
+    xi[0] = f * qx; xi[1] = f * qy; xi[2] = f * qz;
+    double th2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    double C;
+    if (th2 < 1e-4) C = 1.0 / 12.0 + th2 * (1.0 / 720.0 + th2 * (1.0 / 30240.0));
+    else {
+        double th = sqrt(th2), sh, ch;
+        sincos(0.5 * th, &sh, &ch);
+        C = (1.0 - 0.5 * th * ch / sh) / th2;
+    }
+    double wt[3] = {xi[1] * t[2] - xi[2] * t[1], xi[2] * t[0] - xi[0] * t[2], xi[0] * t[1] - xi[1] * t[0]};
+    double wwt[3] = {xi[1] * wt[2] - xi[2] * wt[1], xi[2] * wt[0] - xi[0] * wt[2], xi[0] * wt[1] - xi[1] * wt[0]};
+    for (int a = 0; a < 3; ++a) xi[3 + a] = t[a] - 0.5 * wt[a] + C * wwt[a];
+}
+
+__global__ void k_lsh_keys(const float4* __restrict__ poses, int64_t n, LshArgs A, uint32_t* __restrict__ keys,
+                           uint32_t* __restrict__ buckets) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 a = poses[2 * i], b = poses[2 * i + 1];
+    double qx = a.x, qy = a.y, qz = a.z, qw = a.w;
+    double nrm = rsqrt(qx * qx + qy * qy + qz * qz + qw * qw);
+    qx *= nrm; qy *= nrm; qz *= nrm; qw *= nrm;
+    // relative pose T_LSH^-1 T_i = (Lq (x) q_i, R(Lq) t_i + Lt)
+    const double lx = A.q[0], ly = A.q[1], lz = A.q[2], lw = A.q[3];
+    double rw = lw * qw - lx * qx - ly * qy - lz * qz;
+    double rx = lw * qx + lx * qw + ly * qz - lz * qy;
+    double ry = lw * qy - lx * qz + ly * qw + lz * qx;
+    double rz = lw * qz + lx * qy - ly * qx + lz * qw;
+    double ti[3] = {b.x, b.y, b.z};
+    double R[9];
+    R[0] = 1 - 2 * (ly * ly + lz * lz); R[1] = 2 * (lx * ly - lw * lz); R[2] = 2 * (lx * lz + lw * ly);
+    R[3] = 2 * (lx * ly + lw * lz); R[4] = 1 - 2 * (lx * lx + lz * lz); R[5] = 2 * (ly * lz - lw * lx);
+    R[6] = 2 * (lx * lz - lw * ly); R[7] = 2 * (ly * lz + lw * lx); R[8] = 1 - 2 * (lx * lx + ly * ly);
+    double t[3];
+    for (int r = 0; r < 3; ++r) t[r] = R[3 * r] * ti[0] + R[3 * r + 1] * ti[1] + R[3 * r + 2] * ti[2] + A.t[r];
+    double xi[6];
+    log_se3_d(rx, ry, rz, rw, t, xi);
+    const uint32_t P[6] = {73856093u, 19349663u, 83492791u, 2654435761u, 805459861u, 3674653429u};
+    uint32_t key = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double z = A.scale[k] * xi[k] + A.delta[k];
+        int cell = (int)floor(z);
+        key ^= (uint32_t)cell * P[k];
+    }
+    keys[i] = key;
+    buckets[i] = key & A.mask;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (bucket, id), 8-bit digits, 2048 elements per block
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                    uint32_t* __restrict__ counts, int nblocks) {
+    __shared__ uint32_t h[MP_RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * MP_SORT_TILE;
+#pragma unroll
+    for (int it = 0; it < MP_SORT_TILE / 256; ++it) {
+        int64_t idx = base + it * 256 + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (MP_RADIX - 1)], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ iin,
+                                                       int64_t n, int shift, const uint32_t* __restrict__ offs,
+                                                       int nblocks, uint32_t* __restrict__ kout,
+                                                       int32_t* __restrict__ iout) {
+    constexpr int ITEMS = MP_SORT_TILE / 256;   // per lane, consecutive 32-element rows
+    __shared__ uint32_t wcnt[8][MP_RADIX];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < 8 * MP_RADIX; d += 256) (&wcnt[0][0])[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * MP_SORT_TILE + (int64_t)w * (32 * ITEMS);
+    uint32_t key[ITEMS];
+    int32_t id[ITEMS];
+    uint32_t loc[ITEMS];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        int64_t idx = base + it * 32 + lane;
+        bool ok = idx < n;
+        key[it] = ok ? kin[idx] : 0u;
+        id[it] = ok ? iin[idx] : 0;
+        uint32_t dg = ok ? ((key[it] >> shift) & (MP_RADIX - 1)) : MP_RADIX;
+        unsigned peers = __match_any_sync(0xffffffffu, dg);
+        uint32_t before = ok ? wcnt[w][dg] : 0u;
+        __syncwarp();
+        int leader = __ffs(peers) - 1;
+        if (ok && lane == leader) wcnt[w][dg] = before + __popc(peers);
+        __syncwarp();
+        loc[it] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {   // exclusive prefix over warps, per digit
+        uint32_t run = 0;
+        for (int k = 0; k < 8; ++k) {
+            uint32_t t = wcnt[k][threadIdx.x];
+            wcnt[k][threadIdx.x] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        int64_t idx = base + it * 32 + lane;
+        if (idx < n) {
+            uint32_t dg = (key[it] >> shift) & (MP_RADIX - 1);
+            int64_t pos = (int64_t)offs[(int64_t)dg * nblocks + blockIdx.x] + wcnt[w][dg] + loc[it];
+            kout[pos] = key[it];
+            iout[pos] = id[it];
+        }
+    }
+}
+
+__global__ void k_iota(int32_t* __restrict__ a, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (int32_t)i;
+}
+
+// rank of every particle; [lo, hi) of every present bucket
+__global__ void k_segments(const uint32_t* __restrict__ sk, const int32_t* __restrict__ sid, int64_t n,
+                           int32_t* __restrict__ rank, int32_t* __restrict__ blo, int32_t* __restrict__ bhi) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t b = sk[p];
+    rank[sid[p]] = (int32_t)p;
+    if (p == 0 || sk[p - 1] != b) blo[b] = (int32_t)p;
+    if (p == n - 1 || sk[p + 1] != b) bhi[b] = (int32_t)(p + 1);
+}
+
+// ---------------------------------------------------------------------------
+// neighbour merge: one warp per particle, 64 candidate slots (2 per lane)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cand_eval(const float4* __restrict__ poses, int j, const Quat& qic, const float Rit[9],
+                                          const float ti[3], const float W[2], float d[6], float& s) {
+    float4 a = poses[2 * (int64_t)j], b = poses[2 * (int64_t)j + 1];
+    Quat qr = qmul(qic, Quat{a.x, a.y, a.z, a.w});
+    float dt[3] = {b.x - ti[0], b.y - ti[1], b.z - ti[2]};
+    float tr[3];
+    rot_apply(Rit, dt, tr);
+    se3_log_f(qr, tr, d);
+    s = W[0] * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) + W[1] * (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+}
+
+__device__ __forceinline__ void cswap(uint64_t& x, uint64_t y, bool keep_min) {
+    x = keep_min ? (x < y ? x : y) : (x > y ? x : y);
+}
+
+__global__ void __launch_bounds__(256) k_merge(const float4* __restrict__ poses, int64_t n, int K, int C,
+                                               const int32_t* __restrict__ old_ids, const uint32_t* __restrict__ buckets,
+                                               const int32_t* __restrict__ sorted_ids, const int32_t* __restrict__ rank,
+                                               const int32_t* __restrict__ blo, const int32_t* __restrict__ bhi,
+                                               float wr, float wt, int32_t* __restrict__ ids, float* __restrict__ kk,
+                                               float* __restrict__ dd) {
+    int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    Quat qi;
+    float ti[3];
+    load_pose(poses, i, qi, ti);
+    float Ri[9], Rit[9];
+    quat_rot(qi, Ri);
+    Rit[0] = Ri[0]; Rit[1] = Ri[3]; Rit[2] = Ri[6];
+    Rit[3] = Ri[1]; Rit[4] = Ri[4]; Rit[5] = Ri[7];
+    Rit[6] = Ri[2]; Rit[7] = Ri[5]; Rit[8] = Ri[8];
+    Quat qic{-qi.x, -qi.y, -qi.z, qi.w};
+    const float W[2] = {wr, wt};
+    // element lane: previous list slot `lane`; element 32 + lane: window member
+    int ja = -1, jb = -1;
+    if (lane < K) {
+        int j = old_ids[i * K + lane];
+        if (j >= 0 && j != i) ja = j;
+    }
+    {
+        uint32_t b = buckets[i];
+        int lo = blo[b], hi = bhi[b], r = rank[i];
+        int s0 = r - C / 2;
+        int smax = max(lo, hi - C);
+        s0 = min(s0, smax);
+        s0 = max(s0, lo);
+        int e = min(s0 + C, hi);
+        if (lane < e - s0) {
+            int j = sorted_ids[s0 + lane];
+            if (j != i) jb = j;
+        }
+    }
+    float da[6], db[6], sa = 0.f, sb = 0.f;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) { da[a] = 0.f; db[a] = 0.f; }
+    if (ja >= 0) cand_eval(poses, ja, qic, Rit, ti, W, da, sa);
+    if (jb >= 0) cand_eval(poses, jb, qic, Rit, ti, W, db, sb);
+    uint64_t xa = ja >= 0 ? ((uint64_t)__float_as_uint(sa) << 32) | ((uint64_t)ja << 6) | (uint64_t)lane : ~0ull;
+    uint64_t xb = jb >= 0 ? ((uint64_t)__float_as_uint(sb) << 32) | ((uint64_t)jb << 6) | (uint64_t)(32 + lane) : ~0ull;
+    // bitonic sort of 64 keys: element e = lane (xa) and e = 32 + lane (xb)
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {
+                // partner of e = lane is e + 32 in the same lane; k = 64: ascending
+                uint64_t lo = xa < xb ? xa : xb, hi = xa < xb ? xb : xa;
+                xa = lo;
+                xb = hi;
+            } else {
+                uint64_t pa = __shfl_xor_sync(0xffffffffu, xa, j);
+                uint64_t pb = __shfl_xor_sync(0xffffffffu, xb, j);
+                bool lower = (lane & j) == 0;
+                bool up_a = (lane & k) == 0;            // e = lane
+                bool up_b = ((32 + lane) & k) == 0;     // e = 32 + lane
+                cswap(xa, pa, lower == up_a);
+                cswap(xb, pb, lower == up_b);
+            }
+        }
+    }
+    // drop duplicates (same s and j are adjacent), keep the first K-1 unique
+    uint64_t prev_a = __shfl_up_sync(0xffffffffu, xa, 1);
+    uint64_t last_a = __shfl_sync(0xffffffffu, xa, 31);
+    uint64_t prev_b = __shfl_up_sync(0xffffffffu, xb, 1);
+    if (lane == 0) prev_b = last_a;
+    bool va = xa != ~0ull && (lane == 0 || (prev_a >> 6) != (xa >> 6));
+    bool vb = xb != ~0ull && ((prev_b >> 6) != (xb >> 6));
+    unsigned bal_a = __ballot_sync(0xffffffffu, va), bal_b = __ballot_sync(0xffffffffu, vb);
+    const unsigned lt = (1u << lane) - 1u;
+    int qa = __popc(bal_a & lt);
+    int qb = __popc(bal_a) + __popc(bal_b & lt);
+    int nuniq = __popc(bal_a) + __popc(bal_b);
+    // fetch d of each element from the lane that evaluated it
+    int src_a = (int)(xa & 63u), src_b = (int)(xb & 63u);
+    float oa[6], ob[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float v0 = __shfl_sync(0xffffffffu, da[c], src_a & 31);
+        float v1 = __shfl_sync(0xffffffffu, db[c], src_a & 31);
+        oa[c] = (src_a >= 32) ? v1 : v0;
+        float w0 = __shfl_sync(0xffffffffu, da[c], src_b & 31);
+        float w1 = __shfl_sync(0xffffffffu, db[c], src_b & 31);
+        ob[c] = (src_b >= 32) ? w1 : w0;
+    }
+    int64_t row = i * K;
+    if (lane == 0) {
+        ids[row] = (int32_t)i;
+        kk[row] = 1.f;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dd[row * 6 + c] = 0.f;
+    }
+    if (va && qa < K - 1) {
+        int64_t o = row + 1 + qa;
+        ids[o] = (int32_t)((xa >> 6) & 0x3FFFFFFu);
+        kk[o] = expf(-__uint_as_float((uint32_t)(xa >> 32)));
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dd[o * 6 + c] = oa[c];
+    }
+    if (vb && qb < K - 1) {
+        int64_t o = row + 1 + qb;
+        ids[o] = (int32_t)((xb >> 6) & 0x3FFFFFFu);
+        kk[o] = expf(-__uint_as_float((uint32_t)(xb >> 32)));
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dd[o * 6 + c] = ob[c];
+    }
+    // padding slots
+    int slot = lane + 1;
+    if (slot < K && slot - 1 >= nuniq) {
+        ids[row + slot] = -1;
+        kk[row + slot] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dd[(row + slot) * 6 + c] = 0.f;
+    }
+}
+
+}  // namespace
+
+int mp_launch_exclusive_scan(mp_ctx* c, const uint32_t* in, uint32_t* out, int64_t n) {
+    // c->scan_tmp holds the block sums of the scans of the step; larger
+    // (initialisation-time) scans get a temporary buffer of their own.
+    size_t need = scan_tmp_need(n);
+    uint32_t* tmp = c->scan_tmp;
+    uint32_t* own = nullptr;
+    if (need > c->scan_tmp_cap) {
+        MP_CUDA(c, cudaMalloc(&own, need * sizeof(uint32_t)));
+        tmp = own;
+    }
+    int rc = scan_rec(c, in, out, n, tmp);
+    if (own) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(own);
+    }
+    return rc;
+}
+
+int mp_launch_lsh_keys(mp_ctx* c) {
+    LshArgs A;
+    // inverse of T_LSH: (conj(q), -R^T t)
+    double qx = c->lsh_q[0], qy = c->lsh_q[1], qz = c->lsh_q[2], qw = c->lsh_q[3];
+    A.q[0] = -qx; A.q[1] = -qy; A.q[2] = -qz; A.q[3] = qw;
+    double R[9];
+    R[0] = 1 - 2 * (qy * qy + qz * qz); R[1] = 2 * (qx * qy - qw * qz); R[2] = 2 * (qx * qz + qw * qy);
+    R[3] = 2 * (qx * qy + qw * qz); R[4] = 1 - 2 * (qx * qx + qz * qz); R[5] = 2 * (qy * qz - qw * qx);
+    R[6] = 2 * (qx * qz - qw * qy); R[7] = 2 * (qy * qz + qw * qx); R[8] = 1 - 2 * (qx * qx + qy * qy);
+    for (int r = 0; r < 3; ++r)
+        A.t[r] = -(R[r] * c->lsh_t[0] + R[3 + r] * c->lsh_t[1] + R[6 + r] * c->lsh_t[2]);
+    for (int k = 0; k < 6; ++k) {
+        A.delta[k] = c->lsh_delta[k];
+        A.scale[k] = (double)c->p.alpha * (double)(k < 3 ? c->p.sigma_r : c->p.sigma_t);
+    }
+    A.mask = c->p.n_buckets_log2 >= 32 ? 0xffffffffu : ((1u << c->p.n_buckets_log2) - 1u);
+    k_lsh_keys<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->poses[c->cur], c->n, A, c->keys, c->buckets);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_sort(mp_ctx* c) {
+    int64_t n = c->n;
+    int nblocks = (int)((n + MP_SORT_TILE - 1) / MP_SORT_TILE);
+    k_iota<<<grid_for(n, 256), 256, 0, c->stream>>>(c->sort_ids[0], n);
+    MP_LAUNCHED(c);
+    MP_CUDA(c, cudaMemcpyAsync(c->sort_keys[0], c->buckets, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
+                               c->stream));
+    int passes = (c->p.n_buckets_log2 + MP_RADIX_BITS - 1) / MP_RADIX_BITS;
+    int src = 0;
+    for (int pss = 0; pss < passes; ++pss) {
+        int shift = pss * MP_RADIX_BITS;
+        k_radix_hist<<<nblocks, 256, 0, c->stream>>>(c->sort_keys[src], n, shift, c->radix_counts, nblocks);
+        MP_LAUNCHED(c);
+        int rc = mp_launch_exclusive_scan(c, c->radix_counts, c->radix_counts, (int64_t)MP_RADIX * nblocks);
+        if (rc) return rc;
+        k_radix_scatter<<<nblocks, 256, 0, c->stream>>>(c->sort_keys[src], c->sort_ids[src], n, shift, c->radix_counts,
+                                                        nblocks, c->sort_keys[1 - src], c->sort_ids[1 - src]);
+        MP_LAUNCHED(c);
+        src = 1 - src;
+    }
+    MP_CUDA(c, cudaMemcpyAsync(c->sorted_ids, c->sort_ids[src], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
+                               c->stream));
+    if (src != 0) {
+        MP_CUDA(c, cudaMemcpyAsync(c->sort_keys[0], c->sort_keys[1], sizeof(uint32_t) * (size_t)n,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // sort_keys[0] now holds the sorted buckets; seg[0..2^nb) / seg[2^nb..) hold bucket lo / hi
+    int32_t* blo = c->seg;
+    int32_t* bhi = c->seg + ((int64_t)1 << c->p.n_buckets_log2);
+    k_segments<<<grid_for(n, 256), 256, 0, c->stream>>>(c->sort_keys[0], c->sorted_ids, n, c->rank, blo, bhi);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_merge(mp_ctx* c) {
+    int64_t n = c->n;
+    int32_t* blo = c->seg;
+    int32_t* bhi = c->seg + ((int64_t)1 << c->p.n_buckets_log2);
+    int nxt = 1 - c->nbr_cur;
+    int64_t threads = n * 32;
+    k_merge<<<grid_for(threads, 256), 256, 0, c->stream>>>(c->poses[c->cur], n, c->p.K, c->p.C, c->nbr_ids[c->nbr_cur],
+                                                           c->buckets, c->sorted_ids, c->rank, blo, bhi, c->p.sigma_r,
+                                                           c->p.sigma_t, c->nbr_ids[nxt], c->nbr_k, c->nbr_d);
+    MP_LAUNCHED(c);
+    c->nbr_cur = nxt;
+    return MP_OK;
+}

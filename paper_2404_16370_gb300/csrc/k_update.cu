@@ -1,0 +1,316 @@
+// Particle-state kernels:
+//  * k_predict  Sec. III-B, Eq. 1: T_i <- T_i dT exp(L n_i), n_i ~ N(0, I) by
+//               Box-Muller on Philox(seed; i, {0,1}, step, PREDICT).
+//  * k_solve    Sec. III-C: psi_i = -(H + lambda diag H + eps I)^-1 b, FP64
+//               LDL^T (psi = 0 below 6 inliers or on a non-positive pivot).
+//  * k_svgd     Sec. III-C, Eq. 5-6: phi_i = sum_j (k_ij psi_j - 2 k_ij W d_ij) /
+//               sum_j k_ij over the list of i; T_i <- T_i exp(phi_i). A group
+//               of lanes per particle (one per list slot), shuffle reductions.
+//  * k_init     uniform particle draws (Sec. IV-A).
+//  * pose (un)packing between the ABI layout (7 floats) and 2 x float4.
+#include "mp_internal.cuh"
+
+namespace {
+
+struct PredArgs {
+    float4* poses;
+    int64_t n;
+    float dq[4], dt[3];
+    float L[21];
+    int noise;
+    uint2 key;
+    uint32_t step;
+};
+
+__global__ void k_predict(const PredArgs A) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    Quat q;
+    float t[3];
+    load_pose(A.poses, i, q, t);
+    // T dT
+    float R[9], r[3];
+    quat_rot(q, R);
+    rot_apply(R, A.dt, r);
+    t[0] += r[0]; t[1] += r[1]; t[2] += r[2];
+    q = qmul(q, Quat{A.dq[0], A.dq[1], A.dq[2], A.dq[3]});
+    if (A.noise) {
+        uint4 o0 = philox4x32_10(make_uint4((uint32_t)i, 0u, A.step, MP_STREAM_PREDICT), A.key);
+        uint4 o1 = philox4x32_10(make_uint4((uint32_t)i, 1u, A.step, MP_STREAM_PREDICT), A.key);
+        uint32_t u[6] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y};
+        float z[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float rad = sqrtf(-2.f * logf(u32_to_open01(u[2 * k])));
+            float s, cs;
+            sincospif(2.f * u32_to_open01(u[2 * k + 1]), &s, &cs);
+            z[2 * k] = rad * cs;
+            z[2 * k + 1] = rad * s;
+        }
+        float xi[6];
+        int o = 0;
+#pragma unroll
+        for (int rr = 0; rr < 6; ++rr) {
+            float s = 0.f;
+#pragma unroll
+            for (int cc = 0; cc <= rr; ++cc) s += A.L[o++] * z[cc];
+            xi[rr] = s;
+        }
+        pose_retract(q, t, xi);
+    } else {
+        q = qnormalize(q);
+    }
+    store_pose(A.poses, i, q, t);
+}
+
+__global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int32_t* __restrict__ order, int64_t n,
+                        double lambda, double eps, float* __restrict__ psi, float* __restrict__ loglik,
+                        int32_t* __restrict__ n_in) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t i = order[p];
+    double A[6][6];
+    int o = 0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c) {
+            double v = gn[(int64_t)o++ * stride + p];
+            A[r][c] = v;
+            A[c][r] = v;
+        }
+    double b[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) b[r] = gn[(int64_t)(21 + r) * stride + p];
+    float ll = gn[27 * stride + p];
+    int cnt = (int)gn[28 * stride + p];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) A[r][r] += lambda * A[r][r] + eps;
+    // LDL^T in place: strictly lower part holds L, diagonal holds D
+    bool good = cnt >= 6;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        double d = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k] * A[k][k];
+        good = good && (d > 0.0);
+        A[j][j] = d;
+        double inv = good ? 1.0 / d : 0.0;
+#pragma unroll
+        for (int r = j + 1; r < 6; ++r) {
+            double s = A[r][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= A[r][k] * A[j][k] * A[k][k];
+            A[r][j] = s * inv;
+        }
+    }
+    double x[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        double s = -b[r];
+#pragma unroll
+        for (int k = 0; k < r; ++k) s -= A[r][k] * x[k];
+        x[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) x[r] = good ? x[r] / A[r][r] : 0.0;
+#pragma unroll
+    for (int r = 5; r >= 0; --r) {
+        double s = x[r];
+#pragma unroll
+        for (int k = r + 1; k < 6; ++k) s -= A[k][r] * x[k];
+        x[r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) psi[i * 8 + r] = good ? (float)x[r] : 0.f;
+    loglik[i] = ll;
+    n_in[i] = cnt;
+}
+
+// G lanes per particle (G = power of two >= K, <= 32)
+template <int G>
+__global__ void __launch_bounds__(256) k_svgd(float4* __restrict__ poses, int64_t n, int K,
+                                              const int32_t* __restrict__ ids, const float* __restrict__ kk,
+                                              const float* __restrict__ dd, const float* __restrict__ psi, float wr,
+                                              float wt, float* __restrict__ phi_out) {
+    int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t i = gt / G;
+    int l = (int)(gt % G);
+    bool active = i < n;
+    float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (active && l < K) {
+        int64_t o = i * K + l;
+        int j = ids[o];
+        if (j >= 0) {
+            float k = kk[o];
+            const float* dj = dd + o * 6;
+            const float4 p0 = *reinterpret_cast<const float4*>(psi + (int64_t)j * 8);
+            const float2 p1 = *reinterpret_cast<const float2*>(psi + (int64_t)j * 8 + 4);
+            const float ps[6] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y};
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                float w = a < 3 ? wr : wt;
+                acc[a] = k * ps[a] - 2.f * k * w * dj[a];
+            }
+            acc[6] = k;
+        }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 7; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], off, G);
+    if (!active || l != 0) return;
+    float xi[6];
+    float inv = acc[6] > 0.f ? 1.f / acc[6] : 0.f;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) xi[a] = acc[a] * inv;
+    Quat q;
+    float t[3];
+    load_pose(poses, i, q, t);
+    pose_retract(q, t, xi);
+    store_pose(poses, i, q, t);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) phi_out[i * 8 + a] = xi[a];
+}
+
+struct InitArgs {
+    float4* poses;
+    int64_t n;
+    float lo[6], hi[6];
+    int full;
+    uint2 key;
+};
+
+__global__ void k_init_uniform(const InitArgs A) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    uint4 o0 = philox4x32_10(make_uint4((uint32_t)i, 0u, 0u, MP_STREAM_INIT), A.key);
+    uint4 o1 = philox4x32_10(make_uint4((uint32_t)i, 1u, 0u, MP_STREAM_INIT), A.key);
+    float u[6] = {u32_to_open01(o0.x), u32_to_open01(o0.y), u32_to_open01(o0.z), u32_to_open01(o0.w),
+                  u32_to_open01(o1.x), u32_to_open01(o1.y)};
+    float v[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) v[a] = fmaf(u[a], A.hi[a] - A.lo[a], A.lo[a]);
+    Quat q;
+    if (A.full) {
+        float a = sqrtf(1.f - u[3]), b = sqrtf(u[3]);
+        float s1, c1, s2, c2;
+        sincospif(2.f * u[4], &s1, &c1);
+        sincospif(2.f * u[5], &s2, &c2);
+        q = Quat{a * s1, a * c1, b * s2, b * c2};
+    } else {
+        float sr, cr, sp, cp, sy, cy;
+        sincosf(0.5f * v[3], &sr, &cr);
+        sincosf(0.5f * v[4], &sp, &cp);
+        sincosf(0.5f * v[5], &sy, &cy);
+        q = qmul(Quat{0.f, 0.f, sy, cy}, qmul(Quat{0.f, sp, 0.f, cp}, Quat{sr, 0.f, 0.f, cr}));
+    }
+    q = qnormalize(q);
+    float t[3] = {v[0], v[1], v[2]};
+    store_pose(A.poses, i, q, t);
+}
+
+__global__ void k_pack(const float* __restrict__ src, int64_t n, float4* __restrict__ dst) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // stored exactly as given: the voxel decisions use these FP32 values
+    const float* s = src + 7 * i;
+    dst[2 * i] = make_float4(s[0], s[1], s[2], s[3]);
+    dst[2 * i + 1] = make_float4(s[4], s[5], s[6], 0.f);
+}
+
+__global__ void k_unpack(const float4* __restrict__ src, int64_t n, float* __restrict__ dst) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 a = src[2 * i], b = src[2 * i + 1];
+    float* d = dst + 7 * i;
+    d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w; d[4] = b.x; d[5] = b.y; d[6] = b.z;
+}
+
+__global__ void k_gather_gn(const float* __restrict__ gn, int64_t stride, const int32_t* __restrict__ order, int64_t n,
+                            float* __restrict__ dst) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t i = order[p];
+    for (int f = 0; f < MP_GN; ++f) dst[i * MP_GN + f] = gn[(int64_t)f * stride + p];
+}
+
+}  // namespace
+
+int mp_launch_predict(mp_ctx* c) {
+    PredArgs A;
+    A.poses = c->poses[c->cur];
+    A.n = c->n;
+    for (int k = 0; k < 4; ++k) A.dq[k] = c->odom_q[k];
+    for (int k = 0; k < 3; ++k) A.dt[k] = c->odom_t[k];
+    for (int k = 0; k < 21; ++k) A.L[k] = c->chol[k];
+    A.noise = c->noise;
+    A.key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
+    A.step = (uint32_t)c->step;
+    k_predict<<<grid_for(c->n, 256), 256, 0, c->stream>>>(A);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_solve(mp_ctx* c) {
+    k_solve<<<grid_for(c->n, 128), 128, 0, c->stream>>>(c->gn, c->cap, c->sorted_ids, c->n, (double)c->p.lambda,
+                                                        (double)c->p.eps, c->psi, c->loglik, c->n_in);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+template <int G>
+static int launch_svgd_g(mp_ctx* c) {
+    int64_t threads = c->n * G;
+    k_svgd<G><<<grid_for(threads, 256), 256, 0, c->stream>>>(c->poses[c->cur], c->n, c->p.K, c->nbr_ids[c->nbr_cur],
+                                                             c->nbr_k, c->nbr_d, c->psi, c->p.sigma_r, c->p.sigma_t,
+                                                             c->phi);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_svgd(mp_ctx* c) {
+    int K = c->p.K;
+    if (K <= 1) return launch_svgd_g<1>(c);
+    if (K <= 2) return launch_svgd_g<2>(c);
+    if (K <= 4) return launch_svgd_g<4>(c);
+    if (K <= 8) return launch_svgd_g<8>(c);
+    if (K <= 16) return launch_svgd_g<16>(c);
+    return launch_svgd_g<32>(c);
+}
+
+int mp_launch_init_uniform(mp_ctx* c, const float lo[6], const float hi[6]) {
+    InitArgs A;
+    A.poses = c->poses[c->cur];
+    A.n = c->n;
+    const float two_pi = 6.2831853f;
+    A.full = 1;
+    for (int a = 0; a < 6; ++a) {
+        A.lo[a] = lo[a];
+        A.hi[a] = hi[a];
+        if (a >= 3 && (double)hi[a] - (double)lo[a] < 6.283185307179586 - 1e-6) A.full = 0;
+    }
+    (void)two_pi;
+    A.key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
+    k_init_uniform<<<grid_for(c->n, 256), 256, 0, c->stream>>>(A);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_pack_poses(mp_ctx* c, const float* src7_dev, float4* dst) {
+    k_pack<<<grid_for(c->n, 256), 256, 0, c->stream>>>(src7_dev, c->n, dst);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_unpack_poses(mp_ctx* c, const float4* src, float* dst7_dev) {
+    k_unpack<<<grid_for(c->n, 256), 256, 0, c->stream>>>(src, c->n, dst7_dev);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_gather_gn(mp_ctx* c, float* dst_dev) {
+    k_gather_gn<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->gn, c->cap, c->sorted_ids, c->n, dst_dev);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}

@@ -62,6 +62,7 @@ struct mp_ctx {
     int32_t* sort_ids[2];
     uint32_t* radix_counts; // MP_RADIX * n_sort_blocks
     uint32_t* scan_tmp;     // block sums for the scans
+    size_t scan_tmp_cap;
     int32_t* nbr_ids[2];
     int nbr_cur;
     float* nbr_k;
@@ -76,6 +77,7 @@ struct mp_ctx {
     float* scan_normals;    // max_scan x 3
     uint8_t* scan_valid;    // max_scan
     float4* scan_pts;       // 2 per valid point: (mu.xyz, n.x), (n.y, n.z, 0, 0)
+    float4* scan_tmp4;      // max_scan float4 copy of the raw scan
     int32_t* scan_nvalid;   // device scalar
 
     // odometry of the current step (FP32 for the kernels)

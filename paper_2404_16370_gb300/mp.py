@@ -1,0 +1,261 @@
+"""ctypes binding of libmp.so (include/megaparticles.h), one function per C
+entry point with the same name. Argument marshalling only: every step of the
+filter runs in the library's CUDA kernels. Arrays may be numpy arrays (host)
+or torch tensors (host or CUDA; contiguous); outputs default to new numpy
+arrays. Raises MPError on a non-zero return code, and ImportError when the
+library has not been built (there is no CPU fallback)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmp.so")
+
+MP_OK, MP_EINVAL, MP_ENOMEM, MP_ECUDA, MP_ETIMEOUT, MP_ENOTINIT = 0, -1, -2, -3, -4, -5
+MP_PRESET_BOX_ROOM, MP_PRESET_OUTDOOR = 0, 1
+
+MP_STAGE_PREDICT = 0x001
+MP_STAGE_SCAN = 0x002
+MP_STAGE_LSH = 0x004
+MP_STAGE_SORT = 0x008
+MP_STAGE_MERGE = 0x010
+MP_STAGE_LIKELIHOOD = 0x020
+MP_STAGE_SOLVE = 0x040
+MP_STAGE_SVGD = 0x080
+MP_STAGE_POSTERIOR = 0x100
+MP_STAGE_ALL = 0x1FF
+STAGE_NAMES = ["predict", "scan", "lsh", "sort", "merge", "likelihood", "solve", "svgd", "posterior"]
+
+MP_BUF_POSES, MP_BUF_LOG_PRIOR, MP_BUF_KEYS, MP_BUF_BUCKETS, MP_BUF_SORTED_IDS = 1, 2, 3, 4, 5
+MP_BUF_SEGMENTS, MP_BUF_NBR_IDS, MP_BUF_NBR_K, MP_BUF_NBR_D, MP_BUF_GN = 6, 7, 8, 9, 10
+MP_BUF_PSI, MP_BUF_POST, MP_BUF_POST_INIT, MP_BUF_LOGLIK, MP_BUF_SCAN_NORMALS = 11, 12, 13, 14, 15
+MP_BUF_SCAN_VALID, MP_BUF_MAP_NORMALS, MP_BUF_MAP_VALID, MP_BUF_LSH, MP_BUF_PHI = 16, 17, 18, 19, 20
+
+# element type and trailing shape of each buffer
+_BUF = {
+    MP_BUF_POSES: (np.float32, (7,)), MP_BUF_LOG_PRIOR: (np.float64, ()), MP_BUF_KEYS: (np.uint32, ()),
+    MP_BUF_BUCKETS: (np.uint32, ()), MP_BUF_SORTED_IDS: (np.int32, ()), MP_BUF_SEGMENTS: (np.int32, (2,)),
+    MP_BUF_NBR_IDS: (np.int32, ("K",)), MP_BUF_NBR_K: (np.float32, ("K",)), MP_BUF_NBR_D: (np.float32, ("K", 6)),
+    MP_BUF_GN: (np.float32, (29,)), MP_BUF_PSI: (np.float32, (6,)), MP_BUF_POST: (np.float64, ()),
+    MP_BUF_POST_INIT: (np.float64, ()), MP_BUF_LOGLIK: (np.float32, ()), MP_BUF_SCAN_NORMALS: (np.float32, (3,)),
+    MP_BUF_SCAN_VALID: (np.uint8, ()), MP_BUF_MAP_NORMALS: (np.float32, (3,)), MP_BUF_MAP_VALID: (np.uint8, ()),
+    MP_BUF_LSH: (np.float64, ()), MP_BUF_PHI: (np.float32, (6,)),
+}
+
+
+class mp_params(C.Structure):
+    _fields_ = [("nnf_res", C.c_float), ("r_max", C.c_float), ("c_max", C.c_float),
+                ("sigma_r", C.c_float), ("sigma_t", C.c_float), ("alpha", C.c_float), ("lsh_sigma", C.c_float),
+                ("lambda_", C.c_float), ("eps", C.c_float), ("eps_cov", C.c_float), ("r_cov", C.c_float),
+                ("K", C.c_int32), ("C", C.c_int32), ("cov_k", C.c_int32), ("cov_min", C.c_int32),
+                ("post_iters", C.c_int32), ("n_buckets_log2", C.c_int32), ("max_scan", C.c_int32),
+                ("seed", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"megaparticles error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        V, P, I64, I32, U32, U64, D = C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_uint32, C.c_uint64, C.c_double
+        L.mp_default_params.argtypes = [C.POINTER(mp_params), C.c_int, I64]
+        L.mp_init_map.argtypes = [C.POINTER(V), P, I64, C.POINTER(mp_params), V]
+        L.mp_init_particles.argtypes = [V, I64, P, P, P, P]
+        L.mp_step.argtypes = [V, P, I32, P, P]
+        L.mp_get_posterior.argtypes = [V, P, P, P, P]
+        L.mp_destroy.argtypes = [V]
+        L.mp_last_error.argtypes = [V]
+        L.mp_last_error.restype = C.c_char_p
+        L.mp_set_scan.argtypes = [V, P, I32]
+        L.mp_set_odometry.argtypes = [V, P, P]
+        L.mp_run_stages.argtypes = [V, U32]
+        L.mp_set_step_index.argtypes = [V, U64]
+        L.mp_buffer_size.argtypes = [V, C.c_int, C.POINTER(I64)]
+        L.mp_get_buffer.argtypes = [V, C.c_int, P, I64]
+        L.mp_set_buffer.argtypes = [V, C.c_int, P, I64]
+        L.mp_nnf_query.argtypes = [V, P, I64, P]
+        L.mp_map_info.argtypes = [V, P, P, P, P, P]
+        L.mp_set_timing.argtypes = [V, C.c_int]
+        L.mp_stage_times.argtypes = [V, P]
+        L.mp_kernel_launches.argtypes = [V, C.POINTER(I64)]
+        for f in ("mp_default_params", "mp_init_map", "mp_init_particles", "mp_step", "mp_get_posterior", "mp_destroy",
+                  "mp_set_scan", "mp_set_odometry", "mp_run_stages", "mp_set_step_index", "mp_buffer_size",
+                  "mp_get_buffer", "mp_set_buffer", "mp_nnf_query", "mp_map_info", "mp_set_timing",
+                  "mp_stage_times", "mp_kernel_launches"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x, dtype=None):
+    """(pointer, keep-alive) of None, a numpy array or a torch tensor."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr"):               # torch tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(C.c_void_p), a
+
+
+def _check(rc, ctx):
+    if rc != MP_OK:
+        raise MPError(rc, mp_last_error(ctx))
+
+
+def mp_last_error(ctx) -> str:
+    return lib().mp_last_error(ctx).decode(errors="replace")
+
+
+def mp_default_params(preset=MP_PRESET_BOX_ROOM, n_particles=4096, **overrides) -> mp_params:
+    p = mp_params()
+    rc = lib().mp_default_params(C.byref(p), int(preset), int(n_particles))
+    if rc != MP_OK:
+        raise MPError(rc, f"unknown preset {preset}")
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    return p
+
+
+def mp_init_map(xyz, params: mp_params, cuda_stream=None):
+    ctx = C.c_void_p()
+    ptr, keep = _ptr(xyz, np.float32)
+    n = int(xyz.shape[0])
+    rc = lib().mp_init_map(C.byref(ctx), ptr, n, C.byref(params), C.c_void_p(cuda_stream) if cuda_stream else None)
+    if rc != MP_OK:
+        raise MPError(rc, "mp_init_map failed (details on stderr)")
+    return ctx
+
+
+def mp_init_particles(ctx, n_particles, lo=None, hi=None, poses=None, log_prior=None):
+    pl, kl = _ptr(lo, np.float32)
+    ph, kh = _ptr(hi, np.float32)
+    pp, kp = _ptr(poses, np.float32)
+    pr, kr = _ptr(log_prior, np.float64)
+    _check(lib().mp_init_particles(ctx, int(n_particles), pl, ph, pp, pr), ctx)
+
+
+def mp_step(ctx, scan, odom_T=None, odom_cov=None):
+    ps, ks = _ptr(scan, np.float32)
+    pt, kt = _ptr(odom_T, np.float64)
+    pc, kc = _ptr(odom_cov, np.float64)
+    n = 0 if scan is None else int(scan.shape[0])
+    _check(lib().mp_step(ctx, ps, n, pt, pc), ctx)
+
+
+def mp_get_posterior(ctx, poses_out=None, prob_out=None):
+    best = np.zeros(7, np.float32)
+    bp = np.zeros(1, np.float64)
+    po, ko = _ptr(poses_out)
+    pr, kr = _ptr(prob_out)
+    _check(lib().mp_get_posterior(ctx, po, pr, best.ctypes.data_as(C.c_void_p), bp.ctypes.data_as(C.c_void_p)), ctx)
+    return best, float(bp[0])
+
+
+def mp_destroy(ctx):
+    if ctx:
+        lib().mp_destroy(ctx)
+
+
+def mp_set_scan(ctx, scan):
+    ps, ks = _ptr(scan, np.float32)
+    _check(lib().mp_set_scan(ctx, ps, 0 if scan is None else int(scan.shape[0])), ctx)
+
+
+def mp_set_odometry(ctx, odom_T=None, odom_cov=None):
+    pt, kt = _ptr(odom_T, np.float64)
+    pc, kc = _ptr(odom_cov, np.float64)
+    _check(lib().mp_set_odometry(ctx, pt, pc), ctx)
+
+
+def mp_run_stages(ctx, mask):
+    _check(lib().mp_run_stages(ctx, int(mask)), ctx)
+
+
+def mp_set_step_index(ctx, step):
+    _check(lib().mp_set_step_index(ctx, int(step)), ctx)
+
+
+def mp_buffer_size(ctx, which) -> int:
+    n = C.c_int64()
+    _check(lib().mp_buffer_size(ctx, int(which), C.byref(n)), ctx)
+    return int(n.value)
+
+
+def _shape(which, count, K):
+    dt, tail = _BUF[which]
+    tail = tuple(K if t == "K" else t for t in tail)
+    per = int(np.prod(tail)) if tail else 1
+    return dt, (count // per,) + tail
+
+
+def mp_get_buffer(ctx, which, K=None, out=None):
+    count = mp_buffer_size(ctx, which)
+    if out is None:
+        dt, shape = _shape(which, count, K if K is not None else _guess_k(ctx, which, count))
+        out = np.empty(shape, dt)
+    po, ko = _ptr(out)
+    _check(lib().mp_get_buffer(ctx, int(which), po, count), ctx)
+    return out
+
+
+def _guess_k(ctx, which, count):
+    if _BUF[which][1] and _BUF[which][1][0] == "K":
+        n = mp_buffer_size(ctx, MP_BUF_LOG_PRIOR)
+        per = count // max(n, 1)
+        return per // 6 if which == MP_BUF_NBR_D else per
+    return None
+
+
+def mp_set_buffer(ctx, which, src):
+    dt, _ = _BUF[which]
+    ps, ks = _ptr(src, dt)
+    count = int(np.prod(src.shape))
+    _check(lib().mp_set_buffer(ctx, int(which), ps, count), ctx)
+
+
+def mp_nnf_query(ctx, vox):
+    v = np.ascontiguousarray(vox, np.int32).reshape(-1, 3)
+    out = np.empty(len(v), np.int32)
+    _check(lib().mp_nnf_query(ctx, v.ctypes.data_as(C.c_void_p), len(v), out.ctypes.data_as(C.c_void_p)), ctx)
+    return out
+
+
+def mp_map_info(ctx):
+    o = np.zeros(3, np.float32); d = np.zeros(3, np.int32); inv = np.zeros(1, np.float32)
+    off = np.zeros(3, np.float32); nv = np.zeros(1, np.int64)
+    _check(lib().mp_map_info(ctx, *(a.ctypes.data_as(C.c_void_p) for a in (o, d, inv, off, nv))), ctx)
+    return dict(origin=o, dims=d, inv_res=float(inv[0]), off=off, n_valid=int(nv[0]))
+
+
+def mp_set_timing(ctx, enable=True):
+    _check(lib().mp_set_timing(ctx, int(bool(enable))), ctx)
+
+
+def mp_stage_times(ctx):
+    ms = np.zeros(9, np.float32)
+    _check(lib().mp_stage_times(ctx, ms.ctypes.data_as(C.c_void_p)), ctx)
+    return dict(zip(STAGE_NAMES, ms.tolist()))
+
+
+def mp_kernel_launches(ctx) -> int:
+    n = C.c_int64()
+    _check(lib().mp_kernel_launches(ctx, C.byref(n)), ctx)
+    return int(n.value)

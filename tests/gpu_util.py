@@ -1,0 +1,27 @@
+"""Helpers of the GPU parity tests: comparisons against the oracle with the
+tolerances the tests state, and SE(3) distances between pose arrays."""
+import numpy as np
+from scipy.spatial.transform import Rotation
+
+
+def pose_error(a, b):
+    """(rotation angle, translation distance) between (n,7) pose arrays."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    ra = Rotation.from_quat(a[:, :4] / np.linalg.norm(a[:, :4], axis=1, keepdims=True))
+    rb = Rotation.from_quat(b[:, :4] / np.linalg.norm(b[:, :4], axis=1, keepdims=True))
+    ang = (ra.inv() * rb).magnitude()
+    return ang, np.linalg.norm(a[:, 4:] - b[:, 4:], axis=1)
+
+
+def sum_tolerance(ref_abs, rel=1e-4, floor=1e-6):
+    """1e-4 of the sum of term magnitudes (the rounding scale of an FP32 sum)."""
+    return rel * ref_abs + floor
+
+
+def report(name, err, tol):
+    bad = err > tol
+    if bad.any():
+        k = np.argmax(err - tol)
+        return f"{name}: {bad.sum()} entries over tolerance; worst err {err.flat[k]:.3g} tol {tol.flat[k]:.3g}"
+    return ""

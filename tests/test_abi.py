@@ -1,0 +1,62 @@
+"""CPU checks of the boundary: the CUDA library builds for sm_103a, loads, and
+exports every entry point include/megaparticles.h declares; parameter presets
+agree with the oracle's readings. No kernel runs here."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "megaparticles.h")
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mp_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2404_16370_gb300 import build as B
+    return B.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for must in ("mp_init_map", "mp_init_particles", "mp_step", "mp_get_posterior", "mp_destroy", "mp_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(mp_[a-z_0-9]+)$", out, flags=re.M))
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_reports_without_gpu(built):
+    from paper_2404_16370_gb300 import mp
+    L = mp.lib()
+    for n in declared():
+        assert hasattr(L, n)
+    assert mp.mp_last_error(None) == "null context"
+    p = mp.mp_default_params(mp.MP_PRESET_OUTDOOR, 1 << 20)
+    assert p.n_buckets_log2 == 20 and p.K == 32 and abs(p.nnf_res - 0.2) < 1e-7
+    with pytest.raises(mp.MPError):
+        mp.mp_default_params(7, 10)
+
+
+@pytest.mark.parametrize("preset,n", [(0, 4096), (1, 1 << 20), (0, 3), (1, 5000)])
+def test_presets_match_oracle_readings(built, oracle, preset, n):
+    from paper_2404_16370_gb300 import mp
+    g = mp.mp_default_params(preset, n)
+    o = oracle.Params.box_room(n) if preset == 0 else oracle.Params.outdoor(n)
+    pairs = [("nnf_res", "res"), ("r_max", "r_max"), ("c_max", "c_max"), ("sigma_r", "sigma_r"),
+             ("sigma_t", "sigma_t"), ("alpha", "alpha"), ("lsh_sigma", "lsh_sigma"), ("lambda_", "lam"),
+             ("eps", "eps_damp"), ("eps_cov", "eps_cov"), ("r_cov", "r_cov"), ("K", "K"), ("C", "C"),
+             ("cov_k", "cov_k"), ("cov_min", "cov_min"), ("post_iters", "post_iters"),
+             ("n_buckets_log2", "nb_log2"), ("seed", "seed")]
+    for gk, ok in pairs:
+        assert abs(float(getattr(g, gk)) - float(getattr(o, ok))) <= 1e-7 * max(1.0, abs(float(getattr(o, ok)))), gk
