@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Throughput of one MegaParticles filter step on GB300.
+
+A step = prediction (Eq. 1), scan Gaussians, LSH neighbour-list update
+(Eq. 9-10, Algorithm 1), likelihood + Gauss-Newton sums (Eq. 2-4), GN solve,
+SVGD update (Eq. 5-8) and posterior propagation (Eq. 11), all in the CUDA
+library, through its C ABI.
+
+Workload (paper scale, synthetic): 200 x 200 x 20 m outdoor scene with 1M map
+points, 2^20 particles uniform over the free space, 8192-point scans from a
+32-beam 360-degree sensor along a 1 m/step trajectory, K = 32 neighbours.
+Steps 0 .. W+K-1 of the trajectory are run: W untimed, K timed.
+
+Prints one JSON line. --impl reference times the FP64 CPU oracle instead, on
+a bounded sample of the same workload (extrapolated to the full particle
+count). Under torchrun every rank runs an independent replica on its own GPU
+("replicas only": the filter has no data-path exchange on one GPU per
+instance); value = steps of all ranks / max elapsed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SVGD filter steps/s and particle·point evals/s at 2^20 particles; % GB300 roofline"
+N_PARTICLES = 1 << 20
+N_POINTS = 8192
+N_MAP = 1_000_000
+# FP32 operations of one particle x scan-point pair in the likelihood kernel's
+# formulation (fused multiply-add = 2): transform 18, voxel 9, residual 3,
+# normal rotation 15, information matrix (closed form) 27+21, cost 22,
+# g = Omega e 15, [q]x Omega 27, Hessian/gradient accumulation 54, log-lik 1.
+LK_FLOPS_PER_PAIR = 222
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def workload_desc(nvalid=None):
+    d = {"workload": "outdoor 200x200x20 m, 2^20 particles x 8192-point scans, 1M map points, K=32",
+         "particles": N_PARTICLES, "scan_points": N_POINTS, "map_points": N_MAP, "K": 32,
+         "nnf_res_m": 0.2, "l2": "working set larger than L2 (NNF grid ~0.5 GB, neighbour lists ~1.2 GB): no flush"}
+    if nvalid is not None:
+        d["scan_points_valid_mean"] = nvalid
+    return d
+
+
+def make_workload(n_steps, n_particles=N_PARTICLES):
+    from paper_2404_16370_gb300 import synth
+    return synth.outdoor_workload(n_particles=n_particles, n_steps=max(n_steps, 1), n_map=N_MAP, n_points=N_POINTS)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if "Active" in v and "Not" not in v})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def traffic_from_profile():
+    """DRAM bytes per likelihood launch from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "k_likelihood_outdoor.txt")
+    src = os.path.join(ROOT, "paper_2404_16370_gb300", "csrc", "k_likelihood.cu")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_md5") != hashlib.md5(open(src, "rb").read()).hexdigest():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_setup(wl, n_sample):
+    from oracle import oracle as O
+    P = O.Params.outdoor(N_PARTICLES)
+    t = time.perf_counter()
+    om = O.OracleMap(wl.map_points, P)
+    init_s = time.perf_counter() - t
+    f = O.OracleFilter(om, P, wl.particles[:n_sample].copy())
+    return O, f, init_s
+
+
+def oracle_step_time(f, wl, s):
+    t = time.perf_counter()
+    f.step(wl.scans[s], wl.odom[s], wl.odom_cov[s])
+    return time.perf_counter() - t
+
+
+def cpu_baseline(wl, n_sample=4096):
+    O, f, _ = oracle_setup(wl, n_sample)
+    dt = oracle_step_time(f, wl, 0)
+    cores = os.cpu_count()
+    steps_s = 1.0 / (dt * N_PARTICLES / n_sample)
+    return {"value": steps_s, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"one FP64 oracle step on {n_sample} of the 2^20 particles (full 8192-point scan, full 1M-point "
+                      f"map; {dt:.2f} s), extrapolated linearly to 2^20 particles"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return
+    n_sample = args.sample
+    wl = make_workload(args.warmup + args.steps)
+    O, f, init_s = oracle_setup(wl, n_sample)
+    for s in range(args.warmup):
+        oracle_step_time(f, wl, s)
+    times = [oracle_step_time(f, wl, args.warmup + k) for k in range(args.steps)]
+    dt = float(np.mean(times))
+    value = 1.0 / (dt * N_PARTICLES / n_sample)
+    sample = (f"{n_sample} of the 2^20 particles per step (full scan and map), {dt:.2f} s per sampled step, "
+              f"extrapolated linearly to 2^20 particles")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_desc(),
+           "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    from paper_2404_16370_gb300 import mp
+
+    n_steps = args.warmup + args.steps
+    wl = make_workload(n_steps)
+    stream = torch.cuda.Stream()
+    params = mp.mp_default_params(mp.MP_PRESET_OUTDOOR, N_PARTICLES)
+    params.seed = 4 + rank
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = mp.mp_init_map(wl.map_points, params, cuda_stream=stream.cuda_stream)
+    init_map_s = time.perf_counter() - t0
+    scans_dev = [torch.from_numpy(s).to(f"cuda:{local}") for s in wl.scans]
+    scans_pin = [torch.from_numpy(s).pin_memory() for s in wl.scans]
+    torch.cuda.synchronize()
+
+    def run_steps(lo, hi, host=False):
+        for s in range(lo, hi):
+            sc = scans_pin[s] if host else scans_dev[s]
+            mp.mp_step(ctx, sc if len(sc) else None, wl.odom[s], wl.odom_cov[s])
+            if host:
+                mp.mp_get_posterior(ctx)          # D2H of the step's result (best pose, its probability)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([x], device=f"cuda:{local}", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    try:
+        # ---- device-resident inputs: the timed steps W .. W+K-1
+        mp.mp_init_particles(ctx, N_PARTICLES, poses=wl.particles)
+        run_steps(0, args.warmup)
+        torch.cuda.synchronize()
+        mp.mp_set_timing(ctx, True)
+        launches0 = mp.mp_kernel_launches(ctx)
+        gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] \
+            if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+        clocks = ClockSampler(gpu_index)
+        time.sleep(0.25)
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        run_steps(args.warmup, n_steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        launches = mp.mp_kernel_launches(ctx) - launches0
+        stage_ms, stage_runs, pairs = mp.mp_stage_times(ctx)
+        mp.mp_set_timing(ctx, False)
+        best, best_p = mp.mp_get_posterior(ctx)
+        t_max = max_over_ranks(elapsed)
+
+        # ---- end to end through host (pinned) buffers: same steps again
+        mp.mp_init_particles(ctx, N_PARTICLES, poses=wl.particles)
+        run_steps(0, args.warmup, host=True)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        run_steps(args.warmup, n_steps, host=True)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+    finally:
+        mp.mp_destroy(ctx)
+
+    if rank != 0:
+        return
+    steps_total = args.steps * world
+    value = steps_total / t_max
+    pairs_rank = pairs
+    lk_ms = stage_ms["likelihood"]
+    lk_runs = max(stage_runs["likelihood"], 1)
+    lk_flops = LK_FLOPS_PER_PAIR * pairs_rank
+    achieved = lk_flops / (lk_ms / 1e3) / 1e12 if lk_ms > 0 else None
+    traffic = traffic_from_profile()
+    n_timed_scans = [len(wl.scans[s]) for s in range(args.warmup, n_steps)]
+    h2d = int(np.mean([n * 12 for n in n_timed_scans])) + 16 * 8 + 36 * 8
+    d2h = 7 * 4 + 8
+    nvalid_mean = pairs_rank / N_PARTICLES / max(lk_runs, 1)
+    out = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_desc(round(nvalid_mean, 1)),
+        "pair_evals_per_s": pairs_rank * world / t_max,
+        "roofline": {"bound": "alu", "kernel": "k_likelihood", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": (achieved / ALU_PEAK_TFLOPS) if achieved else None,
+                     "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz max SM clock",
+                     "flops_per_pair": LK_FLOPS_PER_PAIR, "pairs_per_launch": pairs_rank / lk_runs,
+                     "avg_launch_ms": lk_ms / lk_runs},
+        "stage_ms_per_step": {k: v / max(stage_runs[k], 1) for k, v in stage_ms.items()},
+        "e2e": {"value": steps_total / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "init_map_s": round(init_map_s, 3),
+        "best_prob_last_step": best_p,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample)
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--sample", type=int, default=1024, help="particles per step in the reference arm's sample")
+    ap.add_argument("--cpu-sample", type=int, default=4096, help="particles in the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -190,11 +190,15 @@ int mp_nnf_query(mp_ctx* ctx, const int32_t* vox, int64_t m, int32_t* out);
  * number of map points with a covariance. */
 int mp_map_info(mp_ctx* ctx, float origin[3], int32_t dims[3], float* inv_res, float off[3], int64_t* n_valid);
 
-/* Per-stage device times (CUDA events on the context stream) of the last
- * mp_step / mp_run_stages, in stage-bit order (9 floats, ms; 0 for stages not
- * run). Timing must be enabled first; enabling adds event records only. */
+/* Per-stage device timing with CUDA events on the context stream.
+ * mp_set_timing(ctx, 1) enables it and resets every total (0 disables);
+ * enabling adds two event records per stage run and no synchronisation.
+ * mp_stage_times returns, in stage-bit order, the summed device time (ms_out,
+ * 9 floats) and the number of runs (runs_out, 9 int64) of each stage since
+ * timing was enabled, and in *pairs (may be NULL) the particle x scan-point
+ * pairs the likelihood stage evaluated in that interval. Synchronises. */
 int mp_set_timing(mp_ctx* ctx, int enable);
-int mp_stage_times(mp_ctx* ctx, float ms_out[9]);
+int mp_stage_times(mp_ctx* ctx, float ms_out[9], int64_t runs_out[9], int64_t* pairs);
 
 /* Number of kernels this context has launched so far. */
 int mp_kernel_launches(mp_ctx* ctx, int64_t* count);

@@ -47,6 +47,7 @@ struct LkArgs {
     float* gn;
     int64_t stride;
     int32_t* err;
+    unsigned long long* pairs;
 };
 
 __device__ __forceinline__ void issue_chunk(const LkArgs& A, float4* dst, uint64_t* bar, int c, int nv) {
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
 
     const int nv = *A.nvalid;
     const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -258,6 +260,7 @@ int mp_launch_likelihood(mp_ctx* c) {
     A.gn = c->gn;
     A.stride = c->cap;
     A.err = c->dev_error;
+    A.pairs = c->pairs;
     k_likelihood<<<grid_for(c->n, LK_THREADS), LK_THREADS, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
     return MP_OK;

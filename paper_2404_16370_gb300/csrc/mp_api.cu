@@ -138,10 +138,11 @@ void destroy(mp_ctx* c) {
     dfree(c->map_pts); dfree(c->map_normals); dfree(c->map_valid); dfree(c->map_rec); dfree(c->nnf);
     dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pts); dfree(c->scan_tmp4);
     dfree(c->scan_nvalid);
-    dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error);
-    for (int s = 0; s <= MP_NSTAGES; ++s)
-        for (int k = 0; k < 2; ++k)
-            if (c->ev[s][k]) cudaEventDestroy(c->ev[s][k]);
+    dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->pairs);
+    for (int r = 0; r < MP_EV_RING; ++r)
+        for (int s = 0; s < MP_NSTAGES; ++s)
+            for (int k = 0; k < 2; ++k)
+                if (c->ev[r][s][k]) cudaEventDestroy(c->ev[r][s][k]);
     free(c->host_tmp);
     delete c;
 }
@@ -212,13 +213,26 @@ struct DevTmp {
     ~DevTmp() { if (p) cudaFree(p); }
 };
 
+// Stage timing: run r of stage s uses event pair ev[r % RING][s]; before a
+// pair is reused its (long completed) interval is folded into the total.
 int stage_begin(mp_ctx* c, int s) {
-    if (c->timing) MP_CUDA(c, cudaEventRecord(c->ev[s][0], c->stream));
-    c->stage_ran[s] = 1;
+    if (!c->timing) return MP_OK;
+    int64_t r = c->stage_runs[s];
+    int slot = (int)(r % MP_EV_RING);
+    if (r >= MP_EV_RING) {
+        float ms = 0.f;
+        MP_CUDA(c, cudaEventSynchronize(c->ev[slot][s][1]));
+        MP_CUDA(c, cudaEventElapsedTime(&ms, c->ev[slot][s][0], c->ev[slot][s][1]));
+        c->stage_ms[s] += ms;
+    }
+    MP_CUDA(c, cudaEventRecord(c->ev[slot][s][0], c->stream));
     return MP_OK;
 }
 int stage_end(mp_ctx* c, int s) {
-    if (c->timing) MP_CUDA(c, cudaEventRecord(c->ev[s][1], c->stream));
+    if (!c->timing) return MP_OK;
+    int slot = (int)(c->stage_runs[s] % MP_EV_RING);
+    MP_CUDA(c, cudaEventRecord(c->ev[slot][s][1], c->stream));
+    c->stage_runs[s]++;
     return MP_OK;
 }
 
@@ -306,11 +320,16 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
         if (rc) break;
         e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "map preprocessing"); break; }
-        for (int s = 0; s <= MP_NSTAGES; ++s)
-            for (int k = 0; k < 2; ++k) {
-                e = cudaEventCreate(&c->ev[s][k]);
-                if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "event"); break; }
-            }
+        if ((rc = dalloc(c, &c->pairs, 1))) break;
+        e = cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->stream);
+        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "memset"); break; }
+        for (int r = 0; r < MP_EV_RING && !rc; ++r)
+            for (int s = 0; s < MP_NSTAGES && !rc; ++s)
+                for (int k = 0; k < 2 && !rc; ++k) {
+                    e = cudaEventCreate(&c->ev[r][s][k]);
+                    if (e != cudaSuccess) rc = mp_cuda_check(c, e, "event");
+                }
+        if (rc) break;
     } while (0);
     if (xyz_dev) cudaFree(xyz_dev);
     if (rc) {
@@ -415,7 +434,6 @@ int mp_run_stages(mp_ctx* c, uint32_t mask) {
     if (!c) return MP_EINVAL;
     if (c->n == 0) return mp_fail(c, MP_ENOTINIT, "particles not initialised");
     int rc = MP_OK;
-    for (int s = 0; s < MP_NSTAGES; ++s) c->stage_ran[s] = 0;
     for (int s = 0; s < MP_NSTAGES; ++s) {
         uint32_t bit = 1u << s;
         if (!(mask & bit)) continue;
@@ -666,16 +684,38 @@ int mp_map_info(mp_ctx* c, float origin[3], int32_t dims[3], float* inv_res, flo
 
 int mp_set_timing(mp_ctx* c, int enable) {
     if (!c) return MP_EINVAL;
+    MP_CUDA(c, cudaStreamSynchronize(c->stream));
     c->timing = enable ? 1 : 0;
+    if (enable) {
+        for (int s = 0; s < MP_NSTAGES; ++s) {
+            c->stage_runs[s] = 0;
+            c->stage_ms[s] = 0.0;
+        }
+        MP_CUDA(c, cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->stream));
+    }
     return MP_OK;
 }
 
-int mp_stage_times(mp_ctx* c, float ms[9]) {
-    if (!c || !ms) return MP_EINVAL;
+int mp_stage_times(mp_ctx* c, float ms[9], int64_t runs[9], int64_t* pairs) {
+    if (!c) return MP_EINVAL;
     MP_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int s = 0; s < MP_NSTAGES; ++s) {
-        ms[s] = 0.f;
-        if (c->timing && c->stage_ran[s]) MP_CUDA(c, cudaEventElapsedTime(&ms[s], c->ev[s][0], c->ev[s][1]));
+        double tot = c->stage_ms[s];
+        int64_t r = c->stage_runs[s];
+        int64_t first = r > MP_EV_RING ? r - MP_EV_RING : 0;
+        for (int64_t k = first; k < r; ++k) {
+            float m = 0.f;
+            int slot = (int)(k % MP_EV_RING);
+            MP_CUDA(c, cudaEventElapsedTime(&m, c->ev[slot][s][0], c->ev[slot][s][1]));
+            tot += m;
+        }
+        if (ms) ms[s] = (float)tot;
+        if (runs) runs[s] = r;
+    }
+    if (pairs) {
+        unsigned long long v = 0;
+        MP_CUDA(c, cudaMemcpy(&v, c->pairs, sizeof(v), cudaMemcpyDeviceToHost));
+        *pairs = (int64_t)v;
     }
     return MP_OK;
 }

@@ -16,6 +16,7 @@
 // context
 // ---------------------------------------------------------------------------
 #define MP_NSTAGES 9
+#define MP_EV_RING 64       // event pairs per stage kept in flight for timing
 #define MP_MAXK 32          // largest neighbour list (one warp per particle)
 #define MP_COVK 16          // largest covariance neighbourhood
 #define MP_GN 29            // H (21) + b (6) + log-likelihood + inlier count
@@ -96,10 +97,12 @@ struct mp_ctx {
     float4* best_pose;      // 2 float4
     int32_t* dev_error;     // bit 0: a bounded wait gave up
 
-    // timing
+    // timing: a ring of event pairs per stage; totals folded in as slots recycle
     int timing;
-    cudaEvent_t ev[MP_NSTAGES + 1][2];
-    int stage_ran[MP_NSTAGES];
+    cudaEvent_t ev[MP_EV_RING][MP_NSTAGES][2];
+    int64_t stage_runs[MP_NSTAGES];
+    double stage_ms[MP_NSTAGES];
+    unsigned long long* pairs;   // device counter of likelihood pairs
 
     // host staging
     void* host_tmp;

@@ -92,7 +92,7 @@ def lib():
         L.mp_nnf_query.argtypes = [V, P, I64, P]
         L.mp_map_info.argtypes = [V, P, P, P, P, P]
         L.mp_set_timing.argtypes = [V, C.c_int]
-        L.mp_stage_times.argtypes = [V, P]
+        L.mp_stage_times.argtypes = [V, P, P, C.POINTER(I64)]
         L.mp_kernel_launches.argtypes = [V, C.POINTER(I64)]
         for f in ("mp_default_params", "mp_init_map", "mp_init_particles", "mp_step", "mp_get_posterior", "mp_destroy",
                   "mp_set_scan", "mp_set_odometry", "mp_run_stages", "mp_set_step_index", "mp_buffer_size",
@@ -250,9 +250,13 @@ def mp_set_timing(ctx, enable=True):
 
 
 def mp_stage_times(ctx):
+    """(per-stage total ms, per-stage run counts, likelihood pairs) since timing was enabled."""
     ms = np.zeros(9, np.float32)
-    _check(lib().mp_stage_times(ctx, ms.ctypes.data_as(C.c_void_p)), ctx)
-    return dict(zip(STAGE_NAMES, ms.tolist()))
+    runs = np.zeros(9, np.int64)
+    pairs = C.c_int64()
+    _check(lib().mp_stage_times(ctx, ms.ctypes.data_as(C.c_void_p), runs.ctypes.data_as(C.c_void_p),
+                                C.byref(pairs)), ctx)
+    return dict(zip(STAGE_NAMES, ms.tolist())), dict(zip(STAGE_NAMES, runs.tolist())), int(pairs.value)
 
 
 def mp_kernel_launches(ctx) -> int:

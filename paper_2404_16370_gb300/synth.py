@@ -183,11 +183,20 @@ class Cylinders:
 
     def contains(self, p, margin=0.0):
         inside = np.zeros(len(p), bool)
-        for k in range(len(self)):
-            dx = p[:, 0] - self.c[k, 0]
-            dy = p[:, 1] - self.c[k, 1]
-            inside |= ((dx * dx + dy * dy <= (self.r[k] + margin) ** 2) & (p[:, 2] >= self.z0[k] - margin)
-                       & (p[:, 2] <= self.z0[k] + self.h[k] + margin))
+        if len(self) == 0:
+            return inside
+        from scipy.spatial import cKDTree
+        rmax = float(self.r.max()) + margin
+        for k, cand in enumerate(cKDTree(p[:, :2]).query_ball_point(self.c, rmax)):
+            if not cand:
+                continue
+            cand = np.asarray(cand)
+            q = p[cand]
+            dx = q[:, 0] - self.c[k, 0]
+            dy = q[:, 1] - self.c[k, 1]
+            hit = ((dx * dx + dy * dy <= (self.r[k] + margin) ** 2) & (q[:, 2] >= self.z0[k] - margin)
+                   & (q[:, 2] <= self.z0[k] + self.h[k] + margin))
+            inside[cand[hit]] = True
         return inside
 
 
