@@ -55,9 +55,10 @@ def workload_desc(nvalid=None):
     return d
 
 
-def make_workload(n_steps, n_particles=N_PARTICLES):
+def make_workload(n_steps, n_particles=None):
     from paper_2404_16370_gb300 import synth
-    return synth.outdoor_workload(n_particles=n_particles, n_steps=max(n_steps, 1), n_map=N_MAP, n_points=N_POINTS)
+    return synth.outdoor_workload(n_particles=n_particles or N_PARTICLES, n_steps=max(n_steps, 1), n_map=N_MAP,
+                                  n_points=N_POINTS)
 
 
 class ClockSampler:
@@ -306,9 +307,13 @@ def main():
     ap.add_argument("--sample", type=int, default=1024, help="particles per step in the reference arm's sample")
     ap.add_argument("--cpu-sample", type=int, default=4096, help="particles in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--particles", type=int, default=N_PARTICLES,
+                    help="particle count (profiling runs of a smaller case; the benchmark is 2^20)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    global N_PARTICLES
+    N_PARTICLES = args.particles
     if args.impl == "reference":
         run_reference(args)
     else:
