@@ -299,6 +299,7 @@ def run_gpu(args):
 
 
 def main():
+    global N_PARTICLES
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -312,7 +313,6 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    global N_PARTICLES
     N_PARTICLES = args.particles
     if args.impl == "reference":
         run_reference(args)
