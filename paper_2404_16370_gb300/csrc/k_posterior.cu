@@ -2,7 +2,7 @@
 // and the representative state:
 //   l_i = log prior_i + log p(P | x_i); p_i = exp(l_i - max l) (FP64);
 //   post_iters Jacobi sweeps p'_i = sum_j k_ij p_j / sum_j k_ij over the list
-//   of i (a group of lanes per particle, shuffle reductions);
+//   of i (one thread per particle, FP64 fused multiply-adds);
 //   normalise; best = argmax (smallest index on ties); log prior <- log p'.
 // Grid-wide max / sum / argmax are two-level (block partials, one final
 // block), so results do not depend on atomics' order.
@@ -90,29 +90,37 @@ __global__ void __launch_bounds__(1024) k_reduce_sum(const double* __restrict__ 
     }
 }
 
-template <int G>
+// 1 / sum_j k_ij (FP64), fixed for the sweeps of a step
+__global__ void k_post_invden(int64_t n, int K, const int32_t* __restrict__ ids, const float* __restrict__ kk,
+                              double* __restrict__ inv_den) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double den = 0.0;
+    for (int l = 0; l < K; ++l)
+        if (ids[i * K + l] >= 0) den += (double)kk[i * K + l];
+    inv_den[i] = den > 0.0 ? 1.0 / den : 0.0;
+}
+
+// One Jacobi sweep of Eq. 11, one thread per particle: FP64 fused
+// multiply-adds over the list (GB300's FP64 rate is low, so the list is not
+// spread over lanes: that would cost a shuffle-add tree per particle).
+template <int KT>
 __global__ void __launch_bounds__(256) k_post_sweep(const double* __restrict__ pin, double* __restrict__ pout, int64_t n,
-                                                    int K, const int32_t* __restrict__ ids,
-                                                    const float* __restrict__ kk) {
-    int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t i = gt / G;
-    int l = (int)(gt % G);
-    double num = 0.0, den = 0.0;
-    if (i < n && l < K) {
-        int64_t o = i * K + l;
-        int j = ids[o];
-        if (j >= 0) {
-            double k = (double)kk[o];
-            num = k * pin[j];
-            den = k;
-        }
+                                                    int Krt, const int32_t* __restrict__ ids,
+                                                    const float* __restrict__ kk, const double* __restrict__ inv_den) {
+    const int K = KT > 0 ? KT : Krt;   // compile-time list length for the common sizes
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t* row = ids + i * K;
+    const float* kr = kk + i * K;
+    double num = 0.0;
+#pragma unroll 8
+    for (int l = 0; l < K; ++l) {
+        int j = __ldg(row + l);
+        if (j >= 0) num = fma((double)__ldg(kr + l), __ldg(pin + j), num);
     }
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) {
-        num += __shfl_xor_sync(0xffffffffu, num, off, G);
-        den += __shfl_xor_sync(0xffffffffu, den, off, G);
-    }
-    if (i < n && l == 0) pout[i] = den > 0.0 ? num / den : pin[i];
+    double inv = inv_den[i];
+    pout[i] = inv > 0.0 ? num * inv : pin[i];
 }
 
 __global__ void __launch_bounds__(PB) k_post_final_part(const double* __restrict__ p, int64_t n,
@@ -202,12 +210,11 @@ __global__ void k_post_normalise(const double* __restrict__ p, int64_t n, const 
     }
 }
 
-template <int G>
-int sweeps(mp_ctx* c, double*& a, double*& b) {
-    int64_t threads = c->n * G;
+template <int KT>
+int sweeps(mp_ctx* c, double*& a, double*& b, const double* inv_den) {
     for (int it = 0; it < c->p.post_iters; ++it) {
-        k_post_sweep<G><<<grid_for(threads, 256), 256, 0, c->stream>>>(a, b, c->n, c->p.K, c->nbr_ids[c->nbr_cur],
-                                                                      c->nbr_k);
+        k_post_sweep<KT><<<grid_for(c->n, 256), 256, 0, c->stream>>>(a, b, c->n, c->p.K, c->nbr_ids[c->nbr_cur],
+                                                                    c->nbr_k, inv_den);
         MP_LAUNCHED(c);
         double* t = a;
         a = b;
@@ -215,6 +222,8 @@ int sweeps(mp_ctx* c, double*& a, double*& b) {
     }
     return MP_OK;
 }
+
+
 
 }  // namespace
 
@@ -233,15 +242,15 @@ int mp_launch_posterior(mp_ctx* c) {
     MP_LAUNCHED(c);
     k_reduce_sum<<<1, 1024, 0, c->stream>>>(part, nb, &c->scalars[1]);
     MP_LAUNCHED(c);
+    k_post_invden<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->p.K, c->nbr_ids[c->nbr_cur], c->nbr_k,
+                                                           c->post_invden);
+    MP_LAUNCHED(c);
     double* a = c->post_tmp;
     double* b = c->post;
-    int K = c->p.K, rc;
-    if (K <= 1) rc = sweeps<1>(c, a, b);
-    else if (K <= 2) rc = sweeps<2>(c, a, b);
-    else if (K <= 4) rc = sweeps<4>(c, a, b);
-    else if (K <= 8) rc = sweeps<8>(c, a, b);
-    else if (K <= 16) rc = sweeps<16>(c, a, b);
-    else rc = sweeps<32>(c, a, b);
+    int rc;
+    if (c->p.K == 32) rc = sweeps<32>(c, a, b, c->post_invden);
+    else if (c->p.K == 16) rc = sweeps<16>(c, a, b, c->post_invden);
+    else rc = sweeps<0>(c, a, b, c->post_invden);
     if (rc) return rc;
     // a holds the smoothed (unnormalised) posterior
     k_post_final_part<<<nb, PB, 0, c->stream>>>(a, n, part, part2, part_idx);

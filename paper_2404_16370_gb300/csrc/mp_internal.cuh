@@ -52,6 +52,7 @@ struct mp_ctx {
     double* post;
     double* post_tmp;
     double* post_init;      // unnormalised initial posterior exp(l - max l)
+    double* post_invden;    // 1 / sum_j k_ij of the current lists
     float* loglik;
     int32_t* n_in;
     uint32_t* keys;
