@@ -57,6 +57,111 @@ __device__ __forceinline__ void issue_chunk(const LkArgs& A, float4* dst, uint64
     bulk_g2s(dst, A.scan + 2 * (int64_t)c * LK_CHUNK, bytes, bar);
 }
 
+// Sums of one particle over the scan (map frame, see the file comment).
+struct LkAcc {
+    float Hww[6];    // (00 01 02 11 12 22)
+    float Hwv[9];    // row-major
+    float Hvv[6];    // (00 01 02 11 12 22)
+    float bw[3], bv[3];
+    float ll;
+    int cnt;
+};
+
+// Transformed point by the decision sequence.
+__device__ __forceinline__ void lk_transform(const float R[9], float tx, float ty, float tz, const float4& P0,
+                                             float& qtx, float& qty, float& qtz, float& qx, float& qy, float& qz) {
+    qtx = __fmaf_rn(R[2], P0.z, __fmaf_rn(R[1], P0.y, __fmul_rn(R[0], P0.x)));
+    qty = __fmaf_rn(R[5], P0.z, __fmaf_rn(R[4], P0.y, __fmul_rn(R[3], P0.x)));
+    qtz = __fmaf_rn(R[8], P0.z, __fmaf_rn(R[7], P0.y, __fmul_rn(R[6], P0.x)));
+    qx = __fadd_rn(qtx, tx);
+    qy = __fadd_rn(qty, ty);
+    qz = __fadd_rn(qtz, tz);
+}
+
+// NNF entry of a scan point under the particle pose (-1: outside or empty).
+__device__ __forceinline__ int lk_lookup(const LkArgs& A, const float R[9], float tx, float ty, float tz,
+                                         const float4& P0) {
+    float qtx, qty, qtz, qx, qy, qz;
+    lk_transform(R, tx, ty, tz, P0, qtx, qty, qtz, qx, qy, qz);
+    const int vx = floor_to_int(__fmaf_rn(qx, A.inv_res, A.offx));
+    const int vy = floor_to_int(__fmaf_rn(qy, A.inv_res, A.offy));
+    const int vz = floor_to_int(__fmaf_rn(qz, A.inv_res, A.offz));
+    const bool in = (unsigned)vx < (unsigned)A.nx && (unsigned)vy < (unsigned)A.ny && (unsigned)vz < (unsigned)A.nz;
+    int mm = -1;
+    if (in) mm = __ldg(A.nnf + ((vz * A.ny + vy) * A.nx + vx));
+    return mm;
+}
+
+__device__ __forceinline__ void lk_record(const LkArgs& A, int mm, float4& r0, float4& r1) {
+    r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r1 = r0;
+    if (mm >= 0) {
+        r0 = __ldg(A.rec + 2 * mm);
+        r1 = __ldg(A.rec + 2 * mm + 1);
+    }
+}
+
+// One (particle, point) pair: cost, inlier test, and the map-frame sums.
+__device__ __forceinline__ void lk_accumulate(const LkArgs& A, LkAcc& S, const float R[9], float tx, float ty, float tz,
+                                              const float4& P0, const float4& P1, int mm, const float4& r0,
+                                              const float4& r1) {
+    float qtx, qty, qtz, qx, qy, qz;
+    lk_transform(R, tx, ty, tz, P0, qtx, qty, qtz, qx, qy, qz);
+    const float ex = r0.x - qx, ey = r0.y - qy, ez = r0.z - qz;
+    const float ux = R[0] * P0.w + R[1] * P1.x + R[2] * P1.y;
+    const float uy = R[3] * P0.w + R[4] * P1.x + R[5] * P1.y;
+    const float uz = R[6] * P0.w + R[7] * P1.x + R[8] * P1.y;
+    const float wx = r0.w, wy = r1.x, wz = r1.y;
+    const float sg = copysignf(1.f, ux * wx + uy * wy + uz * wz);
+    const float sx = fmaf(sg, wx, ux), sy = fmaf(sg, wy, uy), sz = fmaf(sg, wz, uz);
+    const float dx = fmaf(-sg, wx, ux), dy = fmaf(-sg, wy, uy), dz = fmaf(-sg, wz, uz);
+    const float dd = dx * dx + dy * dy + dz * dz;
+    const float ls = fmaf(A.half_a, dd, A.two_eps);
+    const float ld = fmaf(-A.half_a, dd, 2.f);
+    const float rr = __fdividef(A.quarter_a, ls * ld);
+    const float as = ld * rr, ad = ls * rr;
+    const float se = sx * ex + sy * ey + sz * ez;
+    const float de = dx * ex + dy * ey + dz * ez;
+    const float ee = ex * ex + ey * ey + ez * ez;
+    const float cost = fmaf(0.5f, ee, fmaf(as * se, se, ad * de * de));
+    const bool inl = (mm >= 0) && (cost <= A.c_max);
+    S.ll -= inl ? cost : A.c_max;
+    S.cnt += inl ? 1 : 0;
+    const float h = inl ? 0.5f : 0.f;
+    const float Pw = inl ? as : 0.f, Qw = inl ? ad : 0.f;
+    const float Psx = Pw * sx, Psy = Pw * sy, Psz = Pw * sz;
+    const float Qdx = Qw * dx, Qdy = Qw * dy, Qdz = Qw * dz;
+    const float Oxx = fmaf(Psx, sx, fmaf(Qdx, dx, h));
+    const float Oyy = fmaf(Psy, sy, fmaf(Qdy, dy, h));
+    const float Ozz = fmaf(Psz, sz, fmaf(Qdz, dz, h));
+    const float Oxy = fmaf(Psx, sy, Qdx * dy);
+    const float Oxz = fmaf(Psx, sz, Qdx * dz);
+    const float Oyz = fmaf(Psy, sz, Qdy * dz);
+    const float gx = Oxx * ex + Oxy * ey + Oxz * ez;
+    const float gy = Oxy * ex + Oyy * ey + Oyz * ez;
+    const float gz = Oxz * ex + Oyz * ey + Ozz * ez;
+    // Pm = [q~]x Omega
+    const float P00 = qty * Oxz - qtz * Oxy, P01 = qty * Oyz - qtz * Oyy, P02 = qty * Ozz - qtz * Oyz;
+    const float P10 = qtz * Oxx - qtx * Oxz, P11 = qtz * Oxy - qtx * Oyz, P12 = qtz * Oxz - qtx * Ozz;
+    const float P20 = qtx * Oxy - qty * Oxx, P21 = qtx * Oyy - qty * Oxy, P22 = qtx * Oyz - qty * Oxz;
+    // H~_ww += Pm [q~]x^T ; H~_wv += Pm ; H~_vv += Omega
+    S.Hww[0] += qty * P02 - qtz * P01;
+    S.Hww[1] += qtz * P00 - qtx * P02;
+    S.Hww[2] += qtx * P01 - qty * P00;
+    S.Hww[3] += qtz * P10 - qtx * P12;
+    S.Hww[4] += qtx * P11 - qty * P10;
+    S.Hww[5] += qtx * P21 - qty * P20;
+    S.Hwv[0] += P00; S.Hwv[1] += P01; S.Hwv[2] += P02;
+    S.Hwv[3] += P10; S.Hwv[4] += P11; S.Hwv[5] += P12;
+    S.Hwv[6] += P20; S.Hwv[7] += P21; S.Hwv[8] += P22;
+    S.Hvv[0] += Oxx; S.Hvv[1] += Oxy; S.Hvv[2] += Oxz; S.Hvv[3] += Oyy; S.Hvv[4] += Oyz; S.Hvv[5] += Ozz;
+    // b~ = [ g x q~ ; -g ]
+    S.bw[0] += gy * qtz - gz * qty;
+    S.bw[1] += gz * qtx - gx * qtz;
+    S.bw[2] += gx * qty - gy * qtx;
+    S.bv[0] -= gx; S.bv[1] -= gy; S.bv[2] -= gz;
+}
+
 __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
     __shared__ __align__(128) float4 buf[2][2 * LK_CHUNK];
     __shared__ __align__(8) uint64_t bar[2];
@@ -84,12 +189,15 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
         if (nchunks > 1) issue_chunk(A, buf[1], &bar[1], 1, nv);
     }
 
-    float Hww0 = 0, Hww1 = 0, Hww2 = 0, Hww3 = 0, Hww4 = 0, Hww5 = 0;     // (00 01 02 11 12 22)
-    float Hwv00 = 0, Hwv01 = 0, Hwv02 = 0, Hwv10 = 0, Hwv11 = 0, Hwv12 = 0, Hwv20 = 0, Hwv21 = 0, Hwv22 = 0;
-    float Hvv0 = 0, Hvv1 = 0, Hvv2 = 0, Hvv3 = 0, Hvv4 = 0, Hvv5 = 0;
-    float bw0 = 0, bw1 = 0, bw2 = 0, bv0 = 0, bv1 = 0, bv2 = 0;
-    float ll = 0.f;
-    int cnt = 0;
+    LkAcc S;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { S.Hww[k] = 0.f; S.Hvv[k] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S.Hwv[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { S.bw[k] = 0.f; S.bv[k] = 0.f; }
+    S.ll = 0.f;
+    S.cnt = 0;
 
     const float tx = t[0], ty = t[1], tz = t[2];
     bool failed = false;
@@ -102,80 +210,22 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
         const int m = min(LK_CHUNK, nv - c * LK_CHUNK);
         if (active) {
             const float4* P = buf[b];
-#pragma unroll 4
+            // software pipeline: NNF entries two points ahead, map records one
+            // point ahead, so that each gather has a whole point of arithmetic
+            // (and the other warps' work) to land in
+            int m0 = lk_lookup(A, R, tx, ty, tz, P[0]);
+            int m1 = m > 1 ? lk_lookup(A, R, tx, ty, tz, P[2]) : -1;
+            float4 ra0, ra1;
+            lk_record(A, m0, ra0, ra1);
             for (int k = 0; k < m; ++k) {
-                const float4 P0 = P[2 * k], P1 = P[2 * k + 1];
-                // transformed point by the decision sequence
-                const float qtx = __fmaf_rn(R[2], P0.z, __fmaf_rn(R[1], P0.y, __fmul_rn(R[0], P0.x)));
-                const float qty = __fmaf_rn(R[5], P0.z, __fmaf_rn(R[4], P0.y, __fmul_rn(R[3], P0.x)));
-                const float qtz = __fmaf_rn(R[8], P0.z, __fmaf_rn(R[7], P0.y, __fmul_rn(R[6], P0.x)));
-                const float qx = __fadd_rn(qtx, tx), qy = __fadd_rn(qty, ty), qz = __fadd_rn(qtz, tz);
-                const int vx = floor_to_int(__fmaf_rn(qx, A.inv_res, A.offx));
-                const int vy = floor_to_int(__fmaf_rn(qy, A.inv_res, A.offy));
-                const int vz = floor_to_int(__fmaf_rn(qz, A.inv_res, A.offz));
-                const bool in = (unsigned)vx < (unsigned)A.nx && (unsigned)vy < (unsigned)A.ny &&
-                                (unsigned)vz < (unsigned)A.nz;
-                int mm = -1;
-                if (in) mm = __ldg(A.nnf + ((vz * A.ny + vy) * A.nx + vx));
-                float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-                if (mm >= 0) {
-                    r0 = __ldg(A.rec + 2 * mm);
-                    r1 = __ldg(A.rec + 2 * mm + 1);
-                }
-                // residual and information matrix (map frame)
-                const float ex = r0.x - qx, ey = r0.y - qy, ez = r0.z - qz;
-                const float ux = R[0] * P0.w + R[1] * P1.x + R[2] * P1.y;
-                const float uy = R[3] * P0.w + R[4] * P1.x + R[5] * P1.y;
-                const float uz = R[6] * P0.w + R[7] * P1.x + R[8] * P1.y;
-                const float wx = r0.w, wy = r1.x, wz = r1.y;
-                const float sg = copysignf(1.f, ux * wx + uy * wy + uz * wz);
-                const float sx = fmaf(sg, wx, ux), sy = fmaf(sg, wy, uy), sz = fmaf(sg, wz, uz);
-                const float dx = fmaf(-sg, wx, ux), dy = fmaf(-sg, wy, uy), dz = fmaf(-sg, wz, uz);
-                const float dd = dx * dx + dy * dy + dz * dz;
-                const float ls = fmaf(A.half_a, dd, A.two_eps);
-                const float ld = fmaf(-A.half_a, dd, 2.f);
-                const float rr = __fdividef(A.quarter_a, ls * ld);
-                const float as = ld * rr, ad = ls * rr;
-                const float se = sx * ex + sy * ey + sz * ez;
-                const float de = dx * ex + dy * ey + dz * ez;
-                const float ee = ex * ex + ey * ey + ez * ez;
-                const float cost = fmaf(0.5f, ee, fmaf(as * se, se, ad * de * de));
-                const bool inl = (mm >= 0) && (cost <= A.c_max);
-                ll -= inl ? cost : A.c_max;
-                cnt += inl ? 1 : 0;
-                const float h = inl ? 0.5f : 0.f;
-                const float Pw = inl ? as : 0.f, Qw = inl ? ad : 0.f;
-                const float Psx = Pw * sx, Psy = Pw * sy, Psz = Pw * sz;
-                const float Qdx = Qw * dx, Qdy = Qw * dy, Qdz = Qw * dz;
-                const float Oxx = fmaf(Psx, sx, fmaf(Qdx, dx, h));
-                const float Oyy = fmaf(Psy, sy, fmaf(Qdy, dy, h));
-                const float Ozz = fmaf(Psz, sz, fmaf(Qdz, dz, h));
-                const float Oxy = fmaf(Psx, sy, Qdx * dy);
-                const float Oxz = fmaf(Psx, sz, Qdx * dz);
-                const float Oyz = fmaf(Psy, sz, Qdy * dz);
-                const float gx = Oxx * ex + Oxy * ey + Oxz * ez;
-                const float gy = Oxy * ex + Oyy * ey + Oyz * ez;
-                const float gz = Oxz * ex + Oyz * ey + Ozz * ez;
-                // Pm = [q~]x Omega
-                const float P00 = qty * Oxz - qtz * Oxy, P01 = qty * Oyz - qtz * Oyy, P02 = qty * Ozz - qtz * Oyz;
-                const float P10 = qtz * Oxx - qtx * Oxz, P11 = qtz * Oxy - qtx * Oyz, P12 = qtz * Oxz - qtx * Ozz;
-                const float P20 = qtx * Oxy - qty * Oxx, P21 = qtx * Oyy - qty * Oxy, P22 = qtx * Oyz - qty * Oxz;
-                // H~_ww += Pm [q~]x^T ; H~_wv += Pm ; H~_vv += Omega
-                Hww0 += qty * P02 - qtz * P01;
-                Hww1 += qtz * P00 - qtx * P02;
-                Hww2 += qtx * P01 - qty * P00;
-                Hww3 += qtz * P10 - qtx * P12;
-                Hww4 += qtx * P11 - qty * P10;
-                Hww5 += qtx * P21 - qty * P20;
-                Hwv00 += P00; Hwv01 += P01; Hwv02 += P02;
-                Hwv10 += P10; Hwv11 += P11; Hwv12 += P12;
-                Hwv20 += P20; Hwv21 += P21; Hwv22 += P22;
-                Hvv0 += Oxx; Hvv1 += Oxy; Hvv2 += Oxz; Hvv3 += Oyy; Hvv4 += Oyz; Hvv5 += Ozz;
-                // b~ = [ g x q~ ; -g ]
-                bw0 += gy * qtz - gz * qty;
-                bw1 += gz * qtx - gx * qtz;
-                bw2 += gx * qty - gy * qtx;
-                bv0 -= gx; bv1 -= gy; bv2 -= gz;
+                const int m2 = (k + 2 < m) ? lk_lookup(A, R, tx, ty, tz, P[2 * (k + 2)]) : -1;
+                float4 rb0, rb1;
+                lk_record(A, m1, rb0, rb1);
+                lk_accumulate(A, S, R, tx, ty, tz, P[2 * k], P[2 * k + 1], m0, ra0, ra1);
+                m0 = m1;
+                m1 = m2;
+                ra0 = rb0;
+                ra1 = rb1;
             }
         }
         __syncthreads();
@@ -193,9 +243,9 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
     if (!active) return;
 
     // rotate the sums back to the sensor frame: blocks M -> R^T M R
-    float Hw[3][3] = {{Hww0, Hww1, Hww2}, {Hww1, Hww3, Hww4}, {Hww2, Hww4, Hww5}};
-    float Hc[3][3] = {{Hwv00, Hwv01, Hwv02}, {Hwv10, Hwv11, Hwv12}, {Hwv20, Hwv21, Hwv22}};
-    float Hv[3][3] = {{Hvv0, Hvv1, Hvv2}, {Hvv1, Hvv3, Hvv4}, {Hvv2, Hvv4, Hvv5}};
+    float Hw[3][3] = {{S.Hww[0], S.Hww[1], S.Hww[2]}, {S.Hww[1], S.Hww[3], S.Hww[4]}, {S.Hww[2], S.Hww[4], S.Hww[5]}};
+    float Hc[3][3] = {{S.Hwv[0], S.Hwv[1], S.Hwv[2]}, {S.Hwv[3], S.Hwv[4], S.Hwv[5]}, {S.Hwv[6], S.Hwv[7], S.Hwv[8]}};
+    float Hv[3][3] = {{S.Hvv[0], S.Hvv[1], S.Hvv[2]}, {S.Hvv[1], S.Hvv[3], S.Hvv[4]}, {S.Hvv[2], S.Hvv[4], S.Hvv[5]}};
     float Ow[3][3], Oc[3][3], Ov[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -214,9 +264,8 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
             Ow[a][bb] = sw; Oc[a][bb] = sc; Ov[a][bb] = sv;
         }
     float bwr[3], bvr[3];
-    const float bwm[3] = {bw0, bw1, bw2}, bvm[3] = {bv0, bv1, bv2};
-    rot_apply_T(R, bwm, bwr);
-    rot_apply_T(R, bvm, bvr);
+    rot_apply_T(R, S.bw, bwr);
+    rot_apply_T(R, S.bv, bvr);
     float out[MP_GN];
     // upper rows of the 6x6 [ [Hww, Hwv], [Hwv^T, Hvv] ]
     int o = 0;
@@ -232,8 +281,8 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
         }
     out[21] = bwr[0]; out[22] = bwr[1]; out[23] = bwr[2];
     out[24] = bvr[0]; out[25] = bvr[1]; out[26] = bvr[2];
-    out[27] = ll;
-    out[28] = (float)cnt;
+    out[27] = S.ll;
+    out[28] = (float)S.cnt;
 #pragma unroll
     for (int f = 0; f < MP_GN; ++f) A.gn[(int64_t)f * A.stride + p] = out[f];
 }
