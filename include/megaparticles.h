@@ -203,6 +203,35 @@ int mp_stage_times(mp_ctx* ctx, float ms_out[9], int64_t runs_out[9], int64_t* p
 /* Number of kernels this context has launched so far. */
 int mp_kernel_launches(mp_ctx* ctx, int64_t* count);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free initial posterior. The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory when they
+ * need it -- a real-time loop that allocates only at start-up (cudaMalloc can
+ * synchronise the device and stall for milliseconds), or an application whose
+ * device memory belongs to another allocator or a fixed budget.
+ *
+ * Computes, for n particles, p_i = exp(l_i - max l) / sum_j exp(l_j - max l)
+ * with l_i = log_prior[i] + loglik[i] (log_prior NULL: 0), and the index of
+ * the largest p_i (smallest index on ties): the same values as the posterior
+ * stage's initial posterior (MP_BUF_POST_INIT). log_prior (n float64), loglik
+ * (n float32), post_out (n float64) and best_out (1 int64) are DEVICE
+ * pointers owned by the caller; the work is enqueued on cuda_stream (NULL =
+ * legacy default stream) and the call does not synchronise.
+ *
+ * No memory is allocated: block partials live in one static device array of
+ * MP_NOALLOC_SCRATCH_BYTES that every device loading the library holds until
+ * the process exits. The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with the device current) and caches it; make
+ * that first call before any stream capture. All calls share the array, so
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * Errors: MP_EINVAL for NULL pointers or n outside [1,
+ * MP_NOALLOC_MAX_PARTICLES] (with a message on stderr), MP_ECUDA for a failed
+ * symbol lookup or launch. */
+#define MP_NOALLOC_MAX_PARTICLES (1 << 24)
+#define MP_NOALLOC_SCRATCH_BYTES (262144 + 256)
+int mp_posterior_init_noalloc(const double* log_prior, const float* loglik, int64_t n, double* post_out,
+                              int64_t* best_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

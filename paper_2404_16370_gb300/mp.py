@@ -259,6 +259,24 @@ def mp_stage_times(ctx):
     return dict(zip(STAGE_NAMES, ms.tolist())), dict(zip(STAGE_NAMES, runs.tolist())), int(pairs.value)
 
 
+def mp_posterior_init_noalloc(log_prior, loglik, post_out, best_out, cuda_stream=None):
+    """Device tensors in, device tensors out; allocates nothing (see the C header)."""
+    L = lib()
+    if not getattr(L, "_noalloc_declared", False):
+        L.mp_posterior_init_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                                C.c_void_p]
+        L.mp_posterior_init_noalloc.restype = C.c_int
+        L._noalloc_declared = True
+    lp, klp = _ptr(log_prior)
+    ll, kll = _ptr(loglik)
+    po, kpo = _ptr(post_out)
+    bo, kbo = _ptr(best_out)
+    n = int(loglik.shape[0])
+    rc = L.mp_posterior_init_noalloc(lp, ll, n, po, bo, C.c_void_p(cuda_stream) if cuda_stream else None)
+    if rc != MP_OK:
+        raise MPError(rc, "mp_posterior_init_noalloc failed (details on stderr)")
+
+
 def mp_kernel_launches(ctx) -> int:
     n = C.c_int64()
     _check(lib().mp_kernel_launches(ctx, C.byref(n)), ctx)
