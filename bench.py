@@ -102,8 +102,31 @@ def dist_setup(backend):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group(backend)
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return world, rank, local
+
+
+def rank_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world, device):
+    """Largest value over the ranks (timing: the slowest rank defines the job)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps, world, t_max):
+    """Whole-job throughput: steps of all ranks / elapsed time of the slowest rank."""
+    return steps * world / t_max
 
 
 def traffic_from_profile():
@@ -208,17 +231,10 @@ def run_gpu(args):
                 mp.mp_get_posterior(ctx)          # D2H of the step's result (best pose, its probability)
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        rank_barrier(world)
 
     def max_over_ranks(x):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([x], device=f"cuda:{local}", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        return reduce_max(x, world, f"cuda:{local}")
 
     try:
         # ---- device-resident inputs: the timed steps W .. W+K-1
@@ -262,7 +278,7 @@ def run_gpu(args):
     if rank != 0:
         return
     steps_total = args.steps * world
-    value = steps_total / t_max
+    value = job_value(args.steps, world, t_max)
     pairs_rank = pairs
     lk_ms = stage_ms["likelihood"]
     lk_runs = max(stage_runs["likelihood"], 1)

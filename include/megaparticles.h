@@ -203,6 +203,18 @@ int mp_stage_times(mp_ctx* ctx, float ms_out[9], int64_t runs_out[9], int64_t* p
 /* Number of kernels this context has launched so far. */
 int mp_kernel_launches(mp_ctx* ctx, int64_t* count);
 
+/* Test knobs of the failure path (no counterpart in the paper).
+ * MP_DEBUG_WAIT_BUDGET: SM-clock-cycle limit of every bounded device wait
+ * (default about 2 s; value <= 0 restores it). MP_DEBUG_STARVE_TX: when
+ * non-zero, the likelihood kernel announces 16 bytes more than it copies for
+ * its first scan chunk, so that chunk's barrier never completes and the
+ * bounded wait gives up; the kernel then records the error (reported as
+ * MP_ETIMEOUT by the next mp_get_posterior) and returns. No copy is left in
+ * flight. */
+#define MP_DEBUG_WAIT_BUDGET 1
+#define MP_DEBUG_STARVE_TX 2
+int mp_debug_set(mp_ctx* ctx, int what, int64_t value);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free initial posterior. The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory when they

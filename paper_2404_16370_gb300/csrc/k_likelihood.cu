@@ -48,12 +48,14 @@ struct LkArgs {
     int64_t stride;
     int32_t* err;
     unsigned long long* pairs;
+    long long budget;   // cycle limit of each barrier wait
+    int starve;         // test knob: announce 16 bytes more than copied for chunk 0
 };
 
 __device__ __forceinline__ void issue_chunk(const LkArgs& A, float4* dst, uint64_t* bar, int c, int nv) {
     int m = min(LK_CHUNK, nv - c * LK_CHUNK);
     uint32_t bytes = (uint32_t)m * 32u;
-    mbar_expect_tx(bar, bytes);
+    mbar_expect_tx(bar, bytes + ((A.starve && c == 0) ? 16u : 0u));
     bulk_g2s(dst, A.scan + 2 * (int64_t)c * LK_CHUNK, bytes, bar);
 }
 
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
     for (; c < nchunks; ++c) {
         const int b = c & 1;
         const uint32_t parity = (uint32_t)((c >> 1) & 1);
-        bool got = mbar_wait_bounded(&bar[b], parity, MP_WAIT_BUDGET);
+        bool got = mbar_wait_bounded(&bar[b], parity, A.budget);
         if (__syncthreads_or(!got)) { failed = true; break; }
         const int m = min(LK_CHUNK, nv - c * LK_CHUNK);
         if (active) {
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
             atomicOr(A.err, MP_ERR_WAIT);
             // drain the copies still in flight (bounded)
             for (int k = c; k < min(c + 2, nchunks); ++k)
-                mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), MP_WAIT_BUDGET);
+                mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), A.budget);
         }
         return;
     }
@@ -309,6 +311,8 @@ int mp_launch_likelihood(mp_ctx* c) {
     A.gn = c->gn;
     A.stride = c->cap;
     A.err = c->dev_error;
+    A.budget = c->wait_budget > 0 ? c->wait_budget : MP_WAIT_BUDGET;
+    A.starve = c->starve_tx;
     A.pairs = c->pairs;
     k_likelihood<<<grid_for(c->n, LK_THREADS), LK_THREADS, 0, c->stream>>>(A);
     MP_LAUNCHED(c);

@@ -720,6 +720,15 @@ int mp_stage_times(mp_ctx* c, float ms[9], int64_t runs[9], int64_t* pairs) {
     return MP_OK;
 }
 
+int mp_debug_set(mp_ctx* c, int what, int64_t value) {
+    if (!c) return MP_EINVAL;
+    switch (what) {
+        case MP_DEBUG_WAIT_BUDGET: c->wait_budget = value > 0 ? (long long)value : 0; return MP_OK;
+        case MP_DEBUG_STARVE_TX: c->starve_tx = value ? 1 : 0; return MP_OK;
+    }
+    return mp_fail(c, MP_EINVAL, "unknown debug knob %d", what);
+}
+
 int mp_kernel_launches(mp_ctx* c, int64_t* count) {
     if (!c || !count) return MP_EINVAL;
     *count = c->launches;

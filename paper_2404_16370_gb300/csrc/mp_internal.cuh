@@ -108,6 +108,10 @@ struct mp_ctx {
     // host staging
     void* host_tmp;
     size_t host_tmp_bytes;
+
+    // test knobs of the failure path
+    long long wait_budget;   // cycles; 0 = MP_WAIT_BUDGET
+    int starve_tx;
 };
 
 // ---------------------------------------------------------------------------

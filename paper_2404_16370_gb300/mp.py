@@ -207,10 +207,15 @@ def _shape(which, count, K):
 
 
 def mp_get_buffer(ctx, which, K=None, out=None):
-    count = mp_buffer_size(ctx, which)
+    """Copy a library buffer into a new numpy array, or into `out` (numpy or
+    torch, host or device); the element count passed is out's own, so the
+    library rejects an `out` of the wrong size."""
     if out is None:
+        count = mp_buffer_size(ctx, which)
         dt, shape = _shape(which, count, K if K is not None else _guess_k(ctx, which, count))
         out = np.empty(shape, dt)
+    else:
+        count = int(out.numel()) if hasattr(out, "numel") else int(out.size)
     po, ko = _ptr(out)
     _check(lib().mp_get_buffer(ctx, int(which), po, count), ctx)
     return out
@@ -257,6 +262,16 @@ def mp_stage_times(ctx):
     _check(lib().mp_stage_times(ctx, ms.ctypes.data_as(C.c_void_p), runs.ctypes.data_as(C.c_void_p),
                                 C.byref(pairs)), ctx)
     return dict(zip(STAGE_NAMES, ms.tolist())), dict(zip(STAGE_NAMES, runs.tolist())), int(pairs.value)
+
+
+MP_DEBUG_WAIT_BUDGET, MP_DEBUG_STARVE_TX = 1, 2
+
+
+def mp_debug_set(ctx, what, value):
+    L = lib()
+    L.mp_debug_set.argtypes = [C.c_void_p, C.c_int, C.c_int64]
+    L.mp_debug_set.restype = C.c_int
+    _check(L.mp_debug_set(ctx, int(what), int(value)), ctx)
 
 
 def mp_posterior_init_noalloc(log_prior, loglik, post_out, best_out, cuda_stream=None):

@@ -1,0 +1,145 @@
+"""Parity at the paper-scale workload the benchmark times (2^20 particles,
+8192-point scan, 1M-point outdoor map, K = C = 32, 0.2 m NNF), in the
+benchmark's launch configuration, against the oracle on samples it computes
+one by one: every map point's validity and sampled normals, 500k sampled NNF
+voxels, every particle's LSH key and the whole bucket order, sampled
+neighbour lists and sampled likelihood sums. Properties that hold at any
+size are checked for the rest (stable sort validity, posterior normalisation,
+argmax)."""
+import numpy as np
+import pytest
+
+from gpu_util import report, sum_tolerance
+from paper_2404_16370_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def big(oracle):
+    from paper_2404_16370_gb300 import mp
+    w = synth.outdoor_workload(n_particles=N, n_steps=2)
+    P = oracle.Params.outdoor(N)
+    normals, valid, _, covs = oracle.point_normals(w.map_points, P.r_cov, P.cov_k, P.cov_min, want_covs=True)
+    om = oracle.OracleMap(w.map_points, P, normals=normals, valid=valid)
+    params = mp.mp_default_params(mp.MP_PRESET_OUTDOOR, N)
+    ctx = mp.mp_init_map(w.map_points, params)
+    mp.mp_init_particles(ctx, N, poses=w.particles)
+    yield dict(mp=mp, w=w, P=P, om=om, ctx=ctx, covs=covs)
+    mp.mp_destroy(ctx)
+
+
+def test_map_gaussians_fullsize(big):
+    mp, ctx, om = big["mp"], big["ctx"], big["om"]
+    gv = mp.mp_get_buffer(ctx, mp.MP_BUF_MAP_VALID)
+    assert np.array_equal(gv, om.valid)
+    gn = mp.mp_get_buffer(ctx, mp.MP_BUF_MAP_NORMALS)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(len(gv), 50000, replace=False)
+    w = np.linalg.eigvalsh(big["covs"][idx].reshape(-1, 3, 3))
+    sep = (w[:, 1] - w[:, 0]) > 1e-3 * np.maximum(w[:, 2], 1e-30)
+    m = om.valid[idx].astype(bool) & sep
+    dots = np.abs(np.sum(gn[idx][m].astype(np.float64) * om.normals[idx][m], axis=1))
+    assert m.sum() > 40000 and dots.min() > 1 - 1e-6
+
+
+def test_nnf_sampled_fullsize(big):
+    mp, ctx, om = big["mp"], big["ctx"], big["om"]
+    info = mp.mp_map_info(ctx)
+    o, d, inv, off = om.geometry()
+    assert np.array_equal(info["origin"], o) and np.array_equal(info["dims"], d)
+    assert info["inv_res"] == inv and np.array_equal(info["off"], off)
+    rng = np.random.default_rng(1)
+    uni = np.stack([rng.integers(-1, d[a] + 1, 300000) for a in range(3)], -1)
+    pts = big["w"].map_points[rng.choice(len(big["w"].map_points), 200000)]
+    near = np.floor(pts * inv + off).astype(np.int64) + rng.integers(-10, 11, (200000, 3))
+    vox = np.concatenate([uni, near]).astype(np.int32)
+    g = mp.mp_nnf_query(ctx, vox)
+    r = om.nnf(vox)
+    assert np.array_equal(g, r), f"{(g != r).sum()} voxels differ"
+    assert (r >= 0).mean() > 0.3
+
+
+@pytest.fixture(scope="module")
+def stepped(big):
+    """One step of all stages but the prediction (identity odometry) on scan 1."""
+    mp, ctx = big["mp"], big["ctx"]
+    mp.mp_init_particles(ctx, N, poses=big["w"].particles)
+    mp.mp_set_step_index(ctx, 1)
+    mp.mp_set_scan(ctx, big["w"].scans[1])
+    mp.mp_run_stages(ctx, mp.MP_STAGE_ALL & ~mp.MP_STAGE_PREDICT)
+    best, best_p = mp.mp_get_posterior(ctx)
+    names = {"keys": mp.MP_BUF_KEYS, "buckets": mp.MP_BUF_BUCKETS, "sid": mp.MP_BUF_SORTED_IDS,
+             "seg": mp.MP_BUF_SEGMENTS, "ids": mp.MP_BUF_NBR_IDS, "k": mp.MP_BUF_NBR_K, "gn": mp.MP_BUF_GN,
+             "post": mp.MP_BUF_POST, "psi": mp.MP_BUF_PSI, "poses": mp.MP_BUF_POSES}
+    out = {k: mp.mp_get_buffer(ctx, b) for k, b in names.items()}
+    out.update(best=best, best_p=best_p)
+    return out
+
+
+def test_keys_and_order_fullsize(big, stepped, oracle):
+    om, P = big["om"], big["P"]
+    v = om.valid.astype(bool)
+    q, t, d = oracle.lsh_draw(P.seed, 1, om.pts[v].min(0).astype(np.float64), om.pts[v].max(0).astype(np.float64),
+                              P.lsh_sigma)
+    ref = oracle.lsh_keys(big["w"].particles, q, t, d, P)
+    ok = ref["flags"] == 0
+    assert ok.mean() > 0.9999
+    assert np.array_equal(stepped["keys"][ok], ref["keys"][ok])
+    # the GPU order is the stable order of its own buckets ...
+    assert np.array_equal(stepped["sid"], np.argsort(stepped["buckets"], kind="stable"))
+    # ... and equals the oracle's whenever no key was ambiguous
+    if ok.all():
+        s = oracle.bucket_sort(ref["buckets"])
+        assert np.array_equal(stepped["sid"], s["sorted_ids"])
+        assert np.array_equal(stepped["seg"][:, 0], s["seg_lo"]) and np.array_equal(stepped["seg"][:, 1], s["seg_hi"])
+
+
+def test_neighbour_lists_sampled_fullsize(big, stepped, oracle):
+    om, P = big["om"], big["P"]
+    v = om.valid.astype(bool)
+    q, t, d = oracle.lsh_draw(P.seed, 1, om.pts[v].min(0).astype(np.float64), om.pts[v].max(0).astype(np.float64),
+                              P.lsh_sigma)
+    ref = oracle.lsh_keys(big["w"].particles, q, t, d, P)
+    srt = oracle.bucket_sort(ref["buckets"])
+    rng = np.random.default_rng(2)
+    sub = rng.choice(N, 2000, replace=False).astype(np.int32)
+    old = np.full((N, P.K), -1, np.int32)
+    old[:, 0] = np.arange(N)
+    mg = oracle.neighbor_merge(big["w"].particles, old, srt, P, subset=sub)
+    flagged_key = ref["flags"] != 0
+    bad = 0
+    for r, i in enumerate(sub):
+        if mg["flags"][r] or flagged_key[i]:
+            continue
+        a, b = stepped["ids"][i], mg["ids"][r]
+        if set(a[a >= 0]) != set(b[b >= 0]):
+            bad += 1
+    assert bad == 0
+
+
+def test_likelihood_sampled_fullsize(big, stepped, oracle):
+    P = big["P"]
+    sc = big["w"].scans[1]
+    sn, sv, _, _ = oracle.point_normals(sc, P.r_cov, P.cov_k, P.cov_min)
+    rng = np.random.default_rng(3)
+    sub = rng.choice(N, 384, replace=False)
+    ref = oracle.likelihood(big["om"], big["w"].particles[sub], sc, sn, sv, P, amb_tol=1e-4)
+    gn = stepped["gn"][sub]
+    ok = ref["amb"] == 0
+    assert ok.mean() > 0.95
+    assert np.array_equal(gn[ok, 28].astype(np.int64), ref["n_in"][ok])
+    got = gn[:, :28].astype(np.float64)
+    want = np.concatenate([ref["H"], ref["b"], ref["loglik"][:, None]], 1)
+    msg = report("sums", np.abs(got - want)[ok], sum_tolerance(ref["absum"])[ok])
+    assert not msg, msg
+
+
+def test_posterior_properties_fullsize(stepped):
+    post = stepped["post"]
+    assert abs(post.sum() - 1) < 1e-9 and np.all(post >= 0)
+    b = int(np.argmax(post))
+    assert np.array_equal(stepped["best"], stepped["poses"][b]) and stepped["best_p"] == post[b]
+    assert np.all(np.isfinite(stepped["psi"])) and np.all(np.isfinite(stepped["poses"]))
