@@ -678,10 +678,13 @@ void or_voxel_of(void* h, const float* pose, const float* mu, int32_t v[3], floa
 // amb counts inlier decisions within amb_tol * c_max of the threshold.
 // absum (optional, np x 28): per output entry the sum of the magnitudes of
 // its terms (H 21, b 6, log-likelihood 1), the scale of its rounding error.
+// ambabs (optional, np x 28): the same sums over the ambiguous pairs only
+// (for the log-likelihood: |c_k - c_max|), i.e. how far an output can move if
+// an implementation in another precision takes the other inlier decision.
 int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const double* scan_n,
                   const uint8_t* scan_valid, i64 ns, double c_max, double eps_cov, double amb_tol,
                   double* H, double* b, double* loglik, int32_t* n_in, int32_t* amb, double* absum,
-                  int nthreads) {
+                  double* ambabs, int nthreads) {
   Map* M = (Map*)h;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -700,7 +703,7 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
       double R[9];
       quat_to_R(q, R);  // the stored quaternion as given (unit up to FP32 rounding)
       double t[3] = {P[4], P[5], P[6]};
-      double Hl[21] = {0}, bl[6] = {0}, ll = 0, ab[28] = {0};
+      double Hl[21] = {0}, bl[6] = {0}, ll = 0, ab[28] = {0}, aa[28] = {0};
       int cnt = 0, namb = 0;
       for (i64 k = 0; k < ns; ++k) {
         if (scan_valid && !scan_valid[k]) continue;
@@ -734,11 +737,18 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
         double Oe[3];
         matvec3(Om, e, Oe);
         double c = e[0] * Oe[0] + e[1] * Oe[1] + e[2] * Oe[2];
-        if (std::fabs(c - c_max) <= amb_tol * c_max) namb++;
-        if (!(c <= c_max)) { ll -= c_max; ab[27] += c_max; continue; }
-        ll -= c;
-        ab[27] += std::fabs(c);
-        cnt++;
+        const bool near = std::fabs(c - c_max) <= amb_tol * c_max;
+        const bool inl = c <= c_max;
+        if (near) { namb++; aa[27] += std::fabs(c - c_max); }
+        if (!inl) {
+          ll -= c_max;
+          ab[27] += c_max;
+          if (!near) continue;
+        } else {
+          ll -= c;
+          ab[27] += std::fabs(c);
+          cnt++;
+        }
         // J = R [ [mu]x , -I ]
         double S[9], J0[9], J[3][6];
         skew(mus, S);
@@ -752,13 +762,19 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
           for (int bb = a; bb < 6; ++bb) {
             double s = 0;
             for (int r = 0; r < 3; ++r) s += J[r][a] * OJ[r][bb];
-            Hl[H_IDX[a][bb]] += s;
-            ab[H_IDX[a][bb]] += std::fabs(s);
+            if (inl) {
+              Hl[H_IDX[a][bb]] += s;
+              ab[H_IDX[a][bb]] += std::fabs(s);
+            }
+            if (near) aa[H_IDX[a][bb]] += std::fabs(s);
           }
           double s = 0;
           for (int r = 0; r < 3; ++r) s += J[r][a] * Oe[r];
-          bl[a] += s;
-          ab[21 + a] += std::fabs(s);
+          if (inl) {
+            bl[a] += s;
+            ab[21 + a] += std::fabs(s);
+          }
+          if (near) aa[21 + a] += std::fabs(s);
         }
       }
       for (int a = 0; a < 21; ++a) H[21 * i + a] = Hl[a];
@@ -767,6 +783,7 @@ int or_likelihood(void* h, const float* poses, i64 np, const float* scan, const 
       n_in[i] = cnt;
       if (amb) amb[i] = namb;
       if (absum) for (int a = 0; a < 28; ++a) absum[28 * i + a] = ab[a];
+      if (ambabs) for (int a = 0; a < 28; ++a) ambabs[28 * i + a] = aa[a];
     }
   }
   return 0;

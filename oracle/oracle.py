@@ -76,7 +76,7 @@ def _declare(L):
     L.or_map_geometry.argtypes = [_P, _P, _P, _P, _P]
     L.or_map_nnf.argtypes = [_P, _P, _I64, _P, _INT, _INT]
     L.or_voxel_of.argtypes = [_P, _P, _P, _P, _P]
-    L.or_likelihood.argtypes = [_P, _P, _I64, _P, _P, _P, _I64, _D, _D, _D, _P, _P, _P, _P, _P, _P, _INT]
+    L.or_likelihood.argtypes = [_P, _P, _I64, _P, _P, _P, _I64, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P, _INT]
     L.or_likelihood_pairs.argtypes = [_P, _P, _P, _P, _P, _I64, _D, _D, _P, _P, _P, _P, _P, _P]
     L.or_gn_solve.argtypes = [_P, _P, _P, _I64, _D, _D, _P, _P]
     L.or_lsh_draw.argtypes = [_U64, _U64, _P, _P, _D, _P, _P, _P]
@@ -232,17 +232,19 @@ class OracleMap:
 
 
 def likelihood(m: OracleMap, poses, scan, scan_n, scan_valid, params: Params, amb_tol=1e-3, nthreads=0):
-    """H (n,21), b (n,6), loglik, n_in, amb (ambiguous inlier decisions) and
-    absum (n,28): the sum of term magnitudes of each output entry."""
+    """H (n,21), b (n,6), loglik, n_in, amb (ambiguous inlier decisions),
+    absum (n,28): the sum of term magnitudes of each output entry, and ambabs
+    (n,28): that sum over the ambiguous pairs (the room either decision has)."""
     poses = _c(poses, np.float32).reshape(-1, 7)
     scan = _c(scan, np.float32).reshape(-1, 3)
     npart = len(poses)
     H = np.zeros((npart, 21)); b = np.zeros((npart, 6)); ll = np.zeros(npart)
     n_in = np.zeros(npart, np.int32); amb = np.zeros(npart, np.int32); absum = np.zeros((npart, 28))
+    ambabs = np.zeros((npart, 28))
     lib().or_likelihood(m.h, _p(poses), npart, _p(scan), _p(_c(scan_n, np.float64)),
                         _p(_c(scan_valid, np.uint8)), len(scan), params.c_max, params.eps_cov, amb_tol,
-                        _p(H), _p(b), _p(ll), _p(n_in), _p(amb), _p(absum), nthreads)
-    return dict(H=H, b=b, loglik=ll, n_in=n_in, amb=amb, absum=absum)
+                        _p(H), _p(b), _p(ll), _p(n_in), _p(amb), _p(absum), _p(ambabs), nthreads)
+    return dict(H=H, b=b, loglik=ll, n_in=n_in, amb=amb, absum=absum, ambabs=ambabs)
 
 
 def likelihood_pairs(m: OracleMap, pose, scan, scan_n, scan_valid, params: Params):

@@ -468,7 +468,7 @@ int mp_step(mp_ctx* c, const float* scan, int32_t n_scan, const double odom_T[16
         mask &= ~MP_STAGE_PREDICT;
     if (n_scan == 0) {
         // blackout: no correction; the posterior is smoothed with a zero log-likelihood
-        mask = MP_STAGE_PREDICT | MP_STAGE_LSH | MP_STAGE_SORT | MP_STAGE_MERGE | MP_STAGE_POSTERIOR;
+        mask &= MP_STAGE_PREDICT | MP_STAGE_LSH | MP_STAGE_SORT | MP_STAGE_MERGE | MP_STAGE_POSTERIOR;
         MP_CUDA(c, cudaMemsetAsync(c->loglik, 0, sizeof(float) * (size_t)c->n, c->stream));
         MP_CUDA(c, cudaMemsetAsync(c->scan_nvalid, 0, sizeof(int32_t), c->stream));
     }

@@ -25,3 +25,16 @@ def report(name, err, tol):
         k = np.argmax(err - tol)
         return f"{name}: {bad.sum()} entries over tolerance; worst err {err.flat[k]:.3g} tol {tol.flat[k]:.3g}"
     return ""
+
+
+def check_sums(gn, ref, rel=1e-4, floor=1e-6):
+    """GPU likelihood sums (n, 29) against the oracle: every particle, with the
+    room that ambiguous inlier decisions give (a pair within 1e-4 of c_max may
+    fall either way in FP32): |gpu - ref| <= rel * sum|terms| + sum over
+    ambiguous pairs of |term|, and |inliers - ref| <= ambiguous pairs."""
+    d_in = np.abs(gn[:, 28].astype(np.int64) - ref["n_in"])
+    assert np.all(d_in <= ref["amb"]), f"inlier counts: {np.sum(d_in > ref['amb'])} particles off"
+    got = gn[:, :28].astype(np.float64)
+    want = np.concatenate([ref["H"], ref["b"], ref["loglik"][:, None]], 1)
+    tol = rel * ref["absum"] + ref["ambabs"] + floor
+    return report("H/b/loglik", np.abs(got - want), tol)

@@ -7,7 +7,7 @@ knob withholds 16 announced bytes; nothing faults or hangs)."""
 import numpy as np
 import pytest
 
-from gpu_util import pose_error, report, sum_tolerance
+from gpu_util import check_sums
 from paper_2404_16370_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -57,11 +57,7 @@ def test_ragged_likelihood(room, oracle, n, npts):
     P = room["P"]
     sn, sv, _, _ = oracle.point_normals(sc, P.r_cov, P.cov_k, P.cov_min)
     ref = oracle.likelihood(room["om"], room["w"].particles[:n], sc, sn, sv, P, amb_tol=1e-4)
-    ok = ref["amb"] == 0
-    assert np.array_equal(gn[ok, 28].astype(np.int64), ref["n_in"][ok])
-    got = np.concatenate([gn[:, :27], gn[:, 27:28]], 1).astype(np.float64)
-    want = np.concatenate([ref["H"], ref["b"], ref["loglik"][:, None]], 1)
-    msg = report("sums", np.abs(got - want)[ok], sum_tolerance(ref["absum"])[ok])
+    msg = check_sums(gn, ref)
     assert not msg, msg
 
 
@@ -210,5 +206,5 @@ def test_bounded_wait_gives_up_and_context_recovers(room, oracle):
     P = room["P"]
     sn, sv, _, _ = oracle.point_normals(sc, P.r_cov, P.cov_k, P.cov_min)
     ref = oracle.likelihood(room["om"], room["w"].particles[:n], sc, sn, sv, P, amb_tol=1e-4)
-    ok = ref["amb"] == 0
-    assert np.array_equal(gn[ok, 28].astype(np.int64), ref["n_in"][ok])
+    msg = check_sums(gn, ref)
+    assert not msg, msg

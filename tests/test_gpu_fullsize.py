@@ -9,7 +9,7 @@ argmax)."""
 import numpy as np
 import pytest
 
-from gpu_util import report, sum_tolerance
+from gpu_util import check_sums
 from paper_2404_16370_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -129,11 +129,8 @@ def test_likelihood_sampled_fullsize(big, stepped, oracle):
     ref = oracle.likelihood(big["om"], big["w"].particles[sub], sc, sn, sv, P, amb_tol=1e-4)
     gn = stepped["gn"][sub]
     ok = ref["amb"] == 0
-    assert ok.mean() > 0.95
     assert np.array_equal(gn[ok, 28].astype(np.int64), ref["n_in"][ok])
-    got = gn[:, :28].astype(np.float64)
-    want = np.concatenate([ref["H"], ref["b"], ref["loglik"][:, None]], 1)
-    msg = report("sums", np.abs(got - want)[ok], sum_tolerance(ref["absum"])[ok])
+    msg = check_sums(gn, ref)
     assert not msg, msg
 
 
