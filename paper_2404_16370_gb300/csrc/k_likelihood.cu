@@ -28,6 +28,8 @@
 // a structure of arrays in sorted order.
 #include "mp_internal.cuh"
 
+#include <cstdlib>
+
 namespace {
 
 constexpr int LK_THREADS = 128;
@@ -39,7 +41,7 @@ struct LkArgs {
     int64_t n;
     const float4* scan;
     const int32_t* nvalid;
-    const int32_t* nnf;
+    const int32_t* nnf;      // dense voxel grid of spatial-order map indices
     int nx, ny, nz;
     float inv_res, offx, offy, offz;
     const float4* rec;
@@ -80,18 +82,33 @@ __device__ __forceinline__ void lk_transform(const float R[9], float tx, float t
     qz = __fadd_rn(qtz, tz);
 }
 
-// NNF entry of a scan point under the particle pose (-1: outside or empty).
-__device__ __forceinline__ int lk_lookup(const LkArgs& A, const float R[9], float tx, float ty, float tz,
-                                         const float4& P0) {
-    float qtx, qty, qtz, qx, qy, qz;
-    lk_transform(R, tx, ty, tz, P0, qtx, qty, qtz, qx, qy, qz);
-    const int vx = floor_to_int(__fmaf_rn(qx, A.inv_res, A.offx));
-    const int vy = floor_to_int(__fmaf_rn(qy, A.inv_res, A.offy));
-    const int vz = floor_to_int(__fmaf_rn(qz, A.inv_res, A.offz));
+// Gather pipeline of one scan point: the lookup transforms it and loads its
+// NNF entry (the map index), then the map record is loaded; the arithmetic
+// consumes both.
+struct LkLook {
+    int m;        // map index (-1: outside the grid or no map point)
+    float qx, qy, qz;
+};
+
+__device__ __forceinline__ LkLook lk_lookup(const LkArgs& A, const float R[9], float tx, float ty, float tz,
+                                            const float4& P0) {
+    float qtx, qty, qtz;
+    LkLook L;
+    lk_transform(R, tx, ty, tz, P0, qtx, qty, qtz, L.qx, L.qy, L.qz);
+    const int vx = floor_to_int(__fmaf_rn(L.qx, A.inv_res, A.offx));
+    const int vy = floor_to_int(__fmaf_rn(L.qy, A.inv_res, A.offy));
+    const int vz = floor_to_int(__fmaf_rn(L.qz, A.inv_res, A.offz));
     const bool in = (unsigned)vx < (unsigned)A.nx && (unsigned)vy < (unsigned)A.ny && (unsigned)vz < (unsigned)A.nz;
-    int mm = -1;
-    if (in) mm = __ldg(A.nnf + ((vz * A.ny + vy) * A.nx + vx));
-    return mm;
+    L.m = -1;
+    if (in) L.m = __ldg(A.nnf + ((vz * A.ny + vy) * A.nx + vx));
+    return L;
+}
+
+__device__ __forceinline__ LkLook lk_none() {
+    LkLook L;
+    L.m = -1;
+    L.qx = L.qy = L.qz = 0.f;
+    return L;
 }
 
 __device__ __forceinline__ void lk_record(const LkArgs& A, int mm, float4& r0, float4& r1) {
@@ -105,10 +122,13 @@ __device__ __forceinline__ void lk_record(const LkArgs& A, int mm, float4& r0, f
 
 // One (particle, point) pair: cost, inlier test, and the map-frame sums.
 __device__ __forceinline__ void lk_accumulate(const LkArgs& A, LkAcc& S, const float R[9], float tx, float ty, float tz,
-                                              const float4& P0, const float4& P1, int mm, const float4& r0,
+                                              const float4& P0, const float4& P1, const LkLook& L, const float4& r0,
                                               const float4& r1) {
-    float qtx, qty, qtz, qx, qy, qz;
-    lk_transform(R, tx, ty, tz, P0, qtx, qty, qtz, qx, qy, qz);
+    // lever arm q~ = R mu (value path: q - t differs from the decision
+    // sequence's R mu only by the rounding of the sum)
+    const int mm = L.m;
+    const float qx = L.qx, qy = L.qy, qz = L.qz;
+    const float qtx = qx - tx, qty = qy - ty, qtz = qz - tz;
     const float ex = r0.x - qx, ey = r0.y - qy, ez = r0.z - qz;
     const float ux = R[0] * P0.w + R[1] * P1.x + R[2] * P1.y;
     const float uy = R[3] * P0.w + R[4] * P1.x + R[5] * P1.y;
@@ -164,7 +184,9 @@ __device__ __forceinline__ void lk_accumulate(const LkArgs& A, LkAcc& S, const f
     S.bv[0] -= gx; S.bv[1] -= gy; S.bv[2] -= gz;
 }
 
-__global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
+// MINB: CTAs per SM the registers must allow.
+template <int MINB>
+__global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A) {
     __shared__ __align__(128) float4 buf[2][2 * LK_CHUNK];
     __shared__ __align__(8) uint64_t bar[2];
 
@@ -212,22 +234,25 @@ __global__ void __launch_bounds__(LK_THREADS, 4) k_likelihood(const LkArgs A) {
         const int m = min(LK_CHUNK, nv - c * LK_CHUNK);
         if (active) {
             const float4* P = buf[b];
-            // software pipeline: NNF entries two points ahead, map records one
-            // point ahead, so that each gather has a whole point of arithmetic
-            // (and the other warps' work) to land in
-            int m0 = lk_lookup(A, R, tx, ty, tz, P[0]);
-            int m1 = m > 1 ? lk_lookup(A, R, tx, ty, tz, P[2]) : -1;
-            float4 ra0, ra1;
-            lk_record(A, m0, ra0, ra1);
+            // software pipeline over the two dependent gathers (NNF entry, map
+            // record): every iteration issues the NNF load of point k+2 and
+            // the record load of point k+1 before the arithmetic of point k,
+            // so each gather has a whole point of arithmetic (and the other
+            // warps' work) to land in. Invariant at the loop head: sc = point
+            // k (record loaded), sb = point k+1 (map index loaded).
+            LkLook sb = lk_none(), sc = lk_lookup(A, R, tx, ty, tz, P[0]);
+            float4 rc0, rc1;
+            lk_record(A, sc.m, rc0, rc1);
+            if (m > 1) sb = lk_lookup(A, R, tx, ty, tz, P[2]);
             for (int k = 0; k < m; ++k) {
-                const int m2 = (k + 2 < m) ? lk_lookup(A, R, tx, ty, tz, P[2 * (k + 2)]) : -1;
-                float4 rb0, rb1;
-                lk_record(A, m1, rb0, rb1);
-                lk_accumulate(A, S, R, tx, ty, tz, P[2 * k], P[2 * k + 1], m0, ra0, ra1);
-                m0 = m1;
-                m1 = m2;
-                ra0 = rb0;
-                ra1 = rb1;
+                const LkLook nb = (k + 2 < m) ? lk_lookup(A, R, tx, ty, tz, P[2 * (k + 2)]) : lk_none();
+                float4 n0, n1;
+                lk_record(A, sb.m, n0, n1);
+                lk_accumulate(A, S, R, tx, ty, tz, P[2 * k], P[2 * k + 1], sc, rc0, rc1);
+                sc = sb;
+                sb = nb;
+                rc0 = n0;
+                rc1 = n1;
             }
         }
         __syncthreads();
@@ -314,7 +339,19 @@ int mp_launch_likelihood(mp_ctx* c) {
     A.budget = c->wait_budget > 0 ? c->wait_budget : MP_WAIT_BUDGET;
     A.starve = c->starve_tx;
     A.pairs = c->pairs;
-    k_likelihood<<<grid_for(c->n, LK_THREADS), LK_THREADS, 0, c->stream>>>(A);
+    // occupancy target of the kernel (MP_LK_VARIANT overrides the default for
+    // tuning sweeps; every variant computes the same sums)
+    static int variant = -1;
+    if (variant < 0) {
+        const char* env = getenv("MP_LK_VARIANT");
+        variant = env ? atoi(env) : 0;
+    }
+    const unsigned grid = grid_for(c->n, LK_THREADS);
+    switch (variant) {
+        case 4: k_likelihood<4><<<grid, LK_THREADS, 0, c->stream>>>(A); break;
+        case 5: k_likelihood<5><<<grid, LK_THREADS, 0, c->stream>>>(A); break;
+        default: k_likelihood<6><<<grid, LK_THREADS, 0, c->stream>>>(A); break;
+    }
     MP_LAUNCHED(c);
     return MP_OK;
 }

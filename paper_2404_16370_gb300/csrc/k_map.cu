@@ -8,6 +8,7 @@
 //    the 32-byte records the likelihood kernel streams through shared memory.
 #include "mp_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -301,22 +302,63 @@ __global__ void k_nnf_build(const float4* __restrict__ pts, CellGridDev g, int n
     nnf[idx] = best;
 }
 
-__global__ void k_map_records(const float4* __restrict__ pts, const float* __restrict__ normals, int64_t n,
-                              float4* __restrict__ rec) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// Map records in spatial order: record s holds original point perm[s].
+__global__ void k_map_records(const float4* __restrict__ pts, const float* __restrict__ normals,
+                              const int32_t* __restrict__ perm, int64_t n, float4* __restrict__ rec) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int64_t i = perm[s];
     float4 p = pts[i];
-    rec[2 * i] = make_float4(p.x, p.y, p.z, normals[3 * i]);
-    rec[2 * i + 1] = make_float4(normals[3 * i + 1], normals[3 * i + 2], 0.f, 0.f);
+    rec[2 * s] = make_float4(p.x, p.y, p.z, normals[3 * i]);
+    rec[2 * s + 1] = make_float4(normals[3 * i + 1], normals[3 * i + 2], 0.f, 0.f);
 }
 
-__global__ void k_nnf_query(const int32_t* __restrict__ nnf, int nx, int ny, int nz, const int32_t* __restrict__ vox,
-                            int64_t m, int32_t* __restrict__ out) {
+// Dense NNF entries from original to spatial-order map indices.
+__global__ void k_nnf_remap(int32_t* __restrict__ nnf, int64_t nvox, const int32_t* __restrict__ inv) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nvox) return;
+    int v = nnf[i];
+    if (v >= 0) nnf[i] = inv[v];
+}
+
+// NNF values in original map indices.
+__global__ void k_nnf_query(const int32_t* __restrict__ nnf, const int32_t* __restrict__ perm, int nx, int ny, int nz,
+                            const int32_t* __restrict__ vox, int64_t m, int32_t* __restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m) return;
     int x = vox[3 * i], y = vox[3 * i + 1], z = vox[3 * i + 2];
     bool in = x >= 0 && y >= 0 && z >= 0 && x < nx && y < ny && z < nz;
-    out[i] = in ? nnf[((int64_t)z * ny + y) * nx + x] : -1;
+    int s = in ? nnf[((int64_t)z * ny + y) * nx + x] : -1;
+    out[i] = s < 0 ? -1 : perm[s];
+}
+
+// Spatial order of the map points: Morton code of their cell (side 4 voxels,
+// or larger so that 1024 cells cover the box), ties by index.
+void morton_order(const std::vector<float>& h, int64_t n, const float lo[3], const float hi[3], float cell,
+                  std::vector<int32_t>& perm) {
+    auto spread = [](uint32_t x) {
+        x &= 0x3ffu;
+        x = (x | (x << 16)) & 0x030000FFu;
+        x = (x | (x << 8)) & 0x0300F00Fu;
+        x = (x | (x << 4)) & 0x030C30C3u;
+        x = (x | (x << 2)) & 0x09249249u;
+        return x;
+    };
+    float ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    cell = std::max(cell, ext / 1023.0f);
+    std::vector<uint64_t> key((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t c[3];
+        for (int a = 0; a < 3; ++a) {
+            float f = (h[3 * i + a] - lo[a]) / cell;
+            c[a] = (uint32_t)std::min(std::max(f, 0.0f), 1023.0f);
+        }
+        uint32_t code = spread(c[0]) | (spread(c[1]) << 1) | (spread(c[2]) << 2);
+        key[(size_t)i] = ((uint64_t)code << 32) | (uint64_t)i;
+    }
+    std::sort(key.begin(), key.end());
+    perm.resize((size_t)n);
+    for (int64_t s = 0; s < n; ++s) perm[(size_t)s] = (int32_t)(key[(size_t)s] & 0xffffffffu);
 }
 
 __global__ void k_pts_from_xyz(const float* __restrict__ xyz, int64_t n, float4* __restrict__ out) {
@@ -431,19 +473,35 @@ int mp_launch_map_prepare(mp_ctx* c, const float* xyz_dev) {
     }
     if (c->nnf_voxels >= ((int64_t)1 << 31))
         return mp_fail(c, MP_EINVAL, "NNF grid of %lld voxels exceeds 2^31", (long long)c->nnf_voxels);
-    MP_CUDA(c, cudaMalloc(&c->nnf, sizeof(int32_t) * (size_t)c->nnf_voxels));
+    // dense NNF of original indices (temporary)
+    int32_t* dense = nullptr;
+    MP_CUDA(c, cudaMalloc(&dense, sizeof(int32_t) * (size_t)c->nnf_voxels));
     rc = build_cells(c, c->map_pts, c->map_valid, n, c->p.r_max * 1.001f, vlo, vhi, g, &cell_of);
-    if (rc) return rc;
+    if (rc) { cudaFree(dense); return rc; }
     float r2 = c->p.r_max * c->p.r_max;
     k_nnf_build<<<grid_for(c->nnf_voxels, 256), 256, 0, c->stream>>>(
         c->map_pts, g, c->nnf_dims[0], c->nnf_dims[1], c->nnf_voxels, c->nnf_origin[0], c->nnf_origin[1],
-        c->nnf_origin[2], c->p.nnf_res, r2, c->nnf);
+        c->nnf_origin[2], c->p.nnf_res, r2, dense);
     MP_LAUNCHED(c);
-    k_map_records<<<grid_for(n, 256), 256, 0, c->stream>>>(c->map_pts, c->map_normals, n, c->map_rec);
+    // spatial (Morton) order of the map records: the records that nearby
+    // voxels point to share cache lines
+    std::vector<int32_t> perm, inv((size_t)n);
+    morton_order(h, n, lo, hi, 4.0f * c->p.nnf_res, perm);
+    for (int64_t s = 0; s < n; ++s) inv[(size_t)perm[(size_t)s]] = (int32_t)s;
+    int32_t* inv_dev = nullptr;
+    MP_CUDA(c, cudaMalloc(&c->map_perm, sizeof(int32_t) * (size_t)n));
+    MP_CUDA(c, cudaMalloc(&inv_dev, sizeof(int32_t) * (size_t)n));
+    MP_CUDA(c, cudaMemcpyAsync(c->map_perm, perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    MP_CUDA(c, cudaMemcpyAsync(inv_dev, inv.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    k_map_records<<<grid_for(n, 256), 256, 0, c->stream>>>(c->map_pts, c->map_normals, c->map_perm, n, c->map_rec);
+    MP_LAUNCHED(c);
+    k_nnf_remap<<<grid_for(c->nnf_voxels, 256), 256, 0, c->stream>>>(dense, c->nnf_voxels, inv_dev);
     MP_LAUNCHED(c);
     MP_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->nnf = dense;
     free_cells(g);
     cudaFree(cell_of);
+    cudaFree(inv_dev);
     return MP_OK;
 }
 
@@ -470,8 +528,8 @@ int mp_launch_scan_prepare(mp_ctx* c) {
 
 int mp_launch_nnf_query(mp_ctx* c, const int32_t* vox_dev, int64_t m, int32_t* out_dev) {
     if (m == 0) return MP_OK;
-    k_nnf_query<<<grid_for(m, 256), 256, 0, c->stream>>>(c->nnf, c->nnf_dims[0], c->nnf_dims[1], c->nnf_dims[2],
-                                                         vox_dev, m, out_dev);
+    k_nnf_query<<<grid_for(m, 256), 256, 0, c->stream>>>(c->nnf, c->map_perm, c->nnf_dims[0], c->nnf_dims[1],
+                                                         c->nnf_dims[2], vox_dev, m, out_dev);
     MP_LAUNCHED(c);
     return MP_OK;
 }

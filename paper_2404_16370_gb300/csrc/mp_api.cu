@@ -135,7 +135,8 @@ void destroy(mp_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_particles(c);
-    dfree(c->map_pts); dfree(c->map_normals); dfree(c->map_valid); dfree(c->map_rec); dfree(c->nnf);
+    dfree(c->map_pts); dfree(c->map_normals); dfree(c->map_valid); dfree(c->map_rec); dfree(c->map_perm);
+    dfree(c->nnf);
     dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pts); dfree(c->scan_tmp4);
     dfree(c->scan_nvalid);
     dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->pairs);

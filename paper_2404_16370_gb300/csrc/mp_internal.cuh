@@ -36,8 +36,9 @@ struct mp_ctx {
     float4* map_pts;        // n_map: x, y, z, 0
     float* map_normals;     // n_map x 3
     uint8_t* map_valid;     // n_map
-    float4* map_rec;        // 2 per map point: (mu.xyz, n.x), (n.y, n.z, 0, 0)
-    int32_t* nnf;           // dense voxel grid, -1 = no map point within r_max
+    float4* map_rec;        // 2 per map point, in spatial (Morton) order: (mu.xyz, n.x), (n.y, n.z, 0, 0)
+    int32_t* map_perm;      // spatial order -> original index
+    int32_t* nnf;           // dense voxel grid of spatial-order map indices, -1 = none within r_max
     int32_t nnf_dims[3];
     int64_t nnf_voxels;
     float nnf_origin[3], nnf_inv_res, nnf_off[3];
