@@ -55,10 +55,16 @@ def workload_desc(nvalid=None):
     return d
 
 
-def make_workload(n_steps, n_particles=None):
+def make_workload(n_steps, n_particles=None, init="uniform"):
+    """The outdoor trajectory workload. init="tracking" replaces the uniform
+    particles by a cloud around the first ground-truth pose (0.5 m, 0.05 rad):
+    the converged regime of the filter."""
     from paper_2404_16370_gb300 import synth
-    return synth.outdoor_workload(n_particles=n_particles or N_PARTICLES, n_steps=max(n_steps, 1), n_map=N_MAP,
-                                  n_points=N_POINTS)
+    wl = synth.outdoor_workload(n_particles=n_particles or N_PARTICLES, n_steps=max(n_steps, 1), n_map=N_MAP,
+                                n_points=N_POINTS)
+    if init == "tracking":
+        wl.particles = synth.tracking_particles(wl.gt[0], len(wl.particles), seed=14)
+    return wl
 
 
 class ClockSampler:
@@ -211,7 +217,7 @@ def run_gpu(args):
     from paper_2404_16370_gb300 import mp
 
     n_steps = args.warmup + args.steps
-    wl = make_workload(n_steps)
+    wl = make_workload(n_steps, init=args.init)
     stream = torch.cuda.Stream()
     params = mp.mp_default_params(mp.MP_PRESET_OUTDOOR, N_PARTICLES)
     params.seed = 4 + rank
@@ -293,7 +299,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_desc(round(nvalid_mean, 1)),
+        "config": {**workload_desc(round(nvalid_mean, 1)), "init": args.init},
         "pair_evals_per_s": pairs_rank * world / t_max,
         "roofline": {"bound": "alu", "kernel": "k_likelihood", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": (achieved / ALU_PEAK_TFLOPS) if achieved else None,
@@ -324,6 +330,8 @@ def main():
     ap.add_argument("--sample", type=int, default=1024, help="particles per step in the reference arm's sample")
     ap.add_argument("--cpu-sample", type=int, default=4096, help="particles in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--init", default="uniform", choices=["uniform", "tracking"],
+                    help="particles uniform over the map (the benchmark) or around the true pose")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particle count (profiling runs of a smaller case; the benchmark is 2^20)")
     args = ap.parse_args()

@@ -474,6 +474,14 @@ def outdoor_particles(scene: Outdoor, n: int = 1 << 20, seed: int = 13) -> np.nd
     return poses_from_euler(xyz, yaw, pitch, roll)
 
 
+def tracking_particles(center, n: int, seed: int = 14, sigma_t: float = 0.5, sigma_r: float = 0.05) -> np.ndarray:
+    """n poses scattered around `center` (tangent noise: sigma_r rad, sigma_t m)."""
+    rng = np.random.default_rng(seed)
+    rot = Rotation.from_quat(np.asarray(center[:4], np.float64)) * Rotation.from_rotvec(rng.normal(size=(n, 3)) * sigma_r)
+    xyz = np.asarray(center[4:7], np.float64) + rng.normal(size=(n, 3)) * sigma_t
+    return np.concatenate([rot.as_quat(), xyz], 1).astype(np.float32)
+
+
 # ---------------------------------------------------------------------------
 # sensors
 # ---------------------------------------------------------------------------
