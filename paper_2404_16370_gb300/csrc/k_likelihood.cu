@@ -19,47 +19,49 @@
 //    the map frame with J~ = [ [q~]x , -I ] and rotated once per particle:
 //    H = D H~ D^T, b = D b~ with D = diag(R^T, R^T).
 //
-// Layout: one thread per particle, particles visited in the order of the LSH
-// sort (neighbouring poses share CTAs, so their NNF/map gathers share L1
-// lines once the filter has converged); scan points stream through shared
-// memory in 8 KB chunks, double-buffered with 1-D bulk copies (TMA,
-// cp.async.bulk) completing on mbarriers; every thread of a warp reads the same
-// point (broadcast). Accumulation in FP32 registers; the 29 sums are written as
-// a structure of arrays in sorted order.
+// Layout: two particles per thread on the packed FP32 pipe (f32x2 fma, mul
+// and add; each half rounds exactly as the scalar instruction, so the decision
+// sequences are unchanged and the per-pair instruction count roughly halves).
+// Every per-pair value is a float2 holding particle a in .x and particle b in
+// .y. Particles are visited in the order of the LSH sort (neighbouring poses
+// share CTAs, so their NNF and record gathers share L1 lines once the filter
+// has converged); a thread takes sorted slots p and p + 128, so each half of a
+// warp covers 32 consecutive slots. The scan streams through shared memory in
+// chunks of 256 points stored as broadcast pairs (48 bytes a point), double-
+// buffered with 1-D bulk copies (TMA, cp.async.bulk) completing on mbarriers,
+// and every thread of a warp reads the same point. The two dependent gathers
+// of a point (NNF entry, then map record) are software-pipelined: the NNF
+// entries of point k+2 and the records of point k+1 are in flight while point
+// k is accumulated. Accumulation in FP32 registers; the 29 sums of each
+// particle are written as a structure of arrays in sorted order.
 #include "mp_internal.cuh"
-
-#include <cstdlib>
 
 namespace {
 
 constexpr int LK_THREADS = 128;
-constexpr int LK_CHUNK = 256;   // points per stage: 256 x 32 B = 8 KB
+constexpr int LK_PER_CTA = 2 * LK_THREADS;
+constexpr int LK_CHUNK = 256;   // points per stage: 256 x 48 B = 12 KB
+constexpr int LK_MINB = 3;      // CTAs per SM the register budget must allow (163 registers)
 
 struct LkArgs {
     const float4* poses;
     const int32_t* order;
     int64_t n;
-    const float4* scan;
+    const float4* scan;      // 3 float4 per valid point, every value twice
     const int32_t* nvalid;
     const int32_t* nnf;      // dense voxel grid of spatial-order map indices
     int nx, ny, nz;
-    float inv_res, offx, offy, offz;
     const float4* rec;
-    float c_max, half_a, two_eps, quarter_a;
+    float c_max;
     float* gn;
     int64_t stride;
     int32_t* err;
     unsigned long long* pairs;
     long long budget;   // cycle limit of each barrier wait
     int starve;         // test knob: announce 16 bytes more than copied for chunk 0
+    // constants as pairs (both halves equal)
+    float2 inv2, offx2, offy2, offz2, magic2, m1, half2, half_a2, nhalf_a2, two_eps2, two2, quarter_a2;
 };
-
-__device__ __forceinline__ void issue_chunk(const LkArgs& A, float4* dst, uint64_t* bar, int c, int nv) {
-    int m = min(LK_CHUNK, nv - c * LK_CHUNK);
-    uint32_t bytes = (uint32_t)m * 32u;
-    mbar_expect_tx(bar, bytes + ((A.starve && c == 0) ? 16u : 0u));
-    bulk_g2s(dst, A.scan + 2 * (int64_t)c * LK_CHUNK, bytes, bar);
-}
 
 // Sums of one particle over the scan (map frame, see the file comment).
 struct LkAcc {
@@ -71,205 +73,9 @@ struct LkAcc {
     int cnt;
 };
 
-// Transformed point by the decision sequence.
-__device__ __forceinline__ void lk_transform(const float R[9], float tx, float ty, float tz, const float4& P0,
-                                             float& qtx, float& qty, float& qtz, float& qx, float& qy, float& qz) {
-    qtx = __fmaf_rn(R[2], P0.z, __fmaf_rn(R[1], P0.y, __fmul_rn(R[0], P0.x)));
-    qty = __fmaf_rn(R[5], P0.z, __fmaf_rn(R[4], P0.y, __fmul_rn(R[3], P0.x)));
-    qtz = __fmaf_rn(R[8], P0.z, __fmaf_rn(R[7], P0.y, __fmul_rn(R[6], P0.x)));
-    qx = __fadd_rn(qtx, tx);
-    qy = __fadd_rn(qty, ty);
-    qz = __fadd_rn(qtz, tz);
-}
-
-// Gather pipeline of one scan point: the lookup transforms it and loads its
-// NNF entry (the map index), then the map record is loaded; the arithmetic
-// consumes both.
-struct LkLook {
-    int m;        // map index (-1: outside the grid or no map point)
-    float qx, qy, qz;
-};
-
-__device__ __forceinline__ LkLook lk_lookup(const LkArgs& A, const float R[9], float tx, float ty, float tz,
-                                            const float4& P0) {
-    float qtx, qty, qtz;
-    LkLook L;
-    lk_transform(R, tx, ty, tz, P0, qtx, qty, qtz, L.qx, L.qy, L.qz);
-    const int vx = floor_to_int(__fmaf_rn(L.qx, A.inv_res, A.offx));
-    const int vy = floor_to_int(__fmaf_rn(L.qy, A.inv_res, A.offy));
-    const int vz = floor_to_int(__fmaf_rn(L.qz, A.inv_res, A.offz));
-    const bool in = (unsigned)vx < (unsigned)A.nx && (unsigned)vy < (unsigned)A.ny && (unsigned)vz < (unsigned)A.nz;
-    L.m = -1;
-    if (in) L.m = __ldg(A.nnf + ((vz * A.ny + vy) * A.nx + vx));
-    return L;
-}
-
-__device__ __forceinline__ LkLook lk_none() {
-    LkLook L;
-    L.m = -1;
-    L.qx = L.qy = L.qz = 0.f;
-    return L;
-}
-
-__device__ __forceinline__ void lk_record(const LkArgs& A, int mm, float4& r0, float4& r1) {
-    r0 = make_float4(0.f, 0.f, 0.f, 0.f);
-    r1 = r0;
-    if (mm >= 0) {
-        r0 = __ldg(A.rec + 2 * mm);
-        r1 = __ldg(A.rec + 2 * mm + 1);
-    }
-}
-
-// One (particle, point) pair: cost, inlier test, and the map-frame sums.
-__device__ __forceinline__ void lk_accumulate(const LkArgs& A, LkAcc& S, const float R[9], float tx, float ty, float tz,
-                                              const float4& P0, const float4& P1, const LkLook& L, const float4& r0,
-                                              const float4& r1) {
-    // lever arm q~ = R mu (value path: q - t differs from the decision
-    // sequence's R mu only by the rounding of the sum)
-    const int mm = L.m;
-    const float qx = L.qx, qy = L.qy, qz = L.qz;
-    const float qtx = qx - tx, qty = qy - ty, qtz = qz - tz;
-    const float ex = r0.x - qx, ey = r0.y - qy, ez = r0.z - qz;
-    const float ux = R[0] * P0.w + R[1] * P1.x + R[2] * P1.y;
-    const float uy = R[3] * P0.w + R[4] * P1.x + R[5] * P1.y;
-    const float uz = R[6] * P0.w + R[7] * P1.x + R[8] * P1.y;
-    const float wx = r0.w, wy = r1.x, wz = r1.y;
-    const float sg = copysignf(1.f, ux * wx + uy * wy + uz * wz);
-    const float sx = fmaf(sg, wx, ux), sy = fmaf(sg, wy, uy), sz = fmaf(sg, wz, uz);
-    const float dx = fmaf(-sg, wx, ux), dy = fmaf(-sg, wy, uy), dz = fmaf(-sg, wz, uz);
-    const float dd = dx * dx + dy * dy + dz * dz;
-    const float ls = fmaf(A.half_a, dd, A.two_eps);
-    const float ld = fmaf(-A.half_a, dd, 2.f);
-    const float rr = __fdividef(A.quarter_a, ls * ld);
-    const float as = ld * rr, ad = ls * rr;
-    const float se = sx * ex + sy * ey + sz * ez;
-    const float de = dx * ex + dy * ey + dz * ez;
-    const float ee = ex * ex + ey * ey + ez * ez;
-    const float cost = fmaf(0.5f, ee, fmaf(as * se, se, ad * de * de));
-    const bool inl = (mm >= 0) && (cost <= A.c_max);
-    S.ll -= inl ? cost : A.c_max;
-    S.cnt += inl ? 1 : 0;
-    const float h = inl ? 0.5f : 0.f;
-    const float Pw = inl ? as : 0.f, Qw = inl ? ad : 0.f;
-    const float Psx = Pw * sx, Psy = Pw * sy, Psz = Pw * sz;
-    const float Qdx = Qw * dx, Qdy = Qw * dy, Qdz = Qw * dz;
-    const float Oxx = fmaf(Psx, sx, fmaf(Qdx, dx, h));
-    const float Oyy = fmaf(Psy, sy, fmaf(Qdy, dy, h));
-    const float Ozz = fmaf(Psz, sz, fmaf(Qdz, dz, h));
-    const float Oxy = fmaf(Psx, sy, Qdx * dy);
-    const float Oxz = fmaf(Psx, sz, Qdx * dz);
-    const float Oyz = fmaf(Psy, sz, Qdy * dz);
-    const float gx = Oxx * ex + Oxy * ey + Oxz * ez;
-    const float gy = Oxy * ex + Oyy * ey + Oyz * ez;
-    const float gz = Oxz * ex + Oyz * ey + Ozz * ez;
-    // Pm = [q~]x Omega
-    const float P00 = qty * Oxz - qtz * Oxy, P01 = qty * Oyz - qtz * Oyy, P02 = qty * Ozz - qtz * Oyz;
-    const float P10 = qtz * Oxx - qtx * Oxz, P11 = qtz * Oxy - qtx * Oyz, P12 = qtz * Oxz - qtx * Ozz;
-    const float P20 = qtx * Oxy - qty * Oxx, P21 = qtx * Oyy - qty * Oxy, P22 = qtx * Oyz - qty * Oxz;
-    // H~_ww += Pm [q~]x^T ; H~_wv += Pm ; H~_vv += Omega
-    S.Hww[0] += qty * P02 - qtz * P01;
-    S.Hww[1] += qtz * P00 - qtx * P02;
-    S.Hww[2] += qtx * P01 - qty * P00;
-    S.Hww[3] += qtz * P10 - qtx * P12;
-    S.Hww[4] += qtx * P11 - qty * P10;
-    S.Hww[5] += qtx * P21 - qty * P20;
-    S.Hwv[0] += P00; S.Hwv[1] += P01; S.Hwv[2] += P02;
-    S.Hwv[3] += P10; S.Hwv[4] += P11; S.Hwv[5] += P12;
-    S.Hwv[6] += P20; S.Hwv[7] += P21; S.Hwv[8] += P22;
-    S.Hvv[0] += Oxx; S.Hvv[1] += Oxy; S.Hvv[2] += Oxz; S.Hvv[3] += Oyy; S.Hvv[4] += Oyz; S.Hvv[5] += Ozz;
-    // b~ = [ g x q~ ; -g ]
-    S.bw[0] += gy * qtz - gz * qty;
-    S.bw[1] += gz * qtx - gx * qtz;
-    S.bw[2] += gx * qty - gy * qtx;
-    S.bv[0] -= gx; S.bv[1] -= gy; S.bv[2] -= gz;
-}
-
-// MINB: CTAs per SM the registers must allow.
-template <int MINB>
-__global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A) {
-    __shared__ __align__(128) float4 buf[2][2 * LK_CHUNK];
-    __shared__ __align__(8) uint64_t bar[2];
-
-    const int64_t p = (int64_t)blockIdx.x * LK_THREADS + threadIdx.x;
-    const bool active = p < A.n;
-    const int64_t i = active ? A.order[p] : 0;
-    Quat q;
-    float t[3];
-    load_pose(A.poses, i, q, t);
-    float R[9];
-    quat_rot_exact(q, R);
-
-    const int nv = *A.nvalid;
-    const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (nchunks > 0) issue_chunk(A, buf[0], &bar[0], 0, nv);
-        if (nchunks > 1) issue_chunk(A, buf[1], &bar[1], 1, nv);
-    }
-
-    LkAcc S;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) { S.Hww[k] = 0.f; S.Hvv[k] = 0.f; }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) S.Hwv[k] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { S.bw[k] = 0.f; S.bv[k] = 0.f; }
-    S.ll = 0.f;
-    S.cnt = 0;
-
-    const float tx = t[0], ty = t[1], tz = t[2];
-    bool failed = false;
-    int c = 0;
-    for (; c < nchunks; ++c) {
-        const int b = c & 1;
-        const uint32_t parity = (uint32_t)((c >> 1) & 1);
-        bool got = mbar_wait_bounded(&bar[b], parity, A.budget);
-        if (__syncthreads_or(!got)) { failed = true; break; }
-        const int m = min(LK_CHUNK, nv - c * LK_CHUNK);
-        if (active) {
-            const float4* P = buf[b];
-            // software pipeline over the two dependent gathers (NNF entry, map
-            // record): every iteration issues the NNF load of point k+2 and
-            // the record load of point k+1 before the arithmetic of point k,
-            // so each gather has a whole point of arithmetic (and the other
-            // warps' work) to land in. Invariant at the loop head: sc = point
-            // k (record loaded), sb = point k+1 (map index loaded).
-            LkLook sb = lk_none(), sc = lk_lookup(A, R, tx, ty, tz, P[0]);
-            float4 rc0, rc1;
-            lk_record(A, sc.m, rc0, rc1);
-            if (m > 1) sb = lk_lookup(A, R, tx, ty, tz, P[2]);
-            for (int k = 0; k < m; ++k) {
-                const LkLook nb = (k + 2 < m) ? lk_lookup(A, R, tx, ty, tz, P[2 * (k + 2)]) : lk_none();
-                float4 n0, n1;
-                lk_record(A, sb.m, n0, n1);
-                lk_accumulate(A, S, R, tx, ty, tz, P[2 * k], P[2 * k + 1], sc, rc0, rc1);
-                sc = sb;
-                sb = nb;
-                rc0 = n0;
-                rc1 = n1;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && c + 2 < nchunks) issue_chunk(A, buf[b], &bar[b], c + 2, nv);
-    }
-    if (failed) {
-        if (threadIdx.x == 0) {
-            atomicOr(A.err, MP_ERR_WAIT);
-            // drain the copies still in flight (bounded)
-            for (int k = c; k < min(c + 2, nchunks); ++k)
-                mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), A.budget);
-        }
-        return;
-    }
-    if (!active) return;
-
-    // rotate the sums back to the sensor frame: blocks M -> R^T M R
+// Rotates the map-frame sums of one particle back to the sensor frame
+// (blocks M -> R^T M R, b -> R^T b) and stores the 29 outputs at sorted slot p.
+__device__ __forceinline__ void lk_store(const LkArgs& A, const float R[9], const LkAcc& S, int64_t p) {
     float Hw[3][3] = {{S.Hww[0], S.Hww[1], S.Hww[2]}, {S.Hww[1], S.Hww[3], S.Hww[4]}, {S.Hww[2], S.Hww[4], S.Hww[5]}};
     float Hc[3][3] = {{S.Hwv[0], S.Hwv[1], S.Hwv[2]}, {S.Hwv[3], S.Hwv[4], S.Hwv[5]}, {S.Hwv[6], S.Hwv[7], S.Hwv[8]}};
     float Hv[3][3] = {{S.Hvv[0], S.Hvv[1], S.Hvv[2]}, {S.Hvv[1], S.Hvv[3], S.Hvv[4]}, {S.Hvv[2], S.Hvv[4], S.Hvv[5]}};
@@ -314,6 +120,278 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
     for (int f = 0; f < MP_GN; ++f) A.gn[(int64_t)f * A.stride + p] = out[f];
 }
 
+// ---------------------------------------------------------------------------
+// Packed pair arithmetic.
+
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+struct Lk2Acc {
+    float2 Hww[6], Hwv[9], Hvv[6], bw[3], nbv[3];   // nbv = -bv
+    float2 lc;    // sum of the inlier costs
+    float2 cnt;   // inlier count
+};
+
+struct Lk2Look {
+    int ma, mb;
+    float2 qx, qy, qz;
+};
+
+__device__ __forceinline__ Lk2Look lk2_lookup(const LkArgs& A, const float2 R[9], float2 tx, float2 ty, float2 tz,
+                                              const float4* Pp) {
+    const float4 p0 = Pp[0], p1 = Pp[1];
+    const float2 mx = make_float2(p0.x, p0.y), my = make_float2(p0.z, p0.w), mz = make_float2(p1.x, p1.y);
+    Lk2Look L;
+    // decision sequence: q~ = fma(R_a2, mz, fma(R_a1, my, R_a0 mx)), q = q~ + t
+    L.qx = add2(fma2(R[2], mz, fma2(R[1], my, mul2(R[0], mx))), tx);
+    L.qy = add2(fma2(R[5], mz, fma2(R[4], my, mul2(R[3], mx))), ty);
+    L.qz = add2(fma2(R[8], mz, fma2(R[7], my, mul2(R[6], mx))), tz);
+    // voxel = floor(fma(q, 1/res, off)): round-down add of 1.5 * 2^23
+    const float2 fx = __fadd2_rd(fma2(L.qx, A.inv2, A.offx2), A.magic2);
+    const float2 fy = __fadd2_rd(fma2(L.qy, A.inv2, A.offy2), A.magic2);
+    const float2 fz = __fadd2_rd(fma2(L.qz, A.inv2, A.offz2), A.magic2);
+    const int vxa = __float_as_int(fx.x) - 0x4B400000, vxb = __float_as_int(fx.y) - 0x4B400000;
+    const int vya = __float_as_int(fy.x) - 0x4B400000, vyb = __float_as_int(fy.y) - 0x4B400000;
+    const int vza = __float_as_int(fz.x) - 0x4B400000, vzb = __float_as_int(fz.y) - 0x4B400000;
+    const bool ina = (unsigned)vxa < (unsigned)A.nx && (unsigned)vya < (unsigned)A.ny && (unsigned)vza < (unsigned)A.nz;
+    const bool inb = (unsigned)vxb < (unsigned)A.nx && (unsigned)vyb < (unsigned)A.ny && (unsigned)vzb < (unsigned)A.nz;
+    L.ma = -1;
+    L.mb = -1;
+    if (ina) L.ma = __ldg(A.nnf + ((vza * A.ny + vya) * A.nx + vxa));
+    if (inb) L.mb = __ldg(A.nnf + ((vzb * A.ny + vyb) * A.nx + vxb));
+    return L;
+}
+
+__device__ __forceinline__ Lk2Look lk2_none() {
+    Lk2Look L;
+    L.ma = L.mb = -1;
+    L.qx = L.qy = L.qz = make_float2(0.f, 0.f);
+    return L;
+}
+
+// Map record of index mm: (mu.xyz, w.x) and (w.y, w.z).
+__device__ __forceinline__ void lk2_record(const LkArgs& A, int mm, float4& r0, float2& r1) {
+    r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r1 = make_float2(0.f, 0.f);
+    if (mm >= 0) {
+        r0 = __ldg(A.rec + 2 * mm);
+        r1 = __ldg(reinterpret_cast<const float2*>(A.rec + 2 * mm + 1));
+    }
+}
+
+__device__ __forceinline__ void lk2_accumulate(const LkArgs& A, Lk2Acc& S, const float2 R[9], float2 tx, float2 ty,
+                                               float2 tz, const float4* Pp, const Lk2Look& L, const float4& ra0,
+                                               const float2& ra1, const float4& rb0, const float2& rb1) {
+    const float4 p1 = Pp[1], p2 = Pp[2];
+    const float2 nx = make_float2(p1.z, p1.w), ny = make_float2(p2.x, p2.y), nz = make_float2(p2.z, p2.w);
+    // lever arm q~ = q - t and its negative
+    const float2 qtx = fma2(A.m1, tx, L.qx), qty = fma2(A.m1, ty, L.qy), qtz = fma2(A.m1, tz, L.qz);
+    const float2 nqx = fma2(A.m1, L.qx, tx), nqy = fma2(A.m1, L.qy, ty), nqz = fma2(A.m1, L.qz, tz);
+    // residual e = mu^M - q
+    const float2 ex = make_float2(ra0.x - L.qx.x, rb0.x - L.qx.y);
+    const float2 ey = make_float2(ra0.y - L.qy.x, rb0.y - L.qy.y);
+    const float2 ez = make_float2(ra0.z - L.qz.x, rb0.z - L.qz.y);
+    // u = R n (scan normal in the map frame), w = map normal
+    const float2 ux = fma2(R[2], nz, fma2(R[1], ny, mul2(R[0], nx)));
+    const float2 uy = fma2(R[5], nz, fma2(R[4], ny, mul2(R[3], nx)));
+    const float2 uz = fma2(R[8], nz, fma2(R[7], ny, mul2(R[6], nx)));
+    const float sga = copysignf(1.f, ux.x * ra0.w + uy.x * ra1.x + uz.x * ra1.y);
+    const float sgb = copysignf(1.f, ux.y * rb0.w + uy.y * rb1.x + uz.y * rb1.y);
+    const float2 swx = make_float2(sga * ra0.w, sgb * rb0.w);
+    const float2 swy = make_float2(sga * ra1.x, sgb * rb1.x);
+    const float2 swz = make_float2(sga * ra1.y, sgb * rb1.y);
+    const float2 sx = add2(ux, swx), sy = add2(uy, swy), sz = add2(uz, swz);
+    const float2 dx = fma2(A.m1, swx, ux), dy = fma2(A.m1, swy, uy), dz = fma2(A.m1, swz, uz);
+    // closed-form Omega = I/2 + as s s^T + ad d d^T
+    const float2 dd = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+    const float2 ls = fma2(A.half_a2, dd, A.two_eps2);
+    const float2 ld = fma2(A.nhalf_a2, dd, A.two2);
+    const float2 pr = mul2(ls, ld);
+    const float2 rr = mul2(A.quarter_a2, make_float2(__fdividef(1.f, pr.x), __fdividef(1.f, pr.y)));
+    const float2 as = mul2(ld, rr), ad = mul2(ls, rr);
+    const float2 se = fma2(sz, ez, fma2(sy, ey, mul2(sx, ex)));
+    const float2 de = fma2(dz, ez, fma2(dy, ey, mul2(dx, ex)));
+    const float2 ee = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+    const float2 cost = fma2(A.half2, ee, fma2(mul2(as, se), se, mul2(mul2(ad, de), de)));
+    const bool ia = (L.ma >= 0) && (cost.x <= A.c_max);
+    const bool ib = (L.mb >= 0) && (cost.y <= A.c_max);
+    const float2 inl = make_float2(ia ? 1.f : 0.f, ib ? 1.f : 0.f);
+    S.lc = fma2(inl, cost, S.lc);
+    S.cnt = add2(S.cnt, inl);
+    const float2 h = mul2(A.half2, inl), Pw = mul2(as, inl), Qw = mul2(ad, inl);
+    const float2 Psx = mul2(Pw, sx), Psy = mul2(Pw, sy), Psz = mul2(Pw, sz);
+    const float2 Qdx = mul2(Qw, dx), Qdy = mul2(Qw, dy), Qdz = mul2(Qw, dz);
+    const float2 Oxx = fma2(Psx, sx, fma2(Qdx, dx, h));
+    const float2 Oyy = fma2(Psy, sy, fma2(Qdy, dy, h));
+    const float2 Ozz = fma2(Psz, sz, fma2(Qdz, dz, h));
+    const float2 Oxy = fma2(Psx, sy, mul2(Qdx, dy));
+    const float2 Oxz = fma2(Psx, sz, mul2(Qdx, dz));
+    const float2 Oyz = fma2(Psy, sz, mul2(Qdy, dz));
+    const float2 gx = fma2(Oxz, ez, fma2(Oxy, ey, mul2(Oxx, ex)));
+    const float2 gy = fma2(Oyz, ez, fma2(Oyy, ey, mul2(Oxy, ex)));
+    const float2 gz = fma2(Ozz, ez, fma2(Oyz, ey, mul2(Oxz, ex)));
+    // Pm = [q~]x Omega (nq = -q~ carries the minus signs)
+    const float2 P00 = fma2(qty, Oxz, mul2(nqz, Oxy)), P01 = fma2(qty, Oyz, mul2(nqz, Oyy)),
+                 P02 = fma2(qty, Ozz, mul2(nqz, Oyz));
+    const float2 P10 = fma2(qtz, Oxx, mul2(nqx, Oxz)), P11 = fma2(qtz, Oxy, mul2(nqx, Oyz)),
+                 P12 = fma2(qtz, Oxz, mul2(nqx, Ozz));
+    const float2 P20 = fma2(qtx, Oxy, mul2(nqy, Oxx)), P21 = fma2(qtx, Oyy, mul2(nqy, Oxy)),
+                 P22 = fma2(qtx, Oyz, mul2(nqy, Oxz));
+    // H~_ww += Pm [q~]x^T ; H~_wv += Pm ; H~_vv += Omega
+    S.Hww[0] = fma2(qty, P02, fma2(nqz, P01, S.Hww[0]));
+    S.Hww[1] = fma2(qtz, P00, fma2(nqx, P02, S.Hww[1]));
+    S.Hww[2] = fma2(qtx, P01, fma2(nqy, P00, S.Hww[2]));
+    S.Hww[3] = fma2(qtz, P10, fma2(nqx, P12, S.Hww[3]));
+    S.Hww[4] = fma2(qtx, P11, fma2(nqy, P10, S.Hww[4]));
+    S.Hww[5] = fma2(qtx, P21, fma2(nqy, P20, S.Hww[5]));
+    S.Hwv[0] = add2(S.Hwv[0], P00); S.Hwv[1] = add2(S.Hwv[1], P01); S.Hwv[2] = add2(S.Hwv[2], P02);
+    S.Hwv[3] = add2(S.Hwv[3], P10); S.Hwv[4] = add2(S.Hwv[4], P11); S.Hwv[5] = add2(S.Hwv[5], P12);
+    S.Hwv[6] = add2(S.Hwv[6], P20); S.Hwv[7] = add2(S.Hwv[7], P21); S.Hwv[8] = add2(S.Hwv[8], P22);
+    S.Hvv[0] = add2(S.Hvv[0], Oxx); S.Hvv[1] = add2(S.Hvv[1], Oxy); S.Hvv[2] = add2(S.Hvv[2], Oxz);
+    S.Hvv[3] = add2(S.Hvv[3], Oyy); S.Hvv[4] = add2(S.Hvv[4], Oyz); S.Hvv[5] = add2(S.Hvv[5], Ozz);
+    // b~ = [ g x q~ ; -g ]
+    S.bw[0] = fma2(gy, qtz, fma2(gz, nqy, S.bw[0]));
+    S.bw[1] = fma2(gz, qtx, fma2(gx, nqz, S.bw[1]));
+    S.bw[2] = fma2(gx, qty, fma2(gy, nqx, S.bw[2]));
+    S.nbv[0] = add2(S.nbv[0], gx); S.nbv[1] = add2(S.nbv[1], gy); S.nbv[2] = add2(S.nbv[2], gz);
+}
+
+// One half (particle a: h = 0, b: h = 1) of the packed sums as scalar sums.
+__device__ __forceinline__ LkAcc lk2_half(const LkArgs& A, const Lk2Acc& S, int h, int nv) {
+    LkAcc o;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { o.Hww[k] = h ? S.Hww[k].y : S.Hww[k].x; o.Hvv[k] = h ? S.Hvv[k].y : S.Hvv[k].x; }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) o.Hwv[k] = h ? S.Hwv[k].y : S.Hwv[k].x;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { o.bw[k] = h ? S.bw[k].y : S.bw[k].x; o.bv[k] = -(h ? S.nbv[k].y : S.nbv[k].x); }
+    const float lc = h ? S.lc.y : S.lc.x;
+    const float cnt = h ? S.cnt.y : S.cnt.x;
+    // log p = -(sum of inlier costs) - c_max * (points that are not inliers)
+    o.ll = -lc - A.c_max * (float)(nv - (int)cnt);
+    o.cnt = (int)cnt;
+    return o;
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A) {
+    __shared__ __align__(128) float4 buf[2][3 * LK_CHUNK];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    // particles a and b of this thread sit LK_THREADS apart in sorted order,
+    // so each half of a warp covers 32 consecutive sorted particles
+    const int64_t pa = (int64_t)blockIdx.x * LK_PER_CTA + threadIdx.x;
+    const int64_t pb = pa + LK_THREADS;
+    const bool acta = pa < A.n, actb = pb < A.n;
+    const int64_t ia = acta ? A.order[pa] : 0, ib = actb ? A.order[pb] : 0;
+    float2 R[9];
+    float2 tx, ty, tz;
+    {
+        Quat qa, qb;
+        float ta[3], tb[3], Ra[9], Rb[9];
+        load_pose(A.poses, ia, qa, ta);
+        load_pose(A.poses, ib, qb, tb);
+        quat_rot_exact(qa, Ra);
+        quat_rot_exact(qb, Rb);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = make_float2(Ra[k], Rb[k]);
+        tx = make_float2(ta[0], tb[0]);
+        ty = make_float2(ta[1], tb[1]);
+        tz = make_float2(ta[2], tb[2]);
+    }
+
+    const int nv = *A.nvalid;
+    const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](float4* dst, uint64_t* b, int cc) {
+        int m = min(LK_CHUNK, nv - cc * LK_CHUNK);
+        uint32_t bytes = (uint32_t)m * 48u;
+        mbar_expect_tx(b, bytes + ((A.starve && cc == 0) ? 16u : 0u));
+        bulk_g2s(dst, A.scan + 3 * (int64_t)cc * LK_CHUNK, bytes, b);
+    };
+    if (threadIdx.x == 0) {
+        if (nchunks > 0) issue(buf[0], &bar[0], 0);
+        if (nchunks > 1) issue(buf[1], &bar[1], 1);
+    }
+
+    Lk2Acc S;
+    const float2 z2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { S.Hww[k] = z2; S.Hvv[k] = z2; }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S.Hwv[k] = z2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { S.bw[k] = z2; S.nbv[k] = z2; }
+    S.lc = z2;
+    S.cnt = z2;
+
+    const bool active = acta;   // acta is false only if actb is false too
+    bool failed = false;
+    int c = 0;
+    for (; c < nchunks; ++c) {
+        const int b = c & 1;
+        const uint32_t parity = (uint32_t)((c >> 1) & 1);
+        bool got = mbar_wait_bounded(&bar[b], parity, A.budget);
+        if (__syncthreads_or(!got)) { failed = true; break; }
+        const int m = min(LK_CHUNK, nv - c * LK_CHUNK);
+        if (active) {
+            const float4* P = buf[b];
+            // software pipeline over the two dependent gathers: every
+            // iteration issues the NNF loads of point k+2 and the record loads
+            // of point k+1 before the arithmetic of point k. Invariant at the
+            // loop head: sc = point k (records loaded), sb = point k+1 (map
+            // indices loaded).
+            Lk2Look sb = lk2_none(), sc = lk2_lookup(A, R, tx, ty, tz, P);
+            float4 ra0, rb0;
+            float2 ra1, rb1;
+            lk2_record(A, sc.ma, ra0, ra1);
+            lk2_record(A, sc.mb, rb0, rb1);
+            if (m > 1) sb = lk2_lookup(A, R, tx, ty, tz, P + 3);
+            for (int k = 0; k < m; ++k) {
+                const Lk2Look nb = (k + 2 < m) ? lk2_lookup(A, R, tx, ty, tz, P + 3 * (k + 2)) : lk2_none();
+                float4 na0, nb0;
+                float2 na1, nb1;
+                lk2_record(A, sb.ma, na0, na1);
+                lk2_record(A, sb.mb, nb0, nb1);
+                lk2_accumulate(A, S, R, tx, ty, tz, P + 3 * k, sc, ra0, ra1, rb0, rb1);
+                sc = sb;
+                sb = nb;
+                ra0 = na0; ra1 = na1; rb0 = nb0; rb1 = nb1;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && c + 2 < nchunks) issue(buf[b], &bar[b], c + 2);
+    }
+    if (failed) {
+        if (threadIdx.x == 0) {
+            atomicOr(A.err, MP_ERR_WAIT);
+            for (int k = c; k < min(c + 2, nchunks); ++k)
+                mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), A.budget);
+        }
+        return;
+    }
+    float Rs[9];
+    if (acta) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Rs[k] = R[k].x;
+        lk_store(A, Rs, lk2_half(A, S, 0, nv), pa);
+    }
+    if (actb) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Rs[k] = R[k].y;
+        lk_store(A, Rs, lk2_half(A, S, 1, nv), pb);
+    }
+}
+
+
+
 }  // namespace
 
 int mp_launch_likelihood(mp_ctx* c) {
@@ -321,37 +399,31 @@ int mp_launch_likelihood(mp_ctx* c) {
     A.poses = c->poses[c->cur];
     A.order = c->sorted_ids;
     A.n = c->n;
-    A.scan = c->scan_pts;
+    A.scan = c->scan_pair;
     A.nvalid = c->scan_nvalid;
     A.nnf = c->nnf;
     A.nx = c->nnf_dims[0]; A.ny = c->nnf_dims[1]; A.nz = c->nnf_dims[2];
-    A.inv_res = c->nnf_inv_res;
-    A.offx = c->nnf_off[0]; A.offy = c->nnf_off[1]; A.offz = c->nnf_off[2];
     A.rec = c->map_rec;
-    float a = 1.f - c->p.eps_cov;
     A.c_max = c->p.c_max;
-    A.half_a = 0.5f * a;
-    A.two_eps = 2.f * c->p.eps_cov;
-    A.quarter_a = 0.25f * a;
     A.gn = c->gn;
     A.stride = c->cap;
     A.err = c->dev_error;
     A.budget = c->wait_budget > 0 ? c->wait_budget : MP_WAIT_BUDGET;
     A.starve = c->starve_tx;
     A.pairs = c->pairs;
-    // occupancy target of the kernel (MP_LK_VARIANT overrides the default for
-    // tuning sweeps; every variant computes the same sums)
-    static int variant = -1;
-    if (variant < 0) {
-        const char* env = getenv("MP_LK_VARIANT");
-        variant = env ? atoi(env) : 0;
-    }
-    const unsigned grid = grid_for(c->n, LK_THREADS);
-    switch (variant) {
-        case 4: k_likelihood<4><<<grid, LK_THREADS, 0, c->stream>>>(A); break;
-        case 5: k_likelihood<5><<<grid, LK_THREADS, 0, c->stream>>>(A); break;
-        default: k_likelihood<6><<<grid, LK_THREADS, 0, c->stream>>>(A); break;
-    }
+    const float a = 1.f - c->p.eps_cov;
+    auto pair = [](float v) { return make_float2(v, v); };
+    A.inv2 = pair(c->nnf_inv_res);
+    A.offx2 = pair(c->nnf_off[0]); A.offy2 = pair(c->nnf_off[1]); A.offz2 = pair(c->nnf_off[2]);
+    A.magic2 = pair(12582912.0f);   // 1.5 * 2^23: round-down add gives floor in the low bits
+    A.m1 = pair(-1.f);
+    A.half2 = pair(0.5f);
+    A.half_a2 = pair(0.5f * a);
+    A.nhalf_a2 = pair(-0.5f * a);
+    A.two_eps2 = pair(2.f * c->p.eps_cov);
+    A.two2 = pair(2.f);
+    A.quarter_a2 = pair(0.25f * a);
+    k_likelihood<LK_MINB><<<grid_for(c->n, LK_PER_CTA), LK_THREADS, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
     return MP_OK;
 }

@@ -236,10 +236,11 @@ __global__ void k_scan_to_float4(const float* __restrict__ raw, int n, float4* _
     if (i < n) out[i] = make_float4(raw[3 * i], raw[3 * i + 1], raw[3 * i + 2], 0.f);
 }
 
-// Order-preserving compaction of the valid scan points into 32-byte records.
+// Order-preserving compaction of the valid scan points into 48-byte records of
+// broadcast pairs (every value twice, the operand layout of the packed pipe).
 __global__ void __launch_bounds__(1024) k_scan_compact(const float* __restrict__ raw, const float* __restrict__ normals,
                                                        const uint8_t* __restrict__ valid, int n,
-                                                       float4* __restrict__ out, int32_t* __restrict__ nvalid) {
+                                                       float4* __restrict__ pair, int32_t* __restrict__ nvalid) {
     __shared__ int warp_tot[32];
     __shared__ int base_s;
     if (threadIdx.x == 0) base_s = 0;
@@ -260,8 +261,11 @@ __global__ void __launch_bounds__(1024) k_scan_compact(const float* __restrict__
         int base = base_s;
         if (f) {
             int o = base + off + in_warp;
-            out[2 * o] = make_float4(raw[3 * i], raw[3 * i + 1], raw[3 * i + 2], normals[3 * i]);
-            out[2 * o + 1] = make_float4(normals[3 * i + 1], normals[3 * i + 2], 0.f, 0.f);
+            const float mx = raw[3 * i], my = raw[3 * i + 1], mz = raw[3 * i + 2];
+            const float nx = normals[3 * i], ny = normals[3 * i + 1], nz = normals[3 * i + 2];
+            pair[3 * o] = make_float4(mx, mx, my, my);
+            pair[3 * o + 1] = make_float4(mz, mz, nx, nx);
+            pair[3 * o + 2] = make_float4(ny, ny, nz, nz);
         }
         __syncthreads();
         if (threadIdx.x == 0) base_s = base + tot;
@@ -520,7 +524,7 @@ int mp_launch_scan_prepare(mp_ctx* c) {
     k_scan_normals<<<grid_for(n, 256), 256, 0, c->stream>>>(c->scan_raw, n, r2, c->p.cov_k, c->p.cov_min, tmp,
                                                              c->scan_normals, c->scan_valid);
     MP_LAUNCHED(c);
-    k_scan_compact<<<1, 1024, 0, c->stream>>>(c->scan_raw, c->scan_normals, c->scan_valid, n, c->scan_pts,
+    k_scan_compact<<<1, 1024, 0, c->stream>>>(c->scan_raw, c->scan_normals, c->scan_valid, n, c->scan_pair,
                                               c->scan_nvalid);
     MP_LAUNCHED(c);
     return MP_OK;

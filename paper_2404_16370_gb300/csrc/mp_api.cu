@@ -137,7 +137,7 @@ void destroy(mp_ctx* c) {
     free_particles(c);
     dfree(c->map_pts); dfree(c->map_normals); dfree(c->map_valid); dfree(c->map_rec); dfree(c->map_perm);
     dfree(c->nnf);
-    dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pts); dfree(c->scan_tmp4);
+    dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pair); dfree(c->scan_tmp4);
     dfree(c->scan_nvalid);
     dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->pairs);
     for (int r = 0; r < MP_EV_RING; ++r)
@@ -303,7 +303,7 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
         if ((rc = dalloc(c, &c->scan_raw, 3 * ms))) break;
         if ((rc = dalloc(c, &c->scan_normals, 3 * ms))) break;
         if ((rc = dalloc(c, &c->scan_valid, ms))) break;
-        if ((rc = dalloc(c, &c->scan_pts, 2 * ms))) break;
+        if ((rc = dalloc(c, &c->scan_pair, 3 * ms))) break;
         if ((rc = dalloc(c, &c->scan_tmp4, ms))) break;
         if ((rc = dalloc(c, &c->scan_nvalid, 1))) break;
         if ((rc = dalloc(c, &c->scalars, 8))) break;

@@ -79,7 +79,8 @@ struct mp_ctx {
     float* scan_raw;        // max_scan x 3
     float* scan_normals;    // max_scan x 3
     uint8_t* scan_valid;    // max_scan
-    float4* scan_pts;       // 2 per valid point: (mu.xyz, n.x), (n.y, n.z, 0, 0)
+    float4* scan_pair;      // 3 per valid point, every value twice (a broadcast pair):
+                            // (mx,mx,my,my), (mz,mz,nx,nx), (ny,ny,nz,nz)
     float4* scan_tmp4;      // max_scan float4 copy of the raw scan
     int32_t* scan_nvalid;   // device scalar
 
