@@ -38,12 +38,59 @@ N_PARTICLES = 1 << 20
 N_POINTS = 8192
 N_MAP = 1_000_000
 # FP32 operations of one particle x scan-point pair in the likelihood kernel's
-# formulation (fused multiply-add = 2): transform 18, voxel 9, residual 3,
-# normal rotation 15, information matrix (closed form) 27+21, cost 22,
-# g = Omega e 15, [q]x Omega 27, Hessian/gradient accumulation 54, log-lik 1.
+# formulation (fused multiply-add = 2): transform 18, voxel 9, lever arm 3,
+# residual 3, normal rotation 15, sign and s, d 14, closed-form information
+# matrix scalars 14, cost 22, inlier log-likelihood 1, Omega 27, g = Omega e 15,
+# [q]x Omega 27, Hessian/gradient accumulation 54.
 LK_FLOPS_PER_PAIR = 222
+# One random 32-byte NNF sector from DRAM per pair: the HBM bound of the
+# likelihood while particles are spread (the 0.5 GB grid does not fit in L2).
+LK_SECTOR_BYTES_PER_PAIR = 32
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (non-tensor)
+
+
+def measured_peaks():
+    """HBM GB/s and bf16 TFLOP/s measured on this GPU type (MEASURED_PEAKS.json)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def stage_bounds_ms(n, K, pairs_per_step, hbm_gbs):
+    """Lower bound of each stage's time per step: max(bytes / HBM peak, flops /
+    ALU peak) with the algorithmic bytes and flops of one step (per particle
+    unless stated). FP64 stages use the FP64 peak."""
+    bw = hbm_gbs * 1e9
+    f32 = ALU_PEAK_TFLOPS * 1e12
+    f64 = FP64_PEAK_TFLOPS * 1e12
+    C = K
+    b = {
+        # pose in/out (2 x 32 B) + Philox noise
+        "predict": (n * 64 / bw, 0.0),
+        # 8192 points: brute-force radius kNN (N^2 distances, 8 flops) + normals
+        "scan": (N_POINTS * 64 / bw, N_POINTS * N_POINTS * 8 / f32),
+        # pose read 32 B + key/id write 8 B; SE(3) log in FP64 (~300 flops)
+        "lsh": (n * 40 / bw, n * 300 / f64),
+        # 4 radix passes of 8-byte (key, id) read + write, histogram read
+        "sort": (n * 4 * 20 / bw, 0.0),
+        # old list + window ids, (K + C) 32-byte pose gathers, list/k/d writes
+        "merge": (n * (K * 4 + C * 4 + (K + C) * 32 + K * 32) / bw, n * (K + C) * 120 / f32),
+        # GN sums 29 x 4 B in, psi 32 B out; FP64 LDL^T of a 6x6 (~250 flops)
+        "solve": (n * (29 * 4 + 32) / bw, n * 250 / f64),
+        # list ids, k, d (K x 32 B) + K psi gathers (32 B) + pose in/out + phi
+        "svgd": (n * (K * 64 + 96) / bw, n * K * 30 / f32),
+        # 10 sweeps x K x (id 4 + k 4 + p 8) + normalisation passes (5 x 8 B)
+        "posterior": (n * (10 * (K * 16 + 8) + 40) / bw, 0.0),
+    }
+    out = {k: 1e3 * max(v) for k, v in b.items()}
+    out["likelihood"] = 1e3 * max(pairs_per_step * LK_SECTOR_BYTES_PER_PAIR / bw,
+                                  pairs_per_step * LK_FLOPS_PER_PAIR / f32)
+    return out
 
 
 def workload_desc(nvalid=None):
@@ -295,6 +342,13 @@ def run_gpu(args):
     h2d = int(np.mean([n * 12 for n in n_timed_scans])) + 16 * 8 + 36 * 8
     d2h = 7 * 4 + 8
     nvalid_mean = pairs_rank / N_PARTICLES / max(lk_runs, 1)
+    hbm_gbs, hbm_src = measured_peaks()
+    pairs_step = pairs_rank / lk_runs
+    lk_s = lk_ms / 1e3 / lk_runs
+    sector_gbs = pairs_step * LK_SECTOR_BYTES_PER_PAIR / lk_s / 1e9 if lk_s > 0 else None
+    stage_meas = {k: v / max(stage_runs[k], 1) for k, v in stage_ms.items()}
+    bounds = stage_bounds_ms(N_PARTICLES, 32, pairs_step, hbm_gbs)
+    step_bound = sum(bounds.values())
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -307,7 +361,15 @@ def run_gpu(args):
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz max SM clock",
                      "flops_per_pair": LK_FLOPS_PER_PAIR, "pairs_per_launch": pairs_rank / lk_runs,
                      "avg_launch_ms": lk_ms / lk_runs},
-        "stage_ms_per_step": {k: v / max(stage_runs[k], 1) for k, v in stage_ms.items()},
+        "roofline_hbm_sector": {"bound": "hbm", "kernel": "k_likelihood", "achieved": sector_gbs, "peak": hbm_gbs,
+                                "unit": "GB/s", "frac": (sector_gbs / hbm_gbs) if sector_gbs else None,
+                                "peak_source": hbm_src,
+                                "model": "one 32-byte NNF sector from DRAM per pair (spread particles)"},
+        "roofline_step": {"bound_ms": step_bound, "measured_ms": 1e3 * t_max / args.steps,
+                          "frac": step_bound / (1e3 * t_max / args.steps),
+                          "stage_bound_ms": bounds,
+                          "model": "sum over stages of max(algorithmic bytes / HBM peak, flops / ALU peak)"},
+        "stage_ms_per_step": stage_meas,
         "e2e": {"value": steps_total / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -324,8 +386,8 @@ def main():
     global N_PARTICLES
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--sample", type=int, default=1024, help="particles per step in the reference arm's sample")
     ap.add_argument("--cpu-sample", type=int, default=4096, help="particles in the cpu_baseline sample")
