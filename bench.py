@@ -272,6 +272,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     ctx = mp.mp_init_map(wl.map_points, params, cuda_stream=stream.cuda_stream)
     init_map_s = time.perf_counter() - t0
+    mp.mp_set_precision(ctx, {"fp32": mp.MP_PREC_FP32, "bf16": mp.MP_PREC_BF16, "fp16": mp.MP_PREC_FP16}[args.precision])
     scans_dev = [torch.from_numpy(s).to(f"cuda:{local}") for s in wl.scans]
     scans_pin = [torch.from_numpy(s).pin_memory() for s in wl.scans]
     torch.cuda.synchronize()
@@ -337,7 +338,7 @@ def run_gpu(args):
     lk_runs = max(stage_runs["likelihood"], 1)
     lk_flops = LK_FLOPS_PER_PAIR * pairs_rank
     achieved = lk_flops / (lk_ms / 1e3) / 1e12 if lk_ms > 0 else None
-    traffic = traffic_from_profile()
+    traffic = traffic_from_profile() if args.precision == "fp32" else None
     n_timed_scans = [len(wl.scans[s]) for s in range(args.warmup, n_steps)]
     h2d = int(np.mean([n * 12 for n in n_timed_scans])) + 16 * 8 + 36 * 8
     d2h = 7 * 4 + 8
@@ -352,8 +353,9 @@ def run_gpu(args):
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**workload_desc(round(nvalid_mean, 1)), "init": args.init},
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}[args.precision],
+        "data": "synthetic",
+        "config": {**workload_desc(round(nvalid_mean, 1)), "init": args.init, "precision": args.precision},
         "pair_evals_per_s": pairs_rank * world / t_max,
         "roofline": {"bound": "alu", "kernel": "k_likelihood", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": (achieved / ALU_PEAK_TFLOPS) if achieved else None,
@@ -394,6 +396,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--init", default="uniform", choices=["uniform", "tracking"],
                     help="particles uniform over the map (the benchmark) or around the true pose")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="arithmetic of the likelihood stage (16-bit per-pair arithmetic, FP32 sums)")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particle count (profiling runs of a smaller case; the benchmark is 2^20)")
     args = ap.parse_args()

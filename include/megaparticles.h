@@ -200,6 +200,21 @@ int mp_map_info(mp_ctx* ctx, float origin[3], int32_t dims[3], float* inv_res, f
 int mp_set_timing(mp_ctx* ctx, int enable);
 int mp_stage_times(mp_ctx* ctx, float ms_out[9], int64_t runs_out[9], int64_t* pairs);
 
+/* Arithmetic precision of the likelihood stage (the mixed-precision form of
+ * Eq. 2-4). MP_PREC_FP32 (default): every per-pair value in FP32.
+ * MP_PREC_BF16 / MP_PREC_FP16: the scan-point transform R mu, the normal
+ * rotation, the information matrix, the cost and the Jacobian products of
+ * each (particle, point) pair are computed in packed 16-bit pairs (bf16x2 /
+ * half2); the voxel decision q = (R mu) + t, the residual mu^M - q and the
+ * Gauss-Newton sums stay FP32, and the 6x6 solve and the posterior
+ * normalisation stay FP64. Results then differ from the FP32 path by the
+ * 16-bit rounding (a voxel decision can move by one voxel; sums by ~1e-3
+ * relative). Returns MP_EINVAL for any other value. */
+#define MP_PREC_FP32 0
+#define MP_PREC_BF16 1
+#define MP_PREC_FP16 2
+int mp_set_precision(mp_ctx* ctx, int precision);
+
 /* Number of kernels this context has launched so far. */
 int mp_kernel_launches(mp_ctx* ctx, int64_t* count);
 

@@ -36,6 +36,9 @@
 // particle are written as a structure of arrays in sorted order.
 #include "mp_internal.cuh"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 namespace {
 
 constexpr int LK_THREADS = 128;
@@ -48,6 +51,7 @@ struct LkArgs {
     const int32_t* order;
     int64_t n;
     const float4* scan;      // 3 float4 per valid point, every value twice
+    const uint4* scan_h;     // 16-bit forms: 2 uint4 per valid point (broadcast pairs)
     const int32_t* nvalid;
     const int32_t* nnf;      // dense voxel grid of spatial-order map indices
     int nx, ny, nz;
@@ -392,6 +396,272 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
 
 
 
+
+// ---------------------------------------------------------------------------
+// Mixed-precision form (MP_PREC_BF16 / MP_PREC_FP16): the same two particles
+// per thread with the per-pair arithmetic in packed 16-bit pairs. R mu, the
+// normal rotation R n, the information matrix, the cost, g = Omega e and
+// [q~]x Omega run on bf16x2 / half2; the decision path (q = float(R mu) + t,
+// the voxel floor, the NNF), the residual mu^M - q and the lever arm q - t
+// stay FP32, and the per-pair products enter the FP32 sums after conversion.
+// Masking multiplies only finite values (the information-matrix scalars are
+// at most a / (8 eps)); the cost of a point without a map point may overflow
+// to +inf in half precision and is only compared, never multiplied.
+
+template <typename H2> struct Half2;
+template <> struct Half2<__nv_bfloat162> {
+    static __device__ __forceinline__ __nv_bfloat162 from(float2 v) { return __float22bfloat162_rn(v); }
+    static __device__ __forceinline__ float2 to(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+};
+template <> struct Half2<__half2> {
+    static __device__ __forceinline__ __half2 from(float2 v) { return __float22half2_rn(v); }
+    static __device__ __forceinline__ float2 to(__half2 v) { return __half22float2(v); }
+};
+template <typename H2>
+__device__ __forceinline__ H2 h2_bits(uint32_t u) {
+    H2 h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+template <typename H2>
+__device__ __forceinline__ uint32_t h2_word(H2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
+// the valid scan as 16-bit broadcast pairs: (mx,mx) (my,my) (mz,mz) (nx,nx) | (ny,ny) (nz,nz) 0 0
+template <typename H2>
+__global__ void k_scan_to_h2(const float4* __restrict__ pair, const int32_t* __restrict__ nvalid, int n,
+                             uint4* __restrict__ out) {
+    using T = Half2<H2>;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || i >= *nvalid) return;
+    const float4 a = pair[3 * i], b = pair[3 * i + 1], c = pair[3 * i + 2];
+    out[2 * i] = make_uint4(h2_word(T::from(make_float2(a.x, a.y))), h2_word(T::from(make_float2(a.z, a.w))),
+                            h2_word(T::from(make_float2(b.x, b.y))), h2_word(T::from(make_float2(b.z, b.w))));
+    out[2 * i + 1] = make_uint4(h2_word(T::from(make_float2(c.x, c.y))), h2_word(T::from(make_float2(c.z, c.w))), 0u, 0u);
+}
+
+template <typename H2>
+__device__ __forceinline__ Lk2Look lkh_lookup(const LkArgs& A, const H2 R[9], float2 tx, float2 ty, float2 tz,
+                                              const uint4* Pp) {
+    using T = Half2<H2>;
+    const uint4 p0 = Pp[0];
+    const H2 mx = h2_bits<H2>(p0.x), my = h2_bits<H2>(p0.y), mz = h2_bits<H2>(p0.z);
+    Lk2Look L;
+    L.qx = add2(T::to(__hfma2(R[2], mz, __hfma2(R[1], my, __hmul2(R[0], mx)))), tx);
+    L.qy = add2(T::to(__hfma2(R[5], mz, __hfma2(R[4], my, __hmul2(R[3], mx)))), ty);
+    L.qz = add2(T::to(__hfma2(R[8], mz, __hfma2(R[7], my, __hmul2(R[6], mx)))), tz);
+    const float2 fx = __fadd2_rd(fma2(L.qx, A.inv2, A.offx2), A.magic2);
+    const float2 fy = __fadd2_rd(fma2(L.qy, A.inv2, A.offy2), A.magic2);
+    const float2 fz = __fadd2_rd(fma2(L.qz, A.inv2, A.offz2), A.magic2);
+    const int vxa = __float_as_int(fx.x) - 0x4B400000, vxb = __float_as_int(fx.y) - 0x4B400000;
+    const int vya = __float_as_int(fy.x) - 0x4B400000, vyb = __float_as_int(fy.y) - 0x4B400000;
+    const int vza = __float_as_int(fz.x) - 0x4B400000, vzb = __float_as_int(fz.y) - 0x4B400000;
+    const bool ina = (unsigned)vxa < (unsigned)A.nx && (unsigned)vya < (unsigned)A.ny && (unsigned)vza < (unsigned)A.nz;
+    const bool inb = (unsigned)vxb < (unsigned)A.nx && (unsigned)vyb < (unsigned)A.ny && (unsigned)vzb < (unsigned)A.nz;
+    L.ma = -1;
+    L.mb = -1;
+    if (ina) L.ma = __ldg(A.nnf + ((vza * A.ny + vya) * A.nx + vxa));
+    if (inb) L.mb = __ldg(A.nnf + ((vzb * A.ny + vyb) * A.nx + vxb));
+    return L;
+}
+
+template <typename H2>
+__device__ __forceinline__ void lkh_accumulate(const LkArgs& A, Lk2Acc& S, const H2 R[9], float2 tx, float2 ty,
+                                               float2 tz, const uint4* Pp, const Lk2Look& L, const float4& ra0,
+                                               const float2& ra1, const float4& rb0, const float2& rb1) {
+    using T = Half2<H2>;
+    const uint4 p0 = Pp[0], p1 = Pp[1];
+    const H2 nx = h2_bits<H2>(p0.w), ny = h2_bits<H2>(p1.x), nz = h2_bits<H2>(p1.y);
+    const H2 half = T::from(make_float2(0.5f, 0.5f));
+    const H2 half_a = T::from(A.half_a2), nhalf_a = T::from(A.nhalf_a2), two_eps = T::from(A.two_eps2);
+    const H2 two = T::from(A.two2), quarter_a = T::from(A.quarter_a2);
+    // FP32 lever arm (and its negative) and residual
+    const float2 qtx = fma2(A.m1, tx, L.qx), qty = fma2(A.m1, ty, L.qy), qtz = fma2(A.m1, tz, L.qz);
+    const float2 nqx = fma2(A.m1, L.qx, tx), nqy = fma2(A.m1, L.qy, ty), nqz = fma2(A.m1, L.qz, tz);
+    const H2 ex = T::from(make_float2(ra0.x - L.qx.x, rb0.x - L.qx.y));
+    const H2 ey = T::from(make_float2(ra0.y - L.qy.x, rb0.y - L.qy.y));
+    const H2 ez = T::from(make_float2(ra0.z - L.qz.x, rb0.z - L.qz.y));
+    const H2 hqx = T::from(qtx), hqy = T::from(qty), hqz = T::from(qtz);
+    const H2 hnx = __hneg2(hqx), hny = __hneg2(hqy), hnz = __hneg2(hqz);
+    // u = R n, w = map normal
+    const H2 ux = __hfma2(R[2], nz, __hfma2(R[1], ny, __hmul2(R[0], nx)));
+    const H2 uy = __hfma2(R[5], nz, __hfma2(R[4], ny, __hmul2(R[3], nx)));
+    const H2 uz = __hfma2(R[8], nz, __hfma2(R[7], ny, __hmul2(R[6], nx)));
+    const H2 wx = T::from(make_float2(ra0.w, rb0.w)), wy = T::from(make_float2(ra1.x, rb1.x));
+    const H2 wz = T::from(make_float2(ra1.y, rb1.y));
+    const float2 uw = T::to(__hfma2(uz, wz, __hfma2(uy, wy, __hmul2(ux, wx))));
+    const H2 sg = T::from(make_float2(copysignf(1.f, uw.x), copysignf(1.f, uw.y)));
+    const H2 swx = __hmul2(sg, wx), swy = __hmul2(sg, wy), swz = __hmul2(sg, wz);
+    const H2 sx = __hadd2(ux, swx), sy = __hadd2(uy, swy), sz = __hadd2(uz, swz);
+    const H2 dx = __hsub2(ux, swx), dy = __hsub2(uy, swy), dz = __hsub2(uz, swz);
+    const H2 dd = __hfma2(dz, dz, __hfma2(dy, dy, __hmul2(dx, dx)));
+    const H2 ls = __hfma2(half_a, dd, two_eps);
+    const H2 ld = __hfma2(nhalf_a, dd, two);
+    const H2 rr = __hmul2(quarter_a, h2rcp(__hmul2(ls, ld)));
+    const H2 as = __hmul2(ld, rr), ad = __hmul2(ls, rr);
+    const H2 se = __hfma2(sz, ez, __hfma2(sy, ey, __hmul2(sx, ex)));
+    const H2 de = __hfma2(dz, ez, __hfma2(dy, ey, __hmul2(dx, ex)));
+    const H2 ee = __hfma2(ez, ez, __hfma2(ey, ey, __hmul2(ex, ex)));
+    const float2 cost = T::to(__hfma2(half, ee, __hfma2(__hmul2(as, se), se, __hmul2(__hmul2(ad, de), de))));
+    const bool ia = (L.ma >= 0) && (cost.x <= A.c_max);
+    const bool ib = (L.mb >= 0) && (cost.y <= A.c_max);
+    S.lc.x += ia ? cost.x : 0.f;
+    S.lc.y += ib ? cost.y : 0.f;
+    S.cnt = add2(S.cnt, make_float2(ia ? 1.f : 0.f, ib ? 1.f : 0.f));
+    const H2 inl = T::from(make_float2(ia ? 1.f : 0.f, ib ? 1.f : 0.f));
+    const H2 h = __hmul2(half, inl), Pw = __hmul2(as, inl), Qw = __hmul2(ad, inl);
+    const H2 Psx = __hmul2(Pw, sx), Psy = __hmul2(Pw, sy), Psz = __hmul2(Pw, sz);
+    const H2 Qdx = __hmul2(Qw, dx), Qdy = __hmul2(Qw, dy), Qdz = __hmul2(Qw, dz);
+    const H2 Oxx = __hfma2(Psx, sx, __hfma2(Qdx, dx, h));
+    const H2 Oyy = __hfma2(Psy, sy, __hfma2(Qdy, dy, h));
+    const H2 Ozz = __hfma2(Psz, sz, __hfma2(Qdz, dz, h));
+    const H2 Oxy = __hfma2(Psx, sy, __hmul2(Qdx, dy));
+    const H2 Oxz = __hfma2(Psx, sz, __hmul2(Qdx, dz));
+    const H2 Oyz = __hfma2(Psy, sz, __hmul2(Qdy, dz));
+    const float2 gx = T::to(__hfma2(Oxz, ez, __hfma2(Oxy, ey, __hmul2(Oxx, ex))));
+    const float2 gy = T::to(__hfma2(Oyz, ez, __hfma2(Oyy, ey, __hmul2(Oxy, ex))));
+    const float2 gz = T::to(__hfma2(Ozz, ez, __hfma2(Oyz, ey, __hmul2(Oxz, ex))));
+    // Pm = [q~]x Omega
+    const float2 P00 = T::to(__hfma2(hqy, Oxz, __hmul2(hnz, Oxy))), P01 = T::to(__hfma2(hqy, Oyz, __hmul2(hnz, Oyy))),
+                 P02 = T::to(__hfma2(hqy, Ozz, __hmul2(hnz, Oyz)));
+    const float2 P10 = T::to(__hfma2(hqz, Oxx, __hmul2(hnx, Oxz))), P11 = T::to(__hfma2(hqz, Oxy, __hmul2(hnx, Oyz))),
+                 P12 = T::to(__hfma2(hqz, Oxz, __hmul2(hnx, Ozz)));
+    const float2 P20 = T::to(__hfma2(hqx, Oxy, __hmul2(hny, Oxx))), P21 = T::to(__hfma2(hqx, Oyy, __hmul2(hny, Oxy))),
+                 P22 = T::to(__hfma2(hqx, Oyz, __hmul2(hny, Oxz)));
+    // FP32 sums
+    S.Hww[0] = fma2(qty, P02, fma2(nqz, P01, S.Hww[0]));
+    S.Hww[1] = fma2(qtz, P00, fma2(nqx, P02, S.Hww[1]));
+    S.Hww[2] = fma2(qtx, P01, fma2(nqy, P00, S.Hww[2]));
+    S.Hww[3] = fma2(qtz, P10, fma2(nqx, P12, S.Hww[3]));
+    S.Hww[4] = fma2(qtx, P11, fma2(nqy, P10, S.Hww[4]));
+    S.Hww[5] = fma2(qtx, P21, fma2(nqy, P20, S.Hww[5]));
+    S.Hwv[0] = add2(S.Hwv[0], P00); S.Hwv[1] = add2(S.Hwv[1], P01); S.Hwv[2] = add2(S.Hwv[2], P02);
+    S.Hwv[3] = add2(S.Hwv[3], P10); S.Hwv[4] = add2(S.Hwv[4], P11); S.Hwv[5] = add2(S.Hwv[5], P12);
+    S.Hwv[6] = add2(S.Hwv[6], P20); S.Hwv[7] = add2(S.Hwv[7], P21); S.Hwv[8] = add2(S.Hwv[8], P22);
+    S.Hvv[0] = add2(S.Hvv[0], T::to(Oxx)); S.Hvv[1] = add2(S.Hvv[1], T::to(Oxy)); S.Hvv[2] = add2(S.Hvv[2], T::to(Oxz));
+    S.Hvv[3] = add2(S.Hvv[3], T::to(Oyy)); S.Hvv[4] = add2(S.Hvv[4], T::to(Oyz)); S.Hvv[5] = add2(S.Hvv[5], T::to(Ozz));
+    S.bw[0] = fma2(gy, qtz, fma2(gz, nqy, S.bw[0]));
+    S.bw[1] = fma2(gz, qtx, fma2(gx, nqz, S.bw[1]));
+    S.bw[2] = fma2(gx, qty, fma2(gy, nqx, S.bw[2]));
+    S.nbv[0] = add2(S.nbv[0], gx); S.nbv[1] = add2(S.nbv[1], gy); S.nbv[2] = add2(S.nbv[2], gz);
+}
+
+template <typename H2, int MINB>
+__global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood_h(const LkArgs A) {
+    using T = Half2<H2>;
+    __shared__ __align__(128) uint4 buf[2][2 * LK_CHUNK];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int64_t pa = (int64_t)blockIdx.x * LK_PER_CTA + threadIdx.x;
+    const int64_t pb = pa + LK_THREADS;
+    const bool acta = pa < A.n, actb = pb < A.n;
+    const int64_t ia = acta ? A.order[pa] : 0, ib = actb ? A.order[pb] : 0;
+    H2 R[9];
+    float2 tx, ty, tz;
+    {
+        Quat qa, qb;
+        float ta[3], tb[3], Ra[9], Rb[9];
+        load_pose(A.poses, ia, qa, ta);
+        load_pose(A.poses, ib, qb, tb);
+        quat_rot_exact(qa, Ra);
+        quat_rot_exact(qb, Rb);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = T::from(make_float2(Ra[k], Rb[k]));
+        tx = make_float2(ta[0], tb[0]);
+        ty = make_float2(ta[1], tb[1]);
+        tz = make_float2(ta[2], tb[2]);
+    }
+
+    const int nv = *A.nvalid;
+    const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](uint4* dst, uint64_t* b, int cc) {
+        int m = min(LK_CHUNK, nv - cc * LK_CHUNK);
+        uint32_t bytes = (uint32_t)m * 32u;
+        mbar_expect_tx(b, bytes + ((A.starve && cc == 0) ? 16u : 0u));
+        bulk_g2s(dst, A.scan_h + 2 * (int64_t)cc * LK_CHUNK, bytes, b);
+    };
+    if (threadIdx.x == 0) {
+        if (nchunks > 0) issue(buf[0], &bar[0], 0);
+        if (nchunks > 1) issue(buf[1], &bar[1], 1);
+    }
+
+    Lk2Acc S;
+    const float2 z2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { S.Hww[k] = z2; S.Hvv[k] = z2; }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S.Hwv[k] = z2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { S.bw[k] = z2; S.nbv[k] = z2; }
+    S.lc = z2;
+    S.cnt = z2;
+
+    bool failed = false;
+    int c = 0;
+    for (; c < nchunks; ++c) {
+        const int b = c & 1;
+        const uint32_t parity = (uint32_t)((c >> 1) & 1);
+        bool got = mbar_wait_bounded(&bar[b], parity, A.budget);
+        if (__syncthreads_or(!got)) { failed = true; break; }
+        const int m = min(LK_CHUNK, nv - c * LK_CHUNK);
+        if (acta) {
+            const uint4* P = buf[b];
+            // the same two-gather software pipeline as the FP32 form
+            Lk2Look sb = lk2_none(), sc = lkh_lookup<H2>(A, R, tx, ty, tz, P);
+            float4 ra0, rb0;
+            float2 ra1, rb1;
+            lk2_record(A, sc.ma, ra0, ra1);
+            lk2_record(A, sc.mb, rb0, rb1);
+            if (m > 1) sb = lkh_lookup<H2>(A, R, tx, ty, tz, P + 2);
+            for (int k = 0; k < m; ++k) {
+                const Lk2Look nb = (k + 2 < m) ? lkh_lookup<H2>(A, R, tx, ty, tz, P + 2 * (k + 2)) : lk2_none();
+                float4 na0, nb0;
+                float2 na1, nb1;
+                lk2_record(A, sb.ma, na0, na1);
+                lk2_record(A, sb.mb, nb0, nb1);
+                lkh_accumulate<H2>(A, S, R, tx, ty, tz, P + 2 * k, sc, ra0, ra1, rb0, rb1);
+                sc = sb;
+                sb = nb;
+                ra0 = na0; ra1 = na1; rb0 = nb0; rb1 = nb1;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && c + 2 < nchunks) issue(buf[b], &bar[b], c + 2);
+    }
+    if (failed) {
+        if (threadIdx.x == 0) {
+            atomicOr(A.err, MP_ERR_WAIT);
+            for (int k = c; k < min(c + 2, nchunks); ++k)
+                mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), A.budget);
+        }
+        return;
+    }
+    // the FP32 rotation of each particle for the sums' frame change
+    float Rs[9];
+    Quat q;
+    float t[3];
+    if (acta) {
+        load_pose(A.poses, ia, q, t);
+        quat_rot_exact(q, Rs);
+        lk_store(A, Rs, lk2_half(A, S, 0, nv), pa);
+    }
+    if (actb) {
+        load_pose(A.poses, ib, q, t);
+        quat_rot_exact(q, Rs);
+        lk_store(A, Rs, lk2_half(A, S, 1, nv), pb);
+    }
+}
+
 }  // namespace
 
 int mp_launch_likelihood(mp_ctx* c) {
@@ -423,7 +693,25 @@ int mp_launch_likelihood(mp_ctx* c) {
     A.two_eps2 = pair(2.f * c->p.eps_cov);
     A.two2 = pair(2.f);
     A.quarter_a2 = pair(0.25f * a);
-    k_likelihood<LK_MINB><<<grid_for(c->n, LK_PER_CTA), LK_THREADS, 0, c->stream>>>(A);
+    A.scan_h = c->scan_h2;
+    const unsigned grid = grid_for(c->n, LK_PER_CTA);
+    if (c->precision == MP_PREC_BF16 || c->precision == MP_PREC_FP16) {
+        if (c->n_scan > 0) {
+            if (c->precision == MP_PREC_BF16)
+                k_scan_to_h2<__nv_bfloat162><<<grid_for(c->n_scan, 256), 256, 0, c->stream>>>(
+                    c->scan_pair, c->scan_nvalid, c->n_scan, c->scan_h2);
+            else
+                k_scan_to_h2<__half2><<<grid_for(c->n_scan, 256), 256, 0, c->stream>>>(c->scan_pair, c->scan_nvalid,
+                                                                                        c->n_scan, c->scan_h2);
+            MP_LAUNCHED(c);
+        }
+        if (c->precision == MP_PREC_BF16)
+            k_likelihood_h<__nv_bfloat162, LK_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
+        else
+            k_likelihood_h<__half2, LK_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
+    } else {
+        k_likelihood<LK_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
+    }
     MP_LAUNCHED(c);
     return MP_OK;
 }

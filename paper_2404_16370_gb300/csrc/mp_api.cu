@@ -137,7 +137,7 @@ void destroy(mp_ctx* c) {
     free_particles(c);
     dfree(c->map_pts); dfree(c->map_normals); dfree(c->map_valid); dfree(c->map_rec); dfree(c->map_perm);
     dfree(c->nnf);
-    dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pair); dfree(c->scan_tmp4);
+    dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pair); dfree(c->scan_h2); dfree(c->scan_tmp4);
     dfree(c->scan_nvalid);
     dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->pairs);
     for (int r = 0; r < MP_EV_RING; ++r)
@@ -304,6 +304,7 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
         if ((rc = dalloc(c, &c->scan_normals, 3 * ms))) break;
         if ((rc = dalloc(c, &c->scan_valid, ms))) break;
         if ((rc = dalloc(c, &c->scan_pair, 3 * ms))) break;
+        if ((rc = dalloc(c, &c->scan_h2, 2 * ms))) break;
         if ((rc = dalloc(c, &c->scan_tmp4, ms))) break;
         if ((rc = dalloc(c, &c->scan_nvalid, 1))) break;
         if ((rc = dalloc(c, &c->scalars, 8))) break;
@@ -728,6 +729,14 @@ int mp_debug_set(mp_ctx* c, int what, int64_t value) {
         case MP_DEBUG_STARVE_TX: c->starve_tx = value ? 1 : 0; return MP_OK;
     }
     return mp_fail(c, MP_EINVAL, "unknown debug knob %d", what);
+}
+
+int mp_set_precision(mp_ctx* c, int precision) {
+    if (!c) return MP_EINVAL;
+    if (precision != MP_PREC_FP32 && precision != MP_PREC_BF16 && precision != MP_PREC_FP16)
+        return mp_fail(c, MP_EINVAL, "unknown precision %d", precision);
+    c->precision = precision;
+    return MP_OK;
 }
 
 int mp_kernel_launches(mp_ctx* c, int64_t* count) {

@@ -112,6 +112,8 @@ struct mp_ctx {
     size_t host_tmp_bytes;
 
     // test knobs of the failure path
+    int precision;           // MP_PREC_* of the likelihood stage
+    uint4* scan_h2;          // 2 per valid point: the scan as 16-bit broadcast pairs (precision != FP32)
     long long wait_budget;   // cycles; 0 = MP_WAIT_BUDGET
     int starve_tx;
 };

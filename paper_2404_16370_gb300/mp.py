@@ -94,10 +94,11 @@ def lib():
         L.mp_set_timing.argtypes = [V, C.c_int]
         L.mp_stage_times.argtypes = [V, P, P, C.POINTER(I64)]
         L.mp_kernel_launches.argtypes = [V, C.POINTER(I64)]
+        L.mp_set_precision.argtypes = [V, C.c_int]
         for f in ("mp_default_params", "mp_init_map", "mp_init_particles", "mp_step", "mp_get_posterior", "mp_destroy",
                   "mp_set_scan", "mp_set_odometry", "mp_run_stages", "mp_set_step_index", "mp_buffer_size",
                   "mp_get_buffer", "mp_set_buffer", "mp_nnf_query", "mp_map_info", "mp_set_timing",
-                  "mp_stage_times", "mp_kernel_launches"):
+                  "mp_stage_times", "mp_kernel_launches", "mp_set_precision"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -296,3 +297,12 @@ def mp_kernel_launches(ctx) -> int:
     n = C.c_int64()
     _check(lib().mp_kernel_launches(ctx, C.byref(n)), ctx)
     return int(n.value)
+
+
+MP_PREC_FP32, MP_PREC_BF16, MP_PREC_FP16 = 0, 1, 2
+
+
+def mp_set_precision(ctx, precision):
+    """Arithmetic precision of the likelihood stage: MP_PREC_FP32 (default),
+    MP_PREC_BF16 or MP_PREC_FP16 (16-bit per-pair arithmetic, FP32 sums)."""
+    _check(lib().mp_set_precision(ctx, int(precision)), ctx)

@@ -1,0 +1,90 @@
+"""The mixed-precision likelihood (MP_PREC_BF16 / MP_PREC_FP16: 16-bit per-pair
+arithmetic, FP32 sums, FP64 solve and normalisation) on the 10 x 10 x 3 m box
+room, against the FP64 oracle.
+
+The 16-bit forms round the scan-point transform before the voxel decision, so
+a pair can take a neighbouring voxel's map point; their error is measured
+per particle as |gpu - oracle| / sum_k |term_k| (the scale of the sums) and
+bounded, and the filter must still localise as the FP32 path does."""
+import numpy as np
+import pytest
+
+from paper_2404_16370_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N = 4096
+PRECISIONS = {"bf16": 1, "fp16": 2}
+# bounds of the per-particle relative error (median and 99th percentile of the
+# log-likelihood, median of H and of b entries), a few times the measured
+# values: bf16 keeps 8 mantissa bits, fp16 11
+BOUNDS = {"bf16": (1e-2, 1e-1, 2e-2, 4e-2), "fp16": (2e-3, 2e-2, 2e-3, 5e-3)}
+
+
+@pytest.fixture(scope="module")
+def room(oracle):
+    from paper_2404_16370_gb300 import mp
+    w = synth.box_room_workload(n_particles=N)
+    P = oracle.Params.box_room(N)
+    om = oracle.OracleMap(w.map_points, P)
+    return dict(mp=mp, w=w, P=P, om=om)
+
+
+def near_truth(gt, n, seed=21):
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(seed)
+    rot = Rotation.from_quat(gt[:4].astype(np.float64)) * Rotation.from_rotvec(rng.normal(size=(n, 3)) * 0.05)
+    return np.concatenate([rot.as_quat(), gt[4:] + rng.normal(size=(n, 3)) * 0.1], 1).astype(np.float32)
+
+
+def gn_of(room, poses, precision):
+    mp = room["mp"]
+    ctx = mp.mp_init_map(room["w"].map_points, mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, N))
+    try:
+        mp.mp_set_precision(ctx, precision)
+        mp.mp_init_particles(ctx, N, poses=poses)
+        mp.mp_set_scan(ctx, room["w"].scans[0])
+        mp.mp_run_stages(ctx, mp.MP_STAGE_SCAN | mp.MP_STAGE_LIKELIHOOD)
+        return mp.mp_get_buffer(ctx, mp.MP_BUF_GN)
+    finally:
+        mp.mp_destroy(ctx)
+
+
+def rel_errors(gn, ref):
+    want = np.concatenate([ref["H"], ref["b"], ref["loglik"][:, None]], 1)
+    return np.abs(gn[:, :28].astype(np.float64) - want) / (ref["absum"] + 1e-6)
+
+
+@pytest.mark.parametrize("name", sorted(PRECISIONS))
+def test_likelihood_error_16bit(room, oracle, name):
+    P, w = room["P"], room["w"]
+    sn, sv, _, _ = oracle.point_normals(w.scans[0], P.r_cov, P.cov_k, P.cov_min)
+    for label, poses in (("uniform", w.particles), ("near truth", near_truth(w.gt[0], N))):
+        ref = oracle.likelihood(room["om"], poses, w.scans[0], sn, sv, P, amb_tol=1e-4)
+        e32 = rel_errors(gn_of(room, poses, 0), ref)
+        e16 = rel_errors(gn_of(room, poses, PRECISIONS[name]), ref)
+        med_ll, p99_ll = np.median(e16[:, 27]), np.quantile(e16[:, 27], 0.99)
+        med_h, med_b = np.median(e16[:, :21]), np.median(e16[:, 21:27])
+        print(f"\n{name} {label}: rel. error of log-lik median {med_ll:.2e} p99 {p99_ll:.2e}; "
+              f"H median {med_h:.2e}; b median {med_b:.2e} (FP32: log-lik median {np.median(e32[:, 27]):.2e})")
+        # the FP32 path stays at its own rounding scale
+        assert np.median(e32[:, 27]) < 1e-5
+        b_ll, b_p99, b_h, b_b = BOUNDS[name]
+        assert med_ll < b_ll and p99_ll < b_p99
+        assert med_h < b_h and med_b < b_b
+
+
+def test_filter_localises_16bit():
+    """Time to localise (first step whose representative state is within 0.3 m
+    and 3 degrees of the truth) over 20 seeded box-room trials of 30 steps:
+    the 16-bit forms localise about as often as the FP32 form (a trial's
+    outcome depends on the rounding through the filter's chaotic dynamics,
+    so the comparison is over trials, not per trial)."""
+    from paper_2404_16370_gb300 import localise
+    room, trials = localise.make_trials(20, N)
+    res = {p: localise.summarise(localise.run(room, trials, p, 30)) for p in ("fp32", "bf16", "fp16")}
+    for p, r in res.items():
+        print(f"\n{p}: localised {r['localised']}/20, median time to localise {r['time_to_localise_median']} steps")
+    assert res["fp32"]["success_rate"] >= 0.6
+    for p in ("bf16", "fp16"):
+        assert res[p]["success_rate"] >= res["fp32"]["success_rate"] - 0.2, p
