@@ -1047,18 +1047,33 @@ void or_neighbor_merge(const float* poses, i64 np, const int32_t* old_ids, int K
 // phi_i = sum_j (k_ij psi_j + grad_{T_j} k(T_i, T_j)) / sum_j k_ij over the
 // list of i, with grad_{T_j} k = -2 k_ij W^K d_ij (d_ij in T_i's tangent
 // space, first order in the perturbation of T_j); T_i <- T_i exp(phi_i).
+// pinv (optional, np x 36 row-major): the repulsive sum of particle i is
+// multiplied by pinv_i (a Stein variational Newton reading that scales the
+// repulsion like the Gauss-Newton steps psi_j; not the paper's printed form).
 void or_svgd(const float* poses, i64 np, const int32_t* ids, const double* kk, const double* dd, int K,
-             const double* psi, double sr, double st, double* phi, double* poses_out) {
+             const double* psi, double sr, double st, const double* pinv, double* phi, double* poses_out) {
   double W[6] = {sr, sr, sr, st, st, st};
   for (i64 i = 0; i < np; ++i) {
-    double num[6] = {0}, den = 0;
+    double att[6] = {0}, rep[6] = {0}, den = 0;
     for (int slot = 0; slot < K; ++slot) {
       i64 o = i * K + slot;
       int32_t j = ids[o];
       if (j < 0) continue;
       double k = kk[o];
       den += k;
-      for (int a = 0; a < 6; ++a) num[a] += k * psi[6 * j + a] - 2.0 * k * W[a] * dd[o * 6 + a];
+      for (int a = 0; a < 6; ++a) {
+        att[a] += k * psi[6 * j + a];
+        rep[a] += -2.0 * k * W[a] * dd[o * 6 + a];
+      }
+    }
+    double num[6];
+    for (int a = 0; a < 6; ++a) {
+      double r = rep[a];
+      if (pinv) {
+        r = 0;
+        for (int c = 0; c < 6; ++c) r += pinv[36 * i + 6 * a + c] * rep[c];
+      }
+      num[a] = att[a] + r;
     }
     double ph[6];
     for (int a = 0; a < 6; ++a) ph[a] = den > 0 ? num[a] / den : 0.0;

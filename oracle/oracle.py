@@ -83,7 +83,7 @@ def _declare(L):
     L.or_lsh_keys.argtypes = [_P, _I64, _P, _P, _P, _D, _D, _D, _INT, _P, _P, _P, _P]
     L.or_bucket_sort.argtypes = [_P, _I64, _P, _P, _P, _P]
     L.or_neighbor_merge.argtypes = [_P, _I64, _P, _INT, _INT, _P, _P, _P, _P, _D, _D, _D, _P, _I64, _P, _P, _P, _P, _INT]
-    L.or_svgd.argtypes = [_P, _I64, _P, _P, _P, _INT, _P, _D, _D, _P, _P]
+    L.or_svgd.argtypes = [_P, _I64, _P, _P, _P, _INT, _P, _D, _D, _P, _P, _P]
     L.or_posterior.argtypes = [_P, _P, _I64, _P, _P, _INT, _INT, _P, _P, _P]
     L.or_cholesky6.argtypes = [_P, _P]
     L.or_predict_noise.argtypes = [_I64, _U64, _U64, _P]
@@ -126,6 +126,7 @@ class Params:
     post_iters: int = 10      # Eq. 11 iterations (Sec. III-D: e.g. 10)
     nb_log2: int = 12         # log2 of the number of LSH buckets
     seed: int = 4
+    svgd_precond: int = 0     # 1: repulsion times (H + lambda diag H + eps I)^-1 (not the printed Eq. 6)
 
     @staticmethod
     def box_room(n_particles: int = 4096) -> "Params":
@@ -318,14 +319,33 @@ def neighbor_merge(poses, old_ids, sorting, params: Params, tie_tol=3e-5, nthrea
     return dict(ids=ids, k=kk, d=dd, flags=flags)
 
 
-def svgd(poses, ids, kk, dd, psi, params: Params):
+def svgd(poses, ids, kk, dd, psi, params: Params, pinv=None):
+    """Eq. 5-6; pinv (n, 6, 6), when given, multiplies each particle's
+    repulsive sum (the preconditioned reading, see svgd_precond_matrices)."""
     poses = _c(poses, np.float32).reshape(-1, 7)
     npart = len(poses)
     K = np.asarray(ids).shape[1]
     phi = np.zeros((npart, 6)); out = np.zeros((npart, 7))
+    pv = None if pinv is None else _c(pinv, np.float64).reshape(npart, 36)
     lib().or_svgd(_p(poses), npart, _p(_c(ids, np.int32)), _p(_c(kk, np.float64)), _p(_c(dd, np.float64)), K,
-                  _p(_c(psi, np.float64)), params.sigma_r, params.sigma_t, _p(phi), _p(out))
+                  _p(_c(psi, np.float64)), params.sigma_r, params.sigma_t, _p(pv), _p(phi), _p(out))
     return phi, out
+
+
+def svgd_precond_matrices(H, ok, params: Params):
+    """(H + lambda diag H + eps I)^-1 of each particle whose Gauss-Newton step
+    was taken (ok), zero otherwise; H given as its 21 upper-triangle entries."""
+    H = np.asarray(H, np.float64)
+    n = len(H)
+    iu = np.triu_indices(6)
+    out = np.zeros((n, 6, 6))
+    for i in np.nonzero(np.asarray(ok))[0]:
+        A = np.zeros((6, 6))
+        A[iu] = H[i]
+        A = A + np.triu(A, 1).T
+        A = A + params.lam * np.diag(np.diag(A)) + params.eps_damp * np.eye(6)
+        out[i] = np.linalg.inv(A)
+    return out
 
 
 def posterior(logprior, loglik, ids, kk, iters):
@@ -435,7 +455,8 @@ class OracleFilter:
             out.update(H=lk["H"], b=lk["b"], loglik=lk["loglik"], n_in=lk["n_in"], amb=lk["amb"])
             # particle state update (Eq. 4-6)
             psi, ok = gn_solve(lk["H"], lk["b"], lk["n_in"], P)
-            phi, newp = svgd(poses, mg["ids"], mg["k"], mg["d"], psi, P)
+            pinv = svgd_precond_matrices(lk["H"], ok, P) if P.svgd_precond else None
+            phi, newp = svgd(poses, mg["ids"], mg["k"], mg["d"], psi, P, pinv)
             out.update(psi=psi, phi=phi, new_poses=newp)
             loglik = lk["loglik"]
         else:

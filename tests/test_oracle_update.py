@@ -74,6 +74,42 @@ def test_all_pairs_svgd(oracle):
         assert np.allclose(mat(out[i]), Ts[i] @ expm(hat(num / den)), atol=1e-9)
 
 
+def _all_pairs_case(oracle, n=7, seed=1):
+    rng = np.random.default_rng(seed)
+    rot = Rotation.from_rotvec(rng.normal(size=(n, 3)) * 0.2)
+    poses = np.concatenate([rot.as_quat(), rng.normal(size=(n, 3)) * 0.4], 1).astype(np.float32)
+    P = oracle.Params(alpha=0.0, K=n, C=n, nb_log2=3)
+    srt = oracle.bucket_sort(np.zeros(n, np.uint32))
+    mg = oracle.neighbor_merge(poses, None, srt, P)
+    psi = rng.normal(size=(n, 6)) * 0.1
+    return poses, P, mg, psi
+
+
+def test_preconditioned_repulsion_limits(oracle):
+    """The preconditioned reading reduces to Eq. 6 as printed when every
+    damped Hessian is the identity, scales the repulsion by 1/s when it is s I,
+    and leaves the attraction (sum_j k_ij psi_j) untouched."""
+    poses, P, mg, psi = _all_pairs_case(oracle)
+    n = len(poses)
+    phi_lit, _ = oracle.svgd(poses, mg["ids"], mg["k"], mg["d"], psi, P)
+    # H with H + lambda diag H + eps I = I
+    h = (1.0 - P.eps_damp) / (1.0 + P.lam)
+    H = np.zeros((n, 21))
+    H[:, [0, 6, 11, 15, 18, 20]] = h
+    pinv = oracle.svgd_precond_matrices(H, np.ones(n, np.int32), P)
+    assert np.allclose(pinv, np.eye(6), atol=1e-14)
+    phi_id, _ = oracle.svgd(poses, mg["ids"], mg["k"], mg["d"], psi, P, pinv)
+    assert np.allclose(phi_id, phi_lit, atol=1e-14)
+    # the attraction alone: no repulsion (zero preconditioner)
+    phi_att, _ = oracle.svgd(poses, mg["ids"], mg["k"], mg["d"], psi, P, np.zeros((n, 6, 6)))
+    for s in (0.5, 4.0):
+        phi_s, _ = oracle.svgd(poses, mg["ids"], mg["k"], mg["d"], psi, P, np.broadcast_to(np.eye(6) / s, (n, 6, 6)))
+        assert np.allclose(phi_s - phi_att, (phi_lit - phi_att) / s, atol=1e-14)
+    # particles without a Gauss-Newton step get no repulsion
+    pinv0 = oracle.svgd_precond_matrices(H, np.zeros(n, np.int32), P)
+    assert not pinv0.any()
+
+
 @pytest.mark.parametrize("scale", [1e-2, 3e-3])
 def test_kernel_gradient_fd(oracle, scale):
     # grad_{T_j} k(T_i, T_j) for a right perturbation T_j exp(h e_a) equals
