@@ -69,6 +69,13 @@ typedef struct mp_params {
     int32_t n_buckets_log2;
     int32_t max_scan;
     uint64_t seed;
+    /* 0 (default): the SVGD update of Eq. 6 as printed. 1: the repulsive sum
+     * of particle i is multiplied by (H_i + lambda diag H_i + eps I)^-1, the
+     * matrix of its own Gauss-Newton step, so that it scales like the steps
+     * psi_j it is added to (a Stein variational Newton reading; not the
+     * paper's printed update); a particle without a step (fewer than 6
+     * inliers or a non-positive pivot) gets no repulsion. */
+    int32_t svgd_precond;
 } mp_params;
 
 #define MP_PRESET_BOX_ROOM 0   /* 0.1 m NNF, r_max 1 m, K = C = 16           */

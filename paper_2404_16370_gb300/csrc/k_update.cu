@@ -6,6 +6,8 @@
 //  * k_svgd     Sec. III-C, Eq. 5-6: phi_i = sum_j (k_ij psi_j - 2 k_ij W d_ij) /
 //               sum_j k_ij over the list of i; T_i <- T_i exp(phi_i). A group
 //               of lanes per particle (one per list slot), shuffle reductions.
+//               With svgd_precond the repulsive sum is multiplied by the
+//               particle's damped Gauss-Newton inverse, which k_solve stores.
 //  * k_init     uniform particle draws (Sec. IV-A).
 //  * pose (un)packing between the ABI layout (7 floats) and 2 x float4.
 #include "mp_internal.cuh"
@@ -65,7 +67,7 @@ __global__ void k_predict(const PredArgs A) {
 
 __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int32_t* __restrict__ order, int64_t n,
                         double lambda, double eps, float* __restrict__ psi, float* __restrict__ loglik,
-                        int32_t* __restrict__ n_in) {
+                        int32_t* __restrict__ n_in, float* __restrict__ pinv) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
     int64_t i = order[p];
@@ -123,21 +125,53 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
     }
 #pragma unroll
     for (int r = 0; r < 6; ++r) psi[i * 8 + r] = good ? (float)x[r] : 0.f;
+    if (pinv) {
+        // the damped matrix's inverse from the same factors, column by column
+        // (upper triangle stored); zero when no step was taken
+        int oo = 0;
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+            double z[6];
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                double v = r == cc ? 1.0 : 0.0;
+#pragma unroll
+                for (int k = 0; k < r; ++k) v -= A[r][k] * z[k];
+                z[r] = v;
+            }
+#pragma unroll
+            for (int r = 0; r < 6; ++r) z[r] = good ? z[r] / A[r][r] : 0.0;
+#pragma unroll
+            for (int r = 5; r >= 0; --r) {
+                double v = z[r];
+#pragma unroll
+                for (int k = r + 1; k < 6; ++k) v -= A[k][r] * z[k];
+                z[r] = v;
+            }
+#pragma unroll
+            for (int r = 0; r <= cc; ++r) pinv[i * 24 + oo++] = good ? (float)z[r] : 0.f;
+        }
+    }
     loglik[i] = ll;
     n_in[i] = cnt;
 }
 
 // G lanes per particle (G = power of two >= K, <= 32)
-template <int G>
+template <int G, bool PRE>
 __global__ void __launch_bounds__(256) k_svgd(float4* __restrict__ poses, int64_t n, int K,
                                               const int32_t* __restrict__ ids, const float* __restrict__ kk,
                                               const float* __restrict__ dd, const float* __restrict__ psi, float wr,
-                                              float wt, float* __restrict__ phi_out) {
+                                              float wt, const float* __restrict__ pinv, float* __restrict__ phi_out) {
+    // PRE: the attraction (6), the repulsion (6) and the kernel sum are
+    // reduced apart, and the repulsion is multiplied by pinv_i
+    constexpr int NA = PRE ? 13 : 7;
     int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t i = gt / G;
     int l = (int)(gt % G);
     bool active = i < n;
-    float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    float acc[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) acc[a] = 0.f;
     if (active && l < K) {
         int64_t o = i * K + l;
         int j = ids[o];
@@ -150,20 +184,42 @@ __global__ void __launch_bounds__(256) k_svgd(float4* __restrict__ poses, int64_
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
                 float w = a < 3 ? wr : wt;
-                acc[a] = k * ps[a] - 2.f * k * w * dj[a];
+                if (PRE) {
+                    acc[a] = k * ps[a];
+                    acc[6 + a] = -2.f * k * w * dj[a];
+                } else {
+                    acc[a] = k * ps[a] - 2.f * k * w * dj[a];
+                }
             }
-            acc[6] = k;
+            acc[NA - 1] = k;
         }
     }
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
-        for (int a = 0; a < 7; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], off, G);
+        for (int a = 0; a < NA; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], off, G);
     if (!active || l != 0) return;
     float xi[6];
-    float inv = acc[6] > 0.f ? 1.f / acc[6] : 0.f;
+    float inv = acc[NA - 1] > 0.f ? 1.f / acc[NA - 1] : 0.f;
+    if (PRE) {
+        float P[21];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) xi[a] = acc[a] * inv;
+        for (int e = 0; e < 21; ++e) P[e] = pinv[i * 24 + e];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            float r = 0.f;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                // upper triangle stored column by column: (r, c), r <= c at c (c + 1) / 2 + r
+                const int e = a <= c ? c * (c + 1) / 2 + a : a * (a + 1) / 2 + c;
+                r += P[e] * acc[6 + c];
+            }
+            xi[a] = (acc[a] + r) * inv;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 6; ++a) xi[a] = acc[a] * inv;
+    }
     Quat q;
     float t[3];
     load_pose(poses, i, q, t);
@@ -254,7 +310,8 @@ int mp_launch_predict(mp_ctx* c) {
 
 int mp_launch_solve(mp_ctx* c) {
     k_solve<<<grid_for(c->n, 128), 128, 0, c->stream>>>(c->gn, c->cap, c->sorted_ids, c->n, (double)c->p.lambda,
-                                                        (double)c->p.eps, c->psi, c->loglik, c->n_in);
+                                                        (double)c->p.eps, c->psi, c->loglik, c->n_in,
+                                                        c->p.svgd_precond ? c->pinv : nullptr);
     MP_LAUNCHED(c);
     return MP_OK;
 }
@@ -262,9 +319,14 @@ int mp_launch_solve(mp_ctx* c) {
 template <int G>
 static int launch_svgd_g(mp_ctx* c) {
     int64_t threads = c->n * G;
-    k_svgd<G><<<grid_for(threads, 256), 256, 0, c->stream>>>(c->poses[c->cur], c->n, c->p.K, c->nbr_ids[c->nbr_cur],
-                                                             c->nbr_k, c->nbr_d, c->psi, c->p.sigma_r, c->p.sigma_t,
-                                                             c->phi);
+    if (c->p.svgd_precond)
+        k_svgd<G, true><<<grid_for(threads, 256), 256, 0, c->stream>>>(
+            c->poses[c->cur], c->n, c->p.K, c->nbr_ids[c->nbr_cur], c->nbr_k, c->nbr_d, c->psi, c->p.sigma_r,
+            c->p.sigma_t, c->pinv, c->phi);
+    else
+        k_svgd<G, false><<<grid_for(threads, 256), 256, 0, c->stream>>>(
+            c->poses[c->cur], c->n, c->p.K, c->nbr_ids[c->nbr_cur], c->nbr_k, c->nbr_d, c->psi, c->p.sigma_r,
+            c->p.sigma_t, nullptr, c->phi);
     MP_LAUNCHED(c);
     return MP_OK;
 }

@@ -94,7 +94,7 @@ void free_particles(mp_ctx* c) {
     dfree(c->seg); dfree(c->sort_keys[0]); dfree(c->sort_keys[1]); dfree(c->sort_ids[0]); dfree(c->sort_ids[1]);
     dfree(c->radix_counts); dfree(c->scan_tmp);
     dfree(c->nbr_ids[0]); dfree(c->nbr_ids[1]); dfree(c->nbr_k); dfree(c->nbr_d);
-    dfree(c->gn); dfree(c->psi); dfree(c->phi); dfree(c->red);
+    dfree(c->gn); dfree(c->psi); dfree(c->pinv); dfree(c->phi); dfree(c->red);
     c->cap = 0;
     c->n = 0;
 }
@@ -124,6 +124,7 @@ int alloc_particles(mp_ctx* c, int64_t n) {
     A_(c->scan_tmp, c->scan_tmp_cap);
     A_(c->nbr_ids[0], n * K); A_(c->nbr_ids[1], n * K); A_(c->nbr_k, n * K); A_(c->nbr_d, n * K * 6);
     A_(c->gn, (int64_t)MP_GN * n); A_(c->psi, 8 * n); A_(c->phi, 8 * n);
+    if (c->p.svgd_precond) A_(c->pinv, 24 * n);
     A_(c->red, 3 * (n / 256 + 2));
 #undef A_
     c->cap = n;
@@ -162,6 +163,7 @@ int check_params(mp_ctx* c, const mp_params* p) {
     if (p->post_iters < 0 || p->post_iters > 1000) return mp_fail(c, MP_EINVAL, "post_iters must lie in [0, 1000]");
     if (p->n_buckets_log2 < 1 || p->n_buckets_log2 > 26) return mp_fail(c, MP_EINVAL, "n_buckets_log2 must lie in [1, 26]");
     if (p->max_scan < 1 || p->max_scan > (1 << 20)) return mp_fail(c, MP_EINVAL, "max_scan must lie in [1, 2^20]");
+    if (p->svgd_precond != 0 && p->svgd_precond != 1) return mp_fail(c, MP_EINVAL, "svgd_precond must be 0 or 1");
     return MP_OK;
 }
 

@@ -72,6 +72,8 @@ struct mp_ctx {
     float* nbr_d;
     float* gn;              // MP_GN x cap, structure of arrays, sorted order
     float* psi;             // 8 floats per particle (6 used)
+    float* pinv;            // 24 floats per particle: (H + lambda diag H + eps I)^-1, upper triangle
+                            // (21 used); allocated when svgd_precond is set
     float* phi;             // 8 floats per particle (6 used)
 
     // scan

@@ -50,11 +50,13 @@ def make_trials(n_trials, n_particles, seed0=100):
     return room, trials
 
 
-def run(room, trials, precision, max_steps, seeding=None, stream=None):
+def run(room, trials, precision, max_steps, seeding=None, stream=None, svgd_precond=0):
     """Errors (trials, max_steps, 2) of the representative state per step.
-    seeding(trial_index, scan, particles) -> particles replaces the initial set."""
+    seeding(trial_index, scan, particles) -> particles replaces the initial set;
+    svgd_precond selects the SVGD reading (mp_params.svgd_precond)."""
     n = len(trials[0][2])
     params = mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, n)
+    params.svgd_precond = int(svgd_precond)
     ctx = mp.mp_init_map(room.map_points, params, cuda_stream=stream)
     eye, zero = np.eye(4), np.zeros((6, 6))
     out = np.zeros((len(trials), max_steps, 2))
@@ -97,14 +99,17 @@ def main():
     ap.add_argument("--max-steps", type=int, default=30)
     ap.add_argument("--precision", default="fp32,bf16,fp16")
     ap.add_argument("--seed", type=int, default=100)
+    ap.add_argument("--svgd-precond", default="0", help="comma list of mp_params.svgd_precond values")
     a = ap.parse_args()
     room, trials = make_trials(a.trials, a.particles, a.seed)
-    for prec in a.precision.split(","):
-        t0 = time.perf_counter()
-        errs = run(room, trials, prec, a.max_steps)
-        res = {"scene": "box_room", "precision": prec, "seeding": "uniform", "particles": a.particles,
-               "max_steps": a.max_steps, "wall_s": round(time.perf_counter() - t0, 2), **summarise(errs)}
-        print(json.dumps(res), flush=True)
+    for pre in (int(v) for v in a.svgd_precond.split(",")):
+        for prec in a.precision.split(","):
+            t0 = time.perf_counter()
+            errs = run(room, trials, prec, a.max_steps, svgd_precond=pre)
+            res = {"scene": "box_room", "precision": prec, "svgd_precond": pre, "seeding": "uniform",
+                   "particles": a.particles, "max_steps": a.max_steps, "wall_s": round(time.perf_counter() - t0, 2),
+                   **summarise(errs)}
+            print(json.dumps(res), flush=True)
 
 
 if __name__ == "__main__":

@@ -52,7 +52,7 @@ class mp_params(C.Structure):
                 ("lambda_", C.c_float), ("eps", C.c_float), ("eps_cov", C.c_float), ("r_cov", C.c_float),
                 ("K", C.c_int32), ("C", C.c_int32), ("cov_k", C.c_int32), ("cov_min", C.c_int32),
                 ("post_iters", C.c_int32), ("n_buckets_log2", C.c_int32), ("max_scan", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("svgd_precond", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -306,3 +306,95 @@ def mp_set_precision(ctx, precision):
     """Arithmetic precision of the likelihood stage: MP_PREC_FP32 (default),
     MP_PREC_BF16 or MP_PREC_FP16 (16-bit per-pair arithmetic, FP32 sums)."""
     _check(lib().mp_set_precision(ctx, int(precision)), ctx)
+
+
+# ---------------------------------------------------------------------------
+# learned proposal (include/mp_proposal.h): device tensors in and out
+MP_PN_OUT, MP_PN_COMPONENTS = 416, 32
+
+
+def _pn_lib():
+    L = lib()
+    if not getattr(L, "_pn_declared", False):
+        V, P, I64, U64 = C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64
+        L.mp_pn_sim_box_room.argtypes = [P, C.c_int, C.c_float, C.c_float, P, I64, P, C.c_int, C.c_float, U64, P, V]
+        L.mp_pn_create.argtypes = [C.POINTER(V), C.c_int, C.c_int, C.c_float, P, P, U64, V]
+        L.mp_pn_destroy.argtypes = [V]
+        L.mp_pn_num_params.argtypes = [V, C.POINTER(I64)]
+        L.mp_pn_get_params.argtypes = [V, P]
+        L.mp_pn_set_params.argtypes = [V, P]
+        L.mp_pn_forward.argtypes = [V, P, C.c_int, P]
+        L.mp_pn_loss_grad.argtypes = [V, P, P, C.c_int, P, P]
+        L.mp_pn_adam_step.argtypes = [V, C.c_float, C.c_float, C.c_float, C.c_float]
+        L.mp_pn_sample.argtypes = [V, P, I64, U64, P]
+        for f in ("mp_pn_sim_box_room", "mp_pn_create", "mp_pn_destroy", "mp_pn_num_params", "mp_pn_get_params",
+                  "mp_pn_set_params", "mp_pn_forward", "mp_pn_loss_grad", "mp_pn_adam_step", "mp_pn_sample"):
+            getattr(L, f).restype = C.c_int
+        L._pn_declared = True
+    return L
+
+
+def _pn_check(rc, what):
+    if rc != MP_OK:
+        raise MPError(rc, f"{what} failed (details on stderr)")
+
+
+def _dev(t):
+    """data_ptr of a contiguous CUDA tensor."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def mp_pn_sim_box_room(boxes, half, height, poses, dirs, noise, seed, out, cuda_stream=None):
+    """Ray-cast B x P box-room scans into out (B, P, 3); all tensors on the GPU."""
+    _pn_check(_pn_lib().mp_pn_sim_box_room(_dev(boxes), int(boxes.shape[0]), float(half), float(height), _dev(poses),
+                                           int(poses.shape[0]), _dev(dirs), int(dirs.shape[0]), float(noise),
+                                           int(seed) & (2 ** 64 - 1), _dev(out),
+                                           C.c_void_p(cuda_stream) if cuda_stream else None), "mp_pn_sim_box_room")
+
+
+def mp_pn_create(n_points, max_batch, in_scale, scale, offset, seed=0, cuda_stream=None):
+    net = C.c_void_p()
+    sc = np.ascontiguousarray(scale, np.float32)
+    of = np.ascontiguousarray(offset, np.float32)
+    _pn_check(_pn_lib().mp_pn_create(C.byref(net), int(n_points), int(max_batch), float(in_scale),
+                                     sc.ctypes.data_as(C.c_void_p), of.ctypes.data_as(C.c_void_p),
+                                     int(seed) & (2 ** 64 - 1), C.c_void_p(cuda_stream) if cuda_stream else None),
+              "mp_pn_create")
+    return net
+
+
+def mp_pn_destroy(net):
+    _pn_check(_pn_lib().mp_pn_destroy(net), "mp_pn_destroy")
+
+
+def mp_pn_num_params(net) -> int:
+    n = C.c_int64()
+    _pn_check(_pn_lib().mp_pn_num_params(net, C.byref(n)), "mp_pn_num_params")
+    return int(n.value)
+
+
+def mp_pn_get_params(net, out):
+    _pn_check(_pn_lib().mp_pn_get_params(net, _dev(out)), "mp_pn_get_params")
+
+
+def mp_pn_set_params(net, params):
+    _pn_check(_pn_lib().mp_pn_set_params(net, _dev(params)), "mp_pn_set_params")
+
+
+def mp_pn_forward(net, scans, out):
+    _pn_check(_pn_lib().mp_pn_forward(net, _dev(scans), int(scans.shape[0]), _dev(out)), "mp_pn_forward")
+
+
+def mp_pn_loss_grad(net, scans, targets, loss, grad=None):
+    _pn_check(_pn_lib().mp_pn_loss_grad(net, _dev(scans), _dev(targets), int(scans.shape[0]), _dev(loss),
+                                        _dev(grad) if grad is not None else None), "mp_pn_loss_grad")
+
+
+def mp_pn_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _pn_check(_pn_lib().mp_pn_adam_step(net, float(lr), float(beta1), float(beta2), float(eps)), "mp_pn_adam_step")
+
+
+def mp_pn_sample(net, mix, n, seed, out):
+    _pn_check(_pn_lib().mp_pn_sample(net, _dev(mix), int(n), int(seed) & (2 ** 64 - 1), _dev(out)), "mp_pn_sample")

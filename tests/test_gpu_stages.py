@@ -270,6 +270,41 @@ def test_svgd_update(env, oracle):
     assert np.all(ang <= 1e-5 * mag) and np.all(dist <= 2e-6 * (1 + np.abs(new_ref[:, 4:]).max(1)) * mag)
 
 
+def test_svgd_update_preconditioned(env, oracle):
+    """svgd_precond = 1: k_solve's damped inverse and k_svgd's product against
+    the oracle's Eq. 6 with the repulsion times numpy's inverse, on the same
+    lists, steps and Gauss-Newton sums (from a full pass of the stages)."""
+    mp = env["mp"]
+    P = env["P"]
+    params = mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, N)
+    params.svgd_precond = 1
+    ctx = mp.mp_init_map(env["w"].map_points, params)
+    try:
+        mp.mp_init_particles(ctx, N, poses=env["w"].particles)
+        mp.mp_set_scan(ctx, env["w"].scans[0])
+        mp.mp_run_stages(ctx, mp.MP_STAGE_SCAN | mp.MP_STAGE_LSH | mp.MP_STAGE_SORT | mp.MP_STAGE_MERGE)
+        mp.mp_run_stages(ctx, mp.MP_STAGE_LIKELIHOOD | mp.MP_STAGE_SOLVE)
+        g = {k: mp.mp_get_buffer(ctx, b) for k, b in (("ids", mp.MP_BUF_NBR_IDS), ("k", mp.MP_BUF_NBR_K),
+                                                     ("d", mp.MP_BUF_NBR_D), ("psi", mp.MP_BUF_PSI),
+                                                     ("gn", mp.MP_BUF_GN), ("poses", mp.MP_BUF_POSES))}
+        mp.mp_run_stages(ctx, mp.MP_STAGE_SVGD)
+        phi = mp.mp_get_buffer(ctx, mp.MP_BUF_PHI)
+    finally:
+        mp.mp_destroy(ctx)
+    H = g["gn"][:, :21].astype(np.float64)      # exported in particle order
+    ok = (g["gn"][:, 28] >= 6) & np.any(g["psi"] != 0, axis=1)
+    pinv = oracle.svgd_precond_matrices(H, ok, P)
+    phi_ref, _ = oracle.svgd(g["poses"], g["ids"], g["k"].astype(np.float64), g["d"].astype(np.float64),
+                             g["psi"].astype(np.float64), P, pinv)
+    assert ok.mean() > 0.3
+    scale = 1e-6 + np.abs(phi_ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(phi - phi_ref) <= 2e-4 * scale)
+    # the preconditioned repulsion is far weaker than the printed one
+    phi_lit, _ = oracle.svgd(g["poses"], g["ids"], g["k"].astype(np.float64), g["d"].astype(np.float64),
+                             g["psi"].astype(np.float64), P)
+    assert np.median(np.linalg.norm(phi_ref, axis=1)) < np.median(np.linalg.norm(phi_lit, axis=1))
+
+
 def test_posterior(env, oracle):
     mp, ctx = env["mp"], env["ctx"]
     P = env["P"]
