@@ -222,6 +222,45 @@ int mp_stage_times(mp_ctx* ctx, float ms_out[9], int64_t runs_out[9], int64_t* p
 #define MP_PREC_FP16 2
 int mp_set_precision(mp_ctx* ctx, int precision);
 
+/* Tile knob of the FP32 likelihood stage: the scan is split over `split`
+ * CTAs per block of particles (1 to 64; default 1), whose partial sums are
+ * added atomically into the Gauss-Newton sums (summation order, so the last
+ * bits, then depend on scheduling). Splitting puts more CTAs to work when the
+ * particles are few (a 4096-particle instance has 16 particle blocks for 152
+ * SMs); mp_batch_create picks it per instance by timing. */
+int mp_set_likelihood_split(mp_ctx* ctx, int split);
+
+/* ---- Batched instances ------------------------------------------------
+ * Many independent contexts (each with its own map, particles and CUDA
+ * stream) stepped together: mp_batch_create captures one full step of every
+ * instance into a CUDA graph (each instance on its own stream branch, forked
+ * from and joined into cuda_stream), twice (two pinned staging slots), and
+ * mp_batch_step replays it. Per instance the scan size is fixed (n_scan[i]
+ * points every step) and every step runs all stages, the prediction included
+ * (identity odometry without noise is applied, not skipped). tune_scans (may
+ * be NULL; else one host scan per instance) is used to pick, by timing, each
+ * instance's likelihood split (mp_set_likelihood_split); the pick runs the
+ * scan, LSH and sort stages of each instance once. Contexts must not use
+ * cuda_stream, must not share a stream, and must not have timing enabled.
+ * The batch does not own the contexts; destroy it before them. A context in
+ * a batch is stepped only through the batch (mp_batch_step returns
+ * MP_EINVAL otherwise); reading it (mp_get_posterior, mp_get_buffer) is fine. */
+typedef struct mp_batch mp_batch;
+/* A new non-blocking CUDA stream (one per instance of a batch) and its
+ * release; *stream receives the cudaStream_t. */
+int mp_stream_create(void** stream);
+int mp_stream_destroy(void* stream);
+int mp_batch_create(mp_batch** batch, mp_ctx* const* ctxs, int n, const int32_t* n_scan,
+                    const float* const* tune_scans, void* cuda_stream);
+/* One step of every instance: scans[i] = n_scan[i] x 3 host floats (copied
+ * before return), odom_T = n x 16 and odom_cov = n x 36 host doubles (NULL:
+ * identity motion / no noise for all). Asynchronous: later calls on an
+ * instance (mp_get_posterior, ...) are ordered after it. */
+int mp_batch_step(mp_batch* batch, const float* const* scans, const double* odom_T, const double* odom_cov);
+/* The likelihood split picked for instance i. */
+int mp_batch_split(mp_batch* batch, int i, int* split);
+int mp_batch_destroy(mp_batch* batch);
+
 /* Number of kernels this context has launched so far. */
 int mp_kernel_launches(mp_ctx* ctx, int64_t* count);
 

@@ -1,0 +1,163 @@
+"""Many independent localisation instances stepped together.
+
+Workload: 64 instances on 8 seeded maps (4 box rooms of 20k points, 4
+outdoor scenes of 100k, 250k, 500k and 1M points), particle counts
+log-uniform in 2^12..2^18, scans of 1024..16384 points (log-uniform), every
+instance on its own CUDA stream. Each instance keeps one scan (ray-cast from
+a seeded pose) for every step, with small odometry and noise.
+
+    python -m paper_2404_16370_gb300.batch --instances 64 --steps 10
+
+times the same steps taken (a) instance by instance with mp_step (each call
+launches the step's kernels on the instance's stream; instances overlap on
+the GPU) and (b) with mp_batch_step (one CUDA-graph launch per step for all
+instances, likelihood splits picked by timing), and prints one JSON line
+with instance-steps/s and particle-point pairs/s of both.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import mp, synth
+
+
+def build_instances(n_inst, seed=0, log2_particles=(12, 18), log2_points=(10, 14), outdoor=True):
+    rng = np.random.default_rng(seed)
+    maps = []
+    for k in range(4 if outdoor else 8):
+        room = synth.box_room(1 + k)
+        maps.append(("box_room", room, room.map_points))
+    if outdoor:
+        for k, n_map in enumerate((100_000, 250_000, 500_000, 1_000_000)):
+            sc = synth.outdoor(11 + k, n_map=n_map)
+            maps.append(("outdoor", sc, sc.map_points))
+    inst = []
+    for i in range(n_inst):
+        kind, scene, pts = maps[i % len(maps)]
+        n_part = int(2 ** rng.uniform(*log2_particles))
+        n_pts = int(2 ** rng.uniform(*log2_points))
+        if kind == "box_room":
+            gt = synth.box_room_gt_pose(scene, 1000 + i)
+            scan = synth.scan(scene, gt, synth.spherical_dirs(n_pts), 0.02, 2000 + i)
+            parts = synth.box_room_particles(n_part, 3000 + i, scene.half)
+            preset = mp.MP_PRESET_BOX_ROOM
+        else:
+            traj = synth.outdoor_trajectory(1, 0, seed=4000 + i, scene=scene)
+            gt = traj[0]
+            scan = synth.scan(scene, gt, synth.lidar_dirs(32, 512), 0.03, 2000 + i, dropout=0.1, max_range=100.0,
+                              n_keep=n_pts)
+            parts = synth.outdoor_particles(scene, n_part, 3000 + i)
+            preset = mp.MP_PRESET_OUTDOOR
+        inst.append(dict(map=i % len(maps), kind=kind, pts=pts, scan=scan.astype(np.float32), parts=parts,
+                         preset=preset, n=n_part))
+    return inst
+
+
+def make_contexts(inst):
+    """One context per instance, each on a stream of its own (torch's stream
+    pool would hand out repeated streams beyond 32)."""
+    ctxs, streams = [], []
+    for d in inst:
+        st = mp.mp_stream_create()
+        p = mp.mp_default_params(d["preset"], d["n"])
+        ctx = mp.mp_init_map(d["pts"], p, cuda_stream=st)
+        mp.mp_init_particles(ctx, d["n"], poses=d["parts"])
+        ctxs.append(ctx)
+        streams.append(st)
+    return ctxs, streams
+
+
+def release(ctxs, streams):
+    for c in ctxs:
+        mp.mp_destroy(c)
+    for s in streams:
+        mp.mp_stream_destroy(s)
+
+
+def odometry(n, step):
+    rng = np.random.default_rng(7000 + step)
+    T = np.tile(np.eye(4), (n, 1, 1))
+    T[:, :3, 3] = rng.normal(0, 0.05, (n, 3))
+    cov = np.tile(np.diag([1e-4] * 3 + [2.5e-3] * 3), (n, 1, 1))
+    return T, cov
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--small", action="store_true",
+                    help="8 box rooms, 2^10..2^13 particles, 512..2048-point scans (the launch-bound regime)")
+    a = ap.parse_args()
+    import torch
+    t0 = time.perf_counter()
+    if a.small:
+        inst = build_instances(a.instances, log2_particles=(10, 13), log2_points=(9, 11), outdoor=False)
+    else:
+        inst = build_instances(a.instances)
+    gen_s = time.perf_counter() - t0
+    n = len(inst)
+    scans = [d["scan"] for d in inst]
+    pairs_step = float(sum(d["n"] * len(d["scan"]) for d in inst))
+    res = {"workload": "small box-room instances" if a.small else "64 instances, 8 box-room/outdoor maps",
+           "instances": n, "maps": 8, "particles_total": int(sum(d["n"] for d in inst)),
+           "scan_points_total": int(sum(len(d["scan"]) for d in inst)), "steps": a.steps, "warmup": a.warmup,
+           "inputs_s": round(gen_s, 1)}
+    # (a) instance by instance
+    ctxs, streams = make_contexts(inst)
+    try:
+        for s in range(a.warmup):
+            T, cov = odometry(n, s)
+            for i, c in enumerate(ctxs):
+                mp.mp_step(c, scans[i], T[i], cov[i])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(a.warmup, a.warmup + a.steps):
+            T, cov = odometry(n, s)
+            for i, c in enumerate(ctxs):
+                mp.mp_step(c, scans[i], T[i], cov[i])
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+    finally:
+        release(ctxs, streams)
+    # (b) batched
+    ctxs, streams = make_contexts(inst)
+    origin = mp.mp_stream_create()
+    try:
+        t0 = time.perf_counter()
+        batch = mp.mp_batch_create(ctxs, [len(s) for s in scans], origin, tune_scans=scans)
+        create_s = time.perf_counter() - t0
+        try:
+            for s in range(a.warmup):
+                T, cov = odometry(n, s)
+                mp.mp_batch_step(batch, scans, T, cov)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s in range(a.warmup, a.warmup + a.steps):
+                T, cov = odometry(n, s)
+                mp.mp_batch_step(batch, scans, T, cov)
+            torch.cuda.synchronize()
+            t_bat = time.perf_counter() - t0
+            splits = [mp.mp_batch_split(batch, i) for i in range(n)]
+        finally:
+            mp.mp_batch_destroy(batch)
+    finally:
+        release(ctxs, streams + [origin])
+    res.update({
+        "sequential": {"instance_steps_per_s": n * a.steps / t_seq, "pairs_per_s": pairs_step * a.steps / t_seq,
+                       "ms_per_step": 1e3 * t_seq / a.steps},
+        "batched": {"instance_steps_per_s": n * a.steps / t_bat, "pairs_per_s": pairs_step * a.steps / t_bat,
+                    "ms_per_step": 1e3 * t_bat / a.steps, "create_s": round(create_s, 2)},
+        "speedup": t_seq / t_bat,
+        "splits": {str(k): splits.count(k) for k in sorted(set(splits))},
+    })
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

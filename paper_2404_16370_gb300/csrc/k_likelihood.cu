@@ -63,6 +63,7 @@ struct LkArgs {
     unsigned long long* pairs;
     long long budget;   // cycle limit of each barrier wait
     int starve;         // test knob: announce 16 bytes more than copied for chunk 0
+    int split;          // CTAs sharing the scan of one particle block (gridDim.y); > 1 adds atomically
     // constants as pairs (both halves equal)
     float2 inv2, offx2, offy2, offz2, magic2, m1, half2, half_a2, nhalf_a2, two_eps2, two2, quarter_a2;
 };
@@ -79,7 +80,8 @@ struct LkAcc {
 
 // Rotates the map-frame sums of one particle back to the sensor frame
 // (blocks M -> R^T M R, b -> R^T b) and stores the 29 outputs at sorted slot p.
-__device__ __forceinline__ void lk_store(const LkArgs& A, const float R[9], const LkAcc& S, int64_t p) {
+__device__ __forceinline__ void lk_store(const LkArgs& A, const float R[9], const LkAcc& S, int64_t p,
+                                         bool add = false) {
     float Hw[3][3] = {{S.Hww[0], S.Hww[1], S.Hww[2]}, {S.Hww[1], S.Hww[3], S.Hww[4]}, {S.Hww[2], S.Hww[4], S.Hww[5]}};
     float Hc[3][3] = {{S.Hwv[0], S.Hwv[1], S.Hwv[2]}, {S.Hwv[3], S.Hwv[4], S.Hwv[5]}, {S.Hwv[6], S.Hwv[7], S.Hwv[8]}};
     float Hv[3][3] = {{S.Hvv[0], S.Hvv[1], S.Hvv[2]}, {S.Hvv[1], S.Hvv[3], S.Hvv[4]}, {S.Hvv[2], S.Hvv[4], S.Hvv[5]}};
@@ -121,7 +123,10 @@ __device__ __forceinline__ void lk_store(const LkArgs& A, const float R[9], cons
     out[27] = S.ll;
     out[28] = (float)S.cnt;
 #pragma unroll
-    for (int f = 0; f < MP_GN; ++f) A.gn[(int64_t)f * A.stride + p] = out[f];
+    for (int f = 0; f < MP_GN; ++f) {
+        if (add) atomicAdd(A.gn + (int64_t)f * A.stride + p, out[f]);
+        else A.gn[(int64_t)f * A.stride + p] = out[f];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -307,7 +312,11 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
 
     const int nv = *A.nvalid;
     const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
+    // scan split: this CTA takes chunks blockIdx.y, blockIdx.y + split, ...
+    const int split = A.split, by = blockIdx.y;
+    const int nmine = by < nchunks ? (nchunks - by + split - 1) / split : 0;
+    if (blockIdx.x == 0 && by == 0 && threadIdx.x == 0)
+        atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -321,8 +330,8 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
         bulk_g2s(dst, A.scan + 3 * (int64_t)cc * LK_CHUNK, bytes, b);
     };
     if (threadIdx.x == 0) {
-        if (nchunks > 0) issue(buf[0], &bar[0], 0);
-        if (nchunks > 1) issue(buf[1], &bar[1], 1);
+        if (nmine > 0) issue(buf[0], &bar[0], by);
+        if (nmine > 1) issue(buf[1], &bar[1], by + split);
     }
 
     Lk2Acc S;
@@ -338,13 +347,15 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
 
     const bool active = acta;   // acta is false only if actb is false too
     bool failed = false;
+    int nv_mine = 0;
     int c = 0;
-    for (; c < nchunks; ++c) {
+    for (; c < nmine; ++c) {
         const int b = c & 1;
         const uint32_t parity = (uint32_t)((c >> 1) & 1);
         bool got = mbar_wait_bounded(&bar[b], parity, A.budget);
         if (__syncthreads_or(!got)) { failed = true; break; }
-        const int m = min(LK_CHUNK, nv - c * LK_CHUNK);
+        const int m = min(LK_CHUNK, nv - (by + c * split) * LK_CHUNK);
+        nv_mine += m;
         if (active) {
             const float4* P = buf[b];
             // software pipeline over the two dependent gathers: every
@@ -371,12 +382,12 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0 && c + 2 < nchunks) issue(buf[b], &bar[b], c + 2);
+        if (threadIdx.x == 0 && c + 2 < nmine) issue(buf[b], &bar[b], by + (c + 2) * split);
     }
     if (failed) {
         if (threadIdx.x == 0) {
             atomicOr(A.err, MP_ERR_WAIT);
-            for (int k = c; k < min(c + 2, nchunks); ++k)
+            for (int k = c; k < min(c + 2, nmine); ++k)
                 mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), A.budget);
         }
         return;
@@ -385,12 +396,12 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
     if (acta) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rs[k] = R[k].x;
-        lk_store(A, Rs, lk2_half(A, S, 0, nv), pa);
+        lk_store(A, Rs, lk2_half(A, S, 0, nv_mine), pa, split > 1);
     }
     if (actb) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rs[k] = R[k].y;
-        lk_store(A, Rs, lk2_half(A, S, 1, nv), pb);
+        lk_store(A, Rs, lk2_half(A, S, 1, nv_mine), pb, split > 1);
     }
 }
 
@@ -694,6 +705,7 @@ int mp_launch_likelihood(mp_ctx* c) {
     A.two2 = pair(2.f);
     A.quarter_a2 = pair(0.25f * a);
     A.scan_h = c->scan_h2;
+    A.split = 1;
     const unsigned grid = grid_for(c->n, LK_PER_CTA);
     if (c->precision == MP_PREC_BF16 || c->precision == MP_PREC_FP16) {
         if (c->n_scan > 0) {
@@ -710,7 +722,11 @@ int mp_launch_likelihood(mp_ctx* c) {
         else
             k_likelihood_h<__half2, LK_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
     } else {
-        k_likelihood<LK_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
+        // the scan split (a tuning knob for small particle counts): partial
+        // sums of each CTA are added into a zeroed output
+        A.split = c->lk_split > 1 ? c->lk_split : 1;
+        if (A.split > 1) MP_CUDA(c, cudaMemsetAsync(c->gn, 0, sizeof(float) * MP_GN * (size_t)c->cap, c->stream));
+        k_likelihood<LK_MINB><<<dim3(grid, A.split), LK_THREADS, 0, c->stream>>>(A);
     }
     MP_LAUNCHED(c);
     return MP_OK;

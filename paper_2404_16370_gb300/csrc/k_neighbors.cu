@@ -83,9 +83,6 @@ size_t scan_tmp_need(int64_t n) {
 // LSH keys (FP64)
 // ---------------------------------------------------------------------------
 struct LshArgs {
-    double q[4];       // T_LSH^-1 rotation
-    double t[3];       // T_LSH^-1 translation
-    double delta[6];
     double scale[6];   // alpha * W^K diagonal
     uint32_t mask;
 };
@@ -113,8 +110,9 @@ __device__ __forceinline__ void log_se3_d(double qx, double qy, double qz, doubl
     for (int a = 0; a < 3; ++a) xi[3 + a] = t[a] - 0.5 * wt[a] + C * wwt[a];
 }
 
-__global__ void k_lsh_keys(const float4* __restrict__ poses, int64_t n, LshArgs A, uint32_t* __restrict__ keys,
-                           uint32_t* __restrict__ buckets) {
+// T_LSH^-1 and delta come from the device-side step values (replayable)
+__global__ void k_lsh_keys(const float4* __restrict__ poses, int64_t n, LshArgs A, const StepDev* __restrict__ sd,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ buckets) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 a = poses[2 * i], b = poses[2 * i + 1];
@@ -122,7 +120,7 @@ __global__ void k_lsh_keys(const float4* __restrict__ poses, int64_t n, LshArgs 
     double nrm = rsqrt(qx * qx + qy * qy + qz * qz + qw * qw);
     qx *= nrm; qy *= nrm; qz *= nrm; qw *= nrm;
     // relative pose T_LSH^-1 T_i = (Lq (x) q_i, R(Lq) t_i + Lt)
-    const double lx = A.q[0], ly = A.q[1], lz = A.q[2], lw = A.q[3];
+    const double lx = sd->lsh_qinv[0], ly = sd->lsh_qinv[1], lz = sd->lsh_qinv[2], lw = sd->lsh_qinv[3];
     double rw = lw * qw - lx * qx - ly * qy - lz * qz;
     double rx = lw * qx + lx * qw + ly * qz - lz * qy;
     double ry = lw * qy - lx * qz + ly * qw + lz * qx;
@@ -133,14 +131,14 @@ __global__ void k_lsh_keys(const float4* __restrict__ poses, int64_t n, LshArgs 
     R[3] = 2 * (lx * ly + lw * lz); R[4] = 1 - 2 * (lx * lx + lz * lz); R[5] = 2 * (ly * lz - lw * lx);
     R[6] = 2 * (lx * lz - lw * ly); R[7] = 2 * (ly * lz + lw * lx); R[8] = 1 - 2 * (lx * lx + ly * ly);
     double t[3];
-    for (int r = 0; r < 3; ++r) t[r] = R[3 * r] * ti[0] + R[3 * r + 1] * ti[1] + R[3 * r + 2] * ti[2] + A.t[r];
+    for (int r = 0; r < 3; ++r) t[r] = R[3 * r] * ti[0] + R[3 * r + 1] * ti[1] + R[3 * r + 2] * ti[2] + sd->lsh_tinv[r];
     double xi[6];
     log_se3_d(rx, ry, rz, rw, t, xi);
     const uint32_t P[6] = {73856093u, 19349663u, 83492791u, 2654435761u, 805459861u, 3674653429u};
     uint32_t key = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        double z = A.scale[k] * xi[k] + A.delta[k];
+        double z = A.scale[k] * xi[k] + sd->lsh_delta[k];
         int cell = (int)floor(z);
         key ^= (uint32_t)cell * P[k];
     }
@@ -394,21 +392,10 @@ int mp_launch_exclusive_scan(mp_ctx* c, const uint32_t* in, uint32_t* out, int64
 
 int mp_launch_lsh_keys(mp_ctx* c) {
     LshArgs A;
-    // inverse of T_LSH: (conj(q), -R^T t)
-    double qx = c->lsh_q[0], qy = c->lsh_q[1], qz = c->lsh_q[2], qw = c->lsh_q[3];
-    A.q[0] = -qx; A.q[1] = -qy; A.q[2] = -qz; A.q[3] = qw;
-    double R[9];
-    R[0] = 1 - 2 * (qy * qy + qz * qz); R[1] = 2 * (qx * qy - qw * qz); R[2] = 2 * (qx * qz + qw * qy);
-    R[3] = 2 * (qx * qy + qw * qz); R[4] = 1 - 2 * (qx * qx + qz * qz); R[5] = 2 * (qy * qz - qw * qx);
-    R[6] = 2 * (qx * qz - qw * qy); R[7] = 2 * (qy * qz + qw * qx); R[8] = 1 - 2 * (qx * qx + qy * qy);
-    for (int r = 0; r < 3; ++r)
-        A.t[r] = -(R[r] * c->lsh_t[0] + R[3 + r] * c->lsh_t[1] + R[6 + r] * c->lsh_t[2]);
-    for (int k = 0; k < 6; ++k) {
-        A.delta[k] = c->lsh_delta[k];
-        A.scale[k] = (double)c->p.alpha * (double)(k < 3 ? c->p.sigma_r : c->p.sigma_t);
-    }
+    for (int k = 0; k < 6; ++k) A.scale[k] = (double)c->p.alpha * (double)(k < 3 ? c->p.sigma_r : c->p.sigma_t);
     A.mask = c->p.n_buckets_log2 >= 32 ? 0xffffffffu : ((1u << c->p.n_buckets_log2) - 1u);
-    k_lsh_keys<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->poses[c->cur], c->n, A, c->keys, c->buckets);
+    k_lsh_keys<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->poses[c->cur], c->n, A, c->step_dev, c->keys,
+                                                          c->buckets);
     MP_LAUNCHED(c);
     return MP_OK;
 }

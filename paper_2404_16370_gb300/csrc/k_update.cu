@@ -17,14 +17,12 @@ namespace {
 struct PredArgs {
     float4* poses;
     int64_t n;
-    float dq[4], dt[3];
-    float L[21];
-    int noise;
     uint2 key;
-    uint32_t step;
 };
 
-__global__ void k_predict(const PredArgs A) {
+// the motion dT, the noise factor and the step counter come from the
+// device-side step values (replayable)
+__global__ void k_predict(const PredArgs A, const StepDev* __restrict__ sd) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     Quat q;
@@ -33,12 +31,14 @@ __global__ void k_predict(const PredArgs A) {
     // T dT
     float R[9], r[3];
     quat_rot(q, R);
-    rot_apply(R, A.dt, r);
+    const float dt[3] = {sd->dt[0], sd->dt[1], sd->dt[2]};
+    rot_apply(R, dt, r);
     t[0] += r[0]; t[1] += r[1]; t[2] += r[2];
-    q = qmul(q, Quat{A.dq[0], A.dq[1], A.dq[2], A.dq[3]});
-    if (A.noise) {
-        uint4 o0 = philox4x32_10(make_uint4((uint32_t)i, 0u, A.step, MP_STREAM_PREDICT), A.key);
-        uint4 o1 = philox4x32_10(make_uint4((uint32_t)i, 1u, A.step, MP_STREAM_PREDICT), A.key);
+    q = qmul(q, Quat{sd->dq[0], sd->dq[1], sd->dq[2], sd->dq[3]});
+    if (sd->noise) {
+        const uint32_t step = sd->step;
+        uint4 o0 = philox4x32_10(make_uint4((uint32_t)i, 0u, step, MP_STREAM_PREDICT), A.key);
+        uint4 o1 = philox4x32_10(make_uint4((uint32_t)i, 1u, step, MP_STREAM_PREDICT), A.key);
         uint32_t u[6] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y};
         float z[6];
 #pragma unroll
@@ -55,7 +55,7 @@ __global__ void k_predict(const PredArgs A) {
         for (int rr = 0; rr < 6; ++rr) {
             float s = 0.f;
 #pragma unroll
-            for (int cc = 0; cc <= rr; ++cc) s += A.L[o++] * z[cc];
+            for (int cc = 0; cc <= rr; ++cc) s += sd->L[o++] * z[cc];
             xi[rr] = s;
         }
         pose_retract(q, t, xi);
@@ -297,13 +297,8 @@ int mp_launch_predict(mp_ctx* c) {
     PredArgs A;
     A.poses = c->poses[c->cur];
     A.n = c->n;
-    for (int k = 0; k < 4; ++k) A.dq[k] = c->odom_q[k];
-    for (int k = 0; k < 3; ++k) A.dt[k] = c->odom_t[k];
-    for (int k = 0; k < 21; ++k) A.L[k] = c->chol[k];
-    A.noise = c->noise;
     A.key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
-    A.step = (uint32_t)c->step;
-    k_predict<<<grid_for(c->n, 256), 256, 0, c->stream>>>(A);
+    k_predict<<<grid_for(c->n, 256), 256, 0, c->stream>>>(A, c->step_dev);
     MP_LAUNCHED(c);
     return MP_OK;
 }

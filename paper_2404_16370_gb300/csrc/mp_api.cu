@@ -54,7 +54,11 @@ double u53_host(uint64_t seed, uint64_t step, uint32_t stream, uint32_t k) {
     return (double)((((uint64_t)(hi >> 5)) << 26) | (uint64_t)(lo >> 6)) * (1.0 / 9007199254740992.0);
 }
 
-// T^LSH uniform over SO(3) x map box, delta^LSH ~ N(0, sigma^2 I) (Eq. 10)
+}  // namespace
+
+// LSH draw of step c->step (Eq. 10): uniform rotation (Shoemake), translation
+// uniform in the valid-map box, delta ~ N(0, lsh_sigma^2 I); host FP64 from
+// Philox(seed, counter (k / 2, 0, step, LSH stream)).
 void draw_lsh(mp_ctx* c) {
     double u[12];
     for (uint32_t k = 0; k < 12; ++k) u[k] = u53_host(c->p.seed, c->step, MP_STREAM_LSH, k);
@@ -72,6 +76,45 @@ void draw_lsh(mp_ctx* c) {
         c->lsh_delta[2 * k + 1] = (double)c->p.lsh_sigma * rad * std::sin(ang);
     }
 }
+
+// Per-step values of the current state (c->step, the LSH draw, the odometry)
+// into a host StepDev; T_LSH is inverted here, in FP64.
+void fill_step_host(mp_ctx* c, StepDev* h) {
+    const double qx = c->lsh_q[0], qy = c->lsh_q[1], qz = c->lsh_q[2], qw = c->lsh_q[3];
+    h->lsh_qinv[0] = -qx; h->lsh_qinv[1] = -qy; h->lsh_qinv[2] = -qz; h->lsh_qinv[3] = qw;
+    double R[9];
+    R[0] = 1 - 2 * (qy * qy + qz * qz); R[1] = 2 * (qx * qy - qw * qz); R[2] = 2 * (qx * qz + qw * qy);
+    R[3] = 2 * (qx * qy + qw * qz); R[4] = 1 - 2 * (qx * qx + qz * qz); R[5] = 2 * (qy * qz - qw * qx);
+    R[6] = 2 * (qx * qz - qw * qy); R[7] = 2 * (qy * qz + qw * qx); R[8] = 1 - 2 * (qx * qx + qy * qy);
+    for (int r = 0; r < 3; ++r)
+        h->lsh_tinv[r] = -(R[r] * c->lsh_t[0] + R[3 + r] * c->lsh_t[1] + R[6 + r] * c->lsh_t[2]);
+    for (int k = 0; k < 6; ++k) h->lsh_delta[k] = c->lsh_delta[k];
+    for (int k = 0; k < 4; ++k) h->dq[k] = c->odom_q[k];
+    for (int k = 0; k < 3; ++k) h->dt[k] = c->odom_t[k];
+    for (int k = 0; k < 21; ++k) h->L[k] = c->chol[k];
+    h->noise = c->noise;
+    h->step = (uint32_t)c->step;
+}
+
+// Copies the per-step values to the device on the context stream: from the
+// batch's fixed slot when one is set, else from the next slot of the pinned
+// ring (waiting, if needed, until the copy that last used it has run).
+int upload_step(mp_ctx* c) {
+    StepDev* h = c->batch_slot;
+    int slot = -1;
+    if (!h) {
+        slot = c->step_ring;
+        c->step_ring ^= 1;
+        MP_CUDA(c, cudaEventSynchronize(c->step_ev[slot]));
+        h = c->step_host + slot;
+    }
+    fill_step_host(c, h);
+    MP_CUDA(c, cudaMemcpyAsync(c->step_dev, h, sizeof(StepDev), cudaMemcpyHostToDevice, c->stream));
+    if (slot >= 0) MP_CUDA(c, cudaEventRecord(c->step_ev[slot], c->stream));
+    return MP_OK;
+}
+
+namespace {
 
 template <typename T>
 int dalloc(mp_ctx* c, T** p, size_t count) {
@@ -141,6 +184,10 @@ void destroy(mp_ctx* c) {
     dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pair); dfree(c->scan_h2); dfree(c->scan_tmp4);
     dfree(c->scan_nvalid);
     dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->pairs);
+    dfree(c->step_dev);
+    if (c->step_host) cudaFreeHost(c->step_host);
+    for (int k = 0; k < 2; ++k)
+        if (c->step_ev[k]) cudaEventDestroy(c->step_ev[k]);
     for (int r = 0; r < MP_EV_RING; ++r)
         for (int s = 0; s < MP_NSTAGES; ++s)
             for (int k = 0; k < 2; ++k)
@@ -313,7 +360,12 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
         if ((rc = dalloc(c, &c->best_idx, 1))) break;
         if ((rc = dalloc(c, &c->best_pose, 2))) break;
         if ((rc = dalloc(c, &c->dev_error, 1))) break;
-        cudaError_t e = cudaMemsetAsync(c->dev_error, 0, sizeof(int32_t), c->stream);
+        if ((rc = dalloc(c, &c->step_dev, 1))) break;
+        cudaError_t e = cudaHostAlloc((void**)&c->step_host, 2 * sizeof(StepDev), cudaHostAllocDefault);
+        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "cudaHostAlloc"); break; }
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&c->step_ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "cudaEventCreate"); break; }
+        e = cudaMemsetAsync(c->dev_error, 0, sizeof(int32_t), c->stream);
         if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "memset"); break; }
         e = cudaMemsetAsync(c->scan_nvalid, 0, sizeof(int32_t), c->stream);
         if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "memset"); break; }
@@ -438,6 +490,10 @@ int mp_run_stages(mp_ctx* c, uint32_t mask) {
     if (!c) return MP_EINVAL;
     if (c->n == 0) return mp_fail(c, MP_ENOTINIT, "particles not initialised");
     int rc = MP_OK;
+    if (mask & (MP_STAGE_PREDICT | MP_STAGE_LSH)) {
+        if (mask & MP_STAGE_LSH) draw_lsh(c);
+        if ((rc = upload_step(c))) return rc;
+    }
     for (int s = 0; s < MP_NSTAGES; ++s) {
         uint32_t bit = 1u << s;
         if (!(mask & bit)) continue;
@@ -445,7 +501,7 @@ int mp_run_stages(mp_ctx* c, uint32_t mask) {
         switch (bit) {
             case MP_STAGE_PREDICT: rc = mp_launch_predict(c); break;
             case MP_STAGE_SCAN: rc = mp_launch_scan_prepare(c); break;
-            case MP_STAGE_LSH: draw_lsh(c); rc = mp_launch_lsh_keys(c); break;
+            case MP_STAGE_LSH: rc = mp_launch_lsh_keys(c); break;
             case MP_STAGE_SORT: rc = mp_launch_sort(c); break;
             case MP_STAGE_MERGE: rc = mp_launch_merge(c); break;
             case MP_STAGE_LIKELIHOOD: rc = mp_launch_likelihood(c); break;
@@ -731,6 +787,13 @@ int mp_debug_set(mp_ctx* c, int what, int64_t value) {
         case MP_DEBUG_STARVE_TX: c->starve_tx = value ? 1 : 0; return MP_OK;
     }
     return mp_fail(c, MP_EINVAL, "unknown debug knob %d", what);
+}
+
+int mp_set_likelihood_split(mp_ctx* c, int split) {
+    if (!c) return MP_EINVAL;
+    if (split < 1 || split > 64) return mp_fail(c, MP_EINVAL, "likelihood split %d outside [1, 64]", split);
+    c->lk_split = split;
+    return MP_OK;
 }
 
 int mp_set_precision(mp_ctx* c, int precision) {

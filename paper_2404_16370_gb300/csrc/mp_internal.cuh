@@ -24,6 +24,17 @@
 #define MP_RADIX 256
 #define MP_SORT_TILE 2048   // elements per radix-sort block (256 threads x 8)
 
+// Per-step values the kernels read from device memory rather than from
+// their arguments, so that a captured step can be replayed: the LSH draw (as
+// T_LSH^-1 and the offset delta, Eq. 10) and the prediction's motion dT, noise
+// factor and counter (Eq. 1).
+struct StepDev {
+    double lsh_qinv[4], lsh_tinv[3], lsh_delta[6];
+    float dq[4], dt[3], L[21];
+    int32_t noise;
+    uint32_t step;
+};
+
 struct mp_ctx {
     mp_params p;
     cudaStream_t stream;
@@ -94,6 +105,14 @@ struct mp_ctx {
     // LSH draw of the current step
     double lsh_q[4], lsh_t[3], lsh_delta[6];
     uint64_t step;
+    // device copy of the per-step values, filled from a ring of two pinned
+    // host slots (an event per slot guards its reuse); batch_slot, when set,
+    // replaces the ring (a captured step copies from a fixed slot)
+    StepDev* step_dev;
+    StepDev* step_host;
+    cudaEvent_t step_ev[2];
+    int step_ring;
+    StepDev* batch_slot;
 
     // reductions
     double* red;            // partials
@@ -115,6 +134,7 @@ struct mp_ctx {
 
     // test knobs of the failure path
     int precision;           // MP_PREC_* of the likelihood stage
+    int lk_split;            // CTAs sharing the scan of one particle block (FP32 likelihood; 0/1 = none)
     uint4* scan_h2;          // 2 per valid point: the scan as 16-bit broadcast pairs (precision != FP32)
     long long wait_budget;   // cycles; 0 = MP_WAIT_BUDGET
     int starve_tx;
@@ -385,6 +405,9 @@ static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + b
 
 // launchers (each returns MP_OK or an error code recorded in ctx)
 // k_map.cu
+void draw_lsh(mp_ctx* c);
+void fill_step_host(mp_ctx* c, StepDev* h);
+int upload_step(mp_ctx* c);
 int mp_launch_map_prepare(mp_ctx* c, const float* xyz_dev);
 int mp_launch_scan_prepare(mp_ctx* c);
 int mp_launch_nnf_query(mp_ctx* c, const int32_t* vox_dev, int64_t m, int32_t* out_dev);

@@ -398,3 +398,98 @@ def mp_pn_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def mp_pn_sample(net, mix, n, seed, out):
     _pn_check(_pn_lib().mp_pn_sample(net, _dev(mix), int(n), int(seed) & (2 ** 64 - 1), _dev(out)), "mp_pn_sample")
+
+
+# ---------------------------------------------------------------------------
+# batched instances and the likelihood split
+
+
+def mp_set_likelihood_split(ctx, split):
+    L = lib()
+    L.mp_set_likelihood_split.argtypes = [C.c_void_p, C.c_int]
+    L.mp_set_likelihood_split.restype = C.c_int
+    _check(L.mp_set_likelihood_split(ctx, int(split)), ctx)
+
+
+def _batch_lib():
+    L = lib()
+    if not getattr(L, "_batch_declared", False):
+        V = C.c_void_p
+        L.mp_batch_create.argtypes = [C.POINTER(V), C.POINTER(V), C.c_int, V, C.POINTER(V), V]
+        L.mp_batch_step.argtypes = [V, C.POINTER(V), V, V]
+        L.mp_batch_split.argtypes = [V, C.c_int, C.POINTER(C.c_int)]
+        L.mp_batch_destroy.argtypes = [V]
+        for f in ("mp_batch_create", "mp_batch_step", "mp_batch_split", "mp_batch_destroy"):
+            getattr(L, f).restype = C.c_int
+        L._batch_declared = True
+    return L
+
+
+def mp_batch_create(ctxs, n_scan, cuda_stream, tune_scans=None):
+    """ctxs: contexts (each on its own stream); n_scan: fixed scan size of each;
+    tune_scans: list of (n_scan[i], 3) float32 arrays or None."""
+    n = len(ctxs)
+    arr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    ns = np.ascontiguousarray(n_scan, np.int32)
+    keep = []
+    tp = None
+    if tune_scans is not None:
+        ptrs = []
+        for sc in tune_scans:
+            a = np.ascontiguousarray(sc, np.float32)
+            keep.append(a)
+            ptrs.append(a.ctypes.data)
+        tp = (C.c_void_p * n)(*ptrs)
+    b = C.c_void_p()
+    rc = _batch_lib().mp_batch_create(C.byref(b), arr, n, ns.ctypes.data_as(C.c_void_p), tp,
+                                      C.c_void_p(cuda_stream))
+    if rc != MP_OK:
+        raise MPError(rc, "mp_batch_create failed (details on stderr)")
+    return b
+
+
+def mp_batch_step(batch, scans, odom_T=None, odom_cov=None):
+    n = len(scans)
+    keep = [np.ascontiguousarray(sc, np.float32) for sc in scans]
+    ptrs = (C.c_void_p * n)(*[a.ctypes.data for a in keep])
+    T = None if odom_T is None else np.ascontiguousarray(odom_T, np.float64).reshape(n, 16)
+    Q = None if odom_cov is None else np.ascontiguousarray(odom_cov, np.float64).reshape(n, 36)
+    rc = _batch_lib().mp_batch_step(batch, ptrs, None if T is None else T.ctypes.data_as(C.c_void_p),
+                                    None if Q is None else Q.ctypes.data_as(C.c_void_p))
+    if rc != MP_OK:
+        raise MPError(rc, "mp_batch_step failed (details on stderr)")
+
+
+def mp_batch_split(batch, i) -> int:
+    s = C.c_int()
+    rc = _batch_lib().mp_batch_split(batch, int(i), C.byref(s))
+    if rc != MP_OK:
+        raise MPError(rc, "mp_batch_split failed")
+    return int(s.value)
+
+
+def mp_batch_destroy(batch):
+    rc = _batch_lib().mp_batch_destroy(batch)
+    if rc != MP_OK:
+        raise MPError(rc, "mp_batch_destroy failed")
+
+
+def mp_stream_create() -> int:
+    """A new non-blocking CUDA stream (its cudaStream_t as an int)."""
+    L = lib()
+    L.mp_stream_create.argtypes = [C.POINTER(C.c_void_p)]
+    L.mp_stream_create.restype = C.c_int
+    s = C.c_void_p()
+    rc = L.mp_stream_create(C.byref(s))
+    if rc != MP_OK:
+        raise MPError(rc, "mp_stream_create failed")
+    return int(s.value)
+
+
+def mp_stream_destroy(stream):
+    L = lib()
+    L.mp_stream_destroy.argtypes = [C.c_void_p]
+    L.mp_stream_destroy.restype = C.c_int
+    rc = L.mp_stream_destroy(C.c_void_p(stream))
+    if rc != MP_OK:
+        raise MPError(rc, "mp_stream_destroy failed")

@@ -1,0 +1,122 @@
+"""Batched instances (mp_batch_*) and the likelihood's scan split: the split
+sums equal the unsplit ones up to summation order; a batch step equals the
+same step taken instance by instance with mp_step (bit for bit with split 1);
+the autotuned batch runs with valid splits and posteriors."""
+import numpy as np
+import pytest
+
+from paper_2404_16370_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def _room_instance(seed, n_part, n_rays):
+    room = synth.box_room(seed)
+    gt = synth.box_room_gt_pose(room, seed + 100)
+    sc = synth.scan(room, gt, synth.spherical_dirs(n_rays), 0.02, seed + 200)
+    parts = synth.box_room_particles(n_part, seed + 300, room.half)
+    return room, sc, parts
+
+
+def test_likelihood_split_matches_unsplit():
+    from paper_2404_16370_gb300 import mp
+    room, sc, parts = _room_instance(1, 4096, 2048)
+    ctx = mp.mp_init_map(room.map_points, mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, 4096))
+    try:
+        mp.mp_init_particles(ctx, 4096, poses=parts)
+        mp.mp_set_scan(ctx, sc)
+        mp.mp_run_stages(ctx, mp.MP_STAGE_SCAN | mp.MP_STAGE_LSH | mp.MP_STAGE_SORT)
+        out = {}
+        for split in (1, 3, 8):
+            mp.mp_set_likelihood_split(ctx, split)
+            mp.mp_run_stages(ctx, mp.MP_STAGE_LIKELIHOOD)
+            out[split] = mp.mp_get_buffer(ctx, mp.MP_BUF_GN).astype(np.float64)
+    finally:
+        mp.mp_destroy(ctx)
+    ref = out[1]
+    scale = np.abs(ref).max(axis=0, keepdims=True) + 1e-6
+    for split in (3, 8):
+        assert np.array_equal(out[split][:, 28], ref[:, 28])      # inlier counts: exact
+        assert np.all(np.abs(out[split] - ref) <= 2e-5 * scale)
+
+
+def _instances(torch, specs):
+    from paper_2404_16370_gb300 import mp
+    ctxs, streams, data = [], [], []
+    for seed, n_part, n_rays in specs:
+        room, sc, parts = _room_instance(seed, n_part, n_rays)
+        st = mp.mp_stream_create()
+        ctx = mp.mp_init_map(room.map_points, mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, n_part),
+                             cuda_stream=st)
+        mp.mp_init_particles(ctx, n_part, poses=parts)
+        ctxs.append(ctx)
+        streams.append(st)
+        data.append((sc, parts))
+    return ctxs, streams, data
+
+
+SPECS = [(1, 1024, 512), (2, 3000, 700), (3, 4096, 512)]
+
+
+def _odometry(n, step):
+    rng = np.random.default_rng(1000 + step)
+    T = np.tile(np.eye(4), (n, 1, 1))
+    T[:, :3, 3] = rng.normal(0, 0.02, (n, 3))
+    cov = np.tile(np.diag([1e-6] * 3 + [1e-4] * 3), (n, 1, 1))
+    return T, cov
+
+
+def test_batch_step_equals_sequential_steps(torch):
+    from paper_2404_16370_gb300 import mp
+    A, sa, data = _instances(torch, SPECS)
+    B, sb, _ = _instances(torch, SPECS)
+    origin = mp.mp_stream_create()
+    batch = mp.mp_batch_create(A, [len(d[0]) for d in data], origin)
+    try:
+        for step in range(3):
+            T, cov = _odometry(len(SPECS), step)
+            mp.mp_batch_step(batch, [d[0] for d in data], T, cov)
+            for i, ctx in enumerate(B):
+                mp.mp_step(ctx, data[i][0], T[i], cov[i])
+        for i in range(len(SPECS)):
+            assert mp.mp_batch_split(batch, i) == 1
+            pa, prob_a = mp.mp_get_posterior(A[i])
+            pb, prob_b = mp.mp_get_posterior(B[i])
+            for which in (mp.MP_BUF_POSES, mp.MP_BUF_POST, mp.MP_BUF_NBR_IDS):
+                assert np.array_equal(mp.mp_get_buffer(A[i], which), mp.mp_get_buffer(B[i], which)), (i, which)
+            assert np.array_equal(pa, pb) and prob_a == prob_b
+    finally:
+        mp.mp_batch_destroy(batch)
+        for c in A + B:
+            mp.mp_destroy(c)
+        for st in sa + sb + [origin]:
+            mp.mp_stream_destroy(st)
+
+
+def test_autotuned_batch_runs(torch):
+    from paper_2404_16370_gb300 import mp
+    specs = [(4, 2048, 4096), (5, 8192, 2048), (6, 1024, 512)]
+    A, sa, data = _instances(torch, specs)
+    origin = mp.mp_stream_create()
+    batch = mp.mp_batch_create(A, [len(d[0]) for d in data], origin, tune_scans=[d[0] for d in data])
+    try:
+        splits = [mp.mp_batch_split(batch, i) for i in range(len(specs))]
+        assert all(s in (1, 2, 4, 8, 16) for s in splits)
+        for step in range(4):
+            mp.mp_batch_step(batch, [d[0] for d in data])
+        for i, ctx in enumerate(A):
+            post = mp.mp_get_buffer(ctx, mp.MP_BUF_POST)
+            assert np.isfinite(post).all() and abs(post.sum() - 1) < 1e-9
+        print("\nsplits", splits)
+    finally:
+        mp.mp_batch_destroy(batch)
+        for c in A:
+            mp.mp_destroy(c)
+        for st in sa + [origin]:
+            mp.mp_stream_destroy(st)
