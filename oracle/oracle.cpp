@@ -1043,6 +1043,150 @@ void or_neighbor_merge(const float* poses, i64 np, const int32_t* old_ids, int K
   }
 }
 
+// ---- Scan-to-scan GICP odometry (Sec. III-B) ----
+// Registers the current scan src (sensor frame at t) to the previous scan tgt
+// (sensor frame at t-1): T = (R, t) maps src points into the tgt frame, so T
+// estimates DeltaT_t = T_{t-1}^-1 T_t. Each iteration, for the current T:
+//   * decisions in FP32: T's unit quaternion and translation rounded to
+//     float, q_k = R32 mu_k + t32 (D1, D2); the correspondence of source point
+//     k is the valid target point of smallest squared distance (D3), ties to
+//     the smaller index, if that distance is <= r_corr^2;
+//   * FP64 sums over the correspondences: e = mu^tgt - (R mu + t),
+//     Omega = (Sigma^tgt + R Sigma^src R^T)^-1 (GICP planes),
+//     J = R [ [mu]x , -I ] (right perturbation), H = sum J^T Omega J,
+//     b = sum J^T Omega e (no truncation);
+//   * delta = -(H + lambda diag H + eps I)^-1 b, T <- T exp(delta); stop when
+//     max |delta_a| < tol or after max_iters iterations.
+// Outputs the final T (4x4 row-major) and H of the last iteration (21 upper
+// entries; Sigma^DeltaT = H^-1 is taken by the caller).
+int or_gicp(const float* src, const double* src_n, const uint8_t* src_valid, i64 ns, const float* tgt,
+            const double* tgt_n, const uint8_t* tgt_valid, i64 nt, const double* T0, double r_corr, double eps_cov,
+            double lambda, double eps, int max_iters, double tol, double* T_out, double* H_out, int32_t* n_corr,
+            int32_t* iters) {
+  double R0[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) R0[3 * r + c] = T0[4 * r + c];
+  Pose T;
+  T.q = qnormalize(R_to_quat(R0));
+  for (int a = 0; a < 3; ++a) T.t[a] = T0[4 * a + 3];
+  const float r2 = (float)(r_corr * r_corr);
+  double Hl[21] = {0};
+  int cnt = 0, it = 0;
+  std::vector<int> corr(ns);
+  for (it = 0; it < max_iters; ++it) {
+    // decisions on the FP32 rounding of T
+    Quat qn = qnormalize(T.q);
+    float P32[7] = {(float)qn.x, (float)qn.y, (float)qn.z, (float)qn.w, (float)T.t[0], (float)T.t[1], (float)T.t[2]};
+    float R32[9];
+    R32_of(P32, R32);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (i64 k = 0; k < ns; ++k) {
+      corr[k] = -1;
+      if (src_valid && !src_valid[k]) continue;
+      float q32[3];
+      transform32(R32, P32 + 4, src + 3 * k, q32);
+      float best = INFINITY;
+      int bj = -1;
+      for (i64 j = 0; j < nt; ++j) {
+        if (tgt_valid && !tgt_valid[j]) continue;
+        float d2 = dist2_32(q32, tgt + 3 * j);
+        if (d2 < best) { best = d2; bj = (int)j; }
+      }
+      if (bj >= 0 && best <= r2) corr[k] = bj;
+    }
+    // FP64 sums
+    double R[9];
+    quat_to_R(qn, R);
+    double b[6] = {0};
+    for (int a = 0; a < 21; ++a) Hl[a] = 0;
+    cnt = 0;
+    for (i64 k = 0; k < ns; ++k) {
+      int m = corr[k];
+      if (m < 0) continue;
+      double mus[3] = {src[3 * k], src[3 * k + 1], src[3 * k + 2]};
+      double qk[3];
+      matvec3(R, mus, qk);
+      double e[3];
+      for (int a = 0; a < 3; ++a) e[a] = (double)tgt[3 * m + a] - (qk[a] + T.t[a]);
+      double SM[9], SS[9], RS[9], RSRt[9], Rt[9], C[9], Om[9];
+      gicp_cov(tgt_n + 3 * m, eps_cov, SM);
+      gicp_cov(src_n + 3 * k, eps_cov, SS);
+      for (int r = 0; r < 3; ++r) for (int c = 0; c < 3; ++c) Rt[3 * r + c] = R[3 * c + r];
+      matmul3(R, SS, RS);
+      matmul3(RS, Rt, RSRt);
+      for (int a = 0; a < 9; ++a) C[a] = SM[a] + RSRt[a];
+      if (!inv3(C, Om)) continue;
+      cnt++;
+      double Oe[3];
+      matvec3(Om, e, Oe);
+      double S[9], J0[9], J[3][6];
+      skew(mus, S);
+      matmul3(R, S, J0);
+      for (int r = 0; r < 3; ++r)
+        for (int c2 = 0; c2 < 3; ++c2) { J[r][c2] = J0[3 * r + c2]; J[r][3 + c2] = -R[3 * r + c2]; }
+      for (int a = 0; a < 6; ++a) {
+        for (int bb = a; bb < 6; ++bb) {
+          double sacc = 0;
+          for (int r = 0; r < 3; ++r)
+            sacc += J[r][a] * (Om[3 * r] * J[0][bb] + Om[3 * r + 1] * J[1][bb] + Om[3 * r + 2] * J[2][bb]);
+          Hl[H_IDX[a][bb]] += sacc;
+        }
+        double sacc = 0;
+        for (int r = 0; r < 3; ++r) sacc += J[r][a] * Oe[r];
+        b[a] += sacc;
+      }
+    }
+    // damped Gauss-Newton step
+    double A[36], d[6];
+    for (int a = 0; a < 6; ++a)
+      for (int c = 0; c < 6; ++c) A[6 * a + c] = Hl[H_IDX[a][c]];
+    for (int a = 0; a < 6; ++a) A[7 * a] += lambda * A[7 * a] + eps;
+    // Gaussian elimination with partial pivoting on the 6x6 system A d = -b
+    double M[6][7];
+    for (int a = 0; a < 6; ++a) {
+      for (int c = 0; c < 6; ++c) M[a][c] = A[6 * a + c];
+      M[a][6] = -b[a];
+    }
+    bool ok = cnt >= 6;
+    for (int c = 0; c < 6 && ok; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < 6; ++r)
+        if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+      if (!(std::fabs(M[piv][c]) > 0)) { ok = false; break; }
+      if (piv != c) for (int k = 0; k < 7; ++k) std::swap(M[c][k], M[piv][k]);
+      for (int r = c + 1; r < 6; ++r) {
+        double f = M[r][c] / M[c][c];
+        for (int k = c; k < 7; ++k) M[r][k] -= f * M[c][k];
+      }
+    }
+    if (!ok) break;
+    for (int r = 5; r >= 0; --r) {
+      double v = M[r][6];
+      for (int k = r + 1; k < 6; ++k) v -= M[r][k] * d[k];
+      d[r] = v / M[r][r];
+    }
+    T = compose(T, se3_exp(d));
+    T.q = qnormalize(T.q);
+    double mx = 0;
+    for (int a = 0; a < 6; ++a) mx = std::max(mx, std::fabs(d[a]));
+    if (mx < tol) { ++it; break; }
+  }
+  double R[9];
+  quat_to_R(qnormalize(T.q), R);
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) T_out[4 * r + c] = R[3 * r + c];
+    T_out[4 * r + 3] = T.t[r];
+  }
+  T_out[12] = T_out[13] = T_out[14] = 0.0;
+  T_out[15] = 1.0;
+  if (H_out) for (int a = 0; a < 21; ++a) H_out[a] = Hl[a];
+  if (n_corr) *n_corr = cnt;
+  if (iters) *iters = it;
+  return 0;
+}
+
 // ---- SVGD update (Sec. III-C Eq. 5 and 6) ----
 // phi_i = sum_j (k_ij psi_j + grad_{T_j} k(T_i, T_j)) / sum_j k_ij over the
 // list of i, with grad_{T_j} k = -2 k_ij W^K d_ij (d_ij in T_i's tangent

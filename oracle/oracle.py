@@ -84,6 +84,8 @@ def _declare(L):
     L.or_bucket_sort.argtypes = [_P, _I64, _P, _P, _P, _P]
     L.or_neighbor_merge.argtypes = [_P, _I64, _P, _INT, _INT, _P, _P, _P, _P, _D, _D, _D, _P, _I64, _P, _P, _P, _P, _INT]
     L.or_svgd.argtypes = [_P, _I64, _P, _P, _P, _INT, _P, _D, _D, _P, _P, _P]
+    L.or_gicp.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _I64, _P, _D, _D, _D, _D, _INT, _D, _P, _P, _P, _P]
+    L.or_gicp.restype = _INT
     L.or_posterior.argtypes = [_P, _P, _I64, _P, _P, _INT, _INT, _P, _P, _P]
     L.or_cholesky6.argtypes = [_P, _P]
     L.or_predict_noise.argtypes = [_I64, _U64, _U64, _P]
@@ -330,6 +332,29 @@ def svgd(poses, ids, kk, dd, psi, params: Params, pinv=None):
     lib().or_svgd(_p(poses), npart, _p(_c(ids, np.int32)), _p(_c(kk, np.float64)), _p(_c(dd, np.float64)), K,
                   _p(_c(psi, np.float64)), params.sigma_r, params.sigma_t, _p(pv), _p(phi), _p(out))
     return phi, out
+
+
+def gicp(src, tgt, params: Params, T0=None, max_iters=30, tol=1e-6, r_corr=None, nthreads=0):
+    """Scan-to-scan GICP (Sec. III-B): DeltaT mapping the current scan src into
+    the previous scan tgt's frame, the Gauss-Newton H of the last iteration and
+    Sigma^DeltaT = H^-1. Point Gaussians from point_normals with the params'
+    r_cov / cov_k / cov_min; correspondences within r_corr (default r_max)."""
+    src = _c(src, np.float32).reshape(-1, 3)
+    tgt = _c(tgt, np.float32).reshape(-1, 3)
+    sn, sv, _, _ = point_normals(src, params.r_cov, params.cov_k, params.cov_min, nthreads=nthreads)
+    tn, tv, _, _ = point_normals(tgt, params.r_cov, params.cov_k, params.cov_min, nthreads=nthreads)
+    T0 = np.eye(4) if T0 is None else _c(T0, np.float64)
+    T = np.zeros(16); H = np.zeros(21); nc = np.zeros(1, np.int32); it = np.zeros(1, np.int32)
+    lib().or_gicp(_p(src), _p(_c(sn, np.float64)), _p(_c(sv, np.uint8)), len(src), _p(tgt),
+                  _p(_c(tn, np.float64)), _p(_c(tv, np.uint8)), len(tgt), _p(_c(T0, np.float64).reshape(16)),
+                  float(params.r_max if r_corr is None else r_corr), params.eps_cov, params.lam, params.eps_damp,
+                  int(max_iters), float(tol), _p(T), _p(H), _p(nc), _p(it))
+    Hm = np.zeros((6, 6))
+    Hm[np.triu_indices(6)] = H
+    Hm = Hm + np.triu(Hm, 1).T
+    with np.errstate(all="ignore"):
+        cov = np.linalg.inv(Hm) if nc[0] >= 6 else np.full((6, 6), np.nan)
+    return dict(T=T.reshape(4, 4), H=H, cov=cov, n_corr=int(nc[0]), iters=int(it[0]))
 
 
 def svgd_precond_matrices(H, ok, params: Params):
