@@ -230,6 +230,27 @@ int mp_set_precision(mp_ctx* ctx, int precision);
  * SMs); mp_batch_create picks it per instance by timing. */
 int mp_set_likelihood_split(mp_ctx* ctx, int split);
 
+/* ---- Scan-to-scan GICP odometry (Sec. III-B, prediction step) ----------
+ * mp_gicp registers scan src (n_src x 3, sensor frame at t) to scan tgt
+ * (n_tgt x 3, sensor frame at t-1), host or device pointers: T_out (4x4
+ * row-major) maps src points into the tgt frame, i.e. DeltaT_t = T_{t-1}^-1
+ * T_t; cov_out (6x6 row-major, may be NULL) = H^-1, the inverse of the
+ * Gauss-Newton Hessian sum J^T Omega J at the last iteration (rotation-first
+ * twist). Point Gaussians as for scans (cov_k, cov_min, r_cov, eps_cov);
+ * each src point with a Gaussian takes the nearest tgt point with a Gaussian
+ * (FP32 decisions on T rounded to float, ties to the smaller index) within
+ * r_max; damped Gauss-Newton (lambda, eps) from init_T (NULL: identity) for at
+ * most max_iters iterations, stopping once every step component is below
+ * 1e-6. n_corr / iters (may be NULL) receive the correspondences and the
+ * iterations of the last step. Synchronises. MP_EINVAL when fewer than 6
+ * correspondences remain or the system is singular.
+ * mp_step_gicp: mp_step with odometry from mp_gicp against the previous
+ * scan given to it (first scan, and the first after an empty one: no motion),
+ * started from the previous motion estimate, covariance scaled by cov_scale. */
+int mp_gicp(mp_ctx* ctx, const float* src, int32_t n_src, const float* tgt, int32_t n_tgt, const double init_T[16],
+            int32_t max_iters, double T_out[16], double cov_out[36], int32_t* n_corr, int32_t* iters);
+int mp_step_gicp(mp_ctx* ctx, const float* scan, int32_t n_scan, double cov_scale);
+
 /* ---- Batched instances ------------------------------------------------
  * Many independent contexts (each with its own map, particles and CUDA
  * stream) stepped together: mp_batch_create captures one full step of every

@@ -530,6 +530,19 @@ int mp_launch_scan_prepare(mp_ctx* c) {
     return MP_OK;
 }
 
+// Point Gaussians of an arbitrary point array (the scan-Gaussian kernels
+// without the compaction): normals and validity of n points raw_dev (n x 3).
+int mp_launch_point_gaussians(mp_ctx* c, const float* raw_dev, int n, float4* tmp4, float* normals, uint8_t* valid) {
+    if (n == 0) return MP_OK;
+    k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(raw_dev, n, tmp4);
+    MP_LAUNCHED(c);
+    float r2 = c->p.r_cov * c->p.r_cov;
+    k_scan_normals<<<grid_for(n, 256), 256, 0, c->stream>>>(raw_dev, n, r2, c->p.cov_k, c->p.cov_min, tmp4, normals,
+                                                             valid);
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
 int mp_launch_nnf_query(mp_ctx* c, const int32_t* vox_dev, int64_t m, int32_t* out_dev) {
     if (m == 0) return MP_OK;
     k_nnf_query<<<grid_for(m, 256), 256, 0, c->stream>>>(c->nnf, c->map_perm, c->nnf_dims[0], c->nnf_dims[1],

@@ -185,6 +185,7 @@ void destroy(mp_ctx* c) {
     dfree(c->scan_nvalid);
     dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->pairs);
     dfree(c->step_dev);
+    mp_gicp_free(c);
     if (c->step_host) cudaFreeHost(c->step_host);
     for (int k = 0; k < 2; ++k)
         if (c->step_ev[k]) cudaEventDestroy(c->step_ev[k]);
@@ -237,6 +238,20 @@ void odom_to_pose(const double T[16], double q[4], double t[3]) {
     q[0] = x / nrm; q[1] = y / nrm; q[2] = z / nrm; q[3] = w / nrm;
     t[0] = T[3]; t[1] = T[7]; t[2] = T[11];
 }
+
+}  // namespace
+
+void odom_to_pose_host(const double T[16], double q[4], double t[3]) {
+    if (!T) {
+        q[0] = q[1] = q[2] = 0.0;
+        q[3] = 1.0;
+        t[0] = t[1] = t[2] = 0.0;
+        return;
+    }
+    odom_to_pose(T, q, t);
+}
+
+namespace {
 
 // Lower Cholesky factor of a symmetric PSD 6x6, column by column; a column
 // whose pivot is not positive is left zero (no noise along it).

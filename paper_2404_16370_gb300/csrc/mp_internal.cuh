@@ -135,6 +135,7 @@ struct mp_ctx {
     // test knobs of the failure path
     int precision;           // MP_PREC_* of the likelihood stage
     int lk_split;            // CTAs sharing the scan of one particle block (FP32 likelihood; 0/1 = none)
+    struct GicpBufs* gicp;   // scan-to-scan odometry buffers (allocated at first use)
     uint4* scan_h2;          // 2 per valid point: the scan as 16-bit broadcast pairs (precision != FP32)
     long long wait_budget;   // cycles; 0 = MP_WAIT_BUDGET
     int starve_tx;
@@ -406,10 +407,13 @@ static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + b
 // launchers (each returns MP_OK or an error code recorded in ctx)
 // k_map.cu
 void draw_lsh(mp_ctx* c);
+void odom_to_pose_host(const double T[16], double q[4], double t[3]);   // identity for NULL
+void mp_gicp_free(mp_ctx* c);
 void fill_step_host(mp_ctx* c, StepDev* h);
 int upload_step(mp_ctx* c);
 int mp_launch_map_prepare(mp_ctx* c, const float* xyz_dev);
 int mp_launch_scan_prepare(mp_ctx* c);
+int mp_launch_point_gaussians(mp_ctx* c, const float* raw_dev, int n, float4* tmp4, float* normals, uint8_t* valid);
 int mp_launch_nnf_query(mp_ctx* c, const int32_t* vox_dev, int64_t m, int32_t* out_dev);
 // k_neighbors.cu
 int mp_launch_lsh_keys(mp_ctx* c);

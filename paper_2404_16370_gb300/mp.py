@@ -493,3 +493,38 @@ def mp_stream_destroy(stream):
     rc = L.mp_stream_destroy(C.c_void_p(stream))
     if rc != MP_OK:
         raise MPError(rc, "mp_stream_destroy failed")
+
+
+# ---------------------------------------------------------------------------
+# scan-to-scan GICP odometry
+
+
+def mp_gicp(ctx, src, tgt, init_T=None, max_iters=30):
+    """DeltaT (4x4) mapping src (current scan) into tgt's frame (previous scan),
+    Sigma^DeltaT = H^-1 (6x6), correspondences and iterations."""
+    L = lib()
+    L.mp_gicp.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
+                          C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.mp_gicp.restype = C.c_int
+    sp, ks = _ptr(src, np.float32)
+    tp, kt = _ptr(tgt, np.float32)
+    T0 = None if init_T is None else np.ascontiguousarray(init_T, np.float64)
+    T = np.zeros(16)
+    cov = np.zeros(36)
+    nc, it = C.c_int32(), C.c_int32()
+    _check(L.mp_gicp(ctx, sp, int(src.shape[0]), tp, int(tgt.shape[0]),
+                     None if T0 is None else T0.ctypes.data_as(C.c_void_p), int(max_iters),
+                     T.ctypes.data_as(C.c_void_p), cov.ctypes.data_as(C.c_void_p), C.byref(nc), C.byref(it)), ctx)
+    return dict(T=T.reshape(4, 4), cov=cov.reshape(6, 6), n_corr=int(nc.value), iters=int(it.value))
+
+
+def mp_step_gicp(ctx, scan, cov_scale=1.0):
+    """mp_step with GICP odometry against the previous scan given here."""
+    L = lib()
+    L.mp_step_gicp.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_double]
+    L.mp_step_gicp.restype = C.c_int
+    if scan is None or len(scan) == 0:
+        _check(L.mp_step_gicp(ctx, None, 0, float(cov_scale)), ctx)
+        return
+    sp, keep = _ptr(scan, np.float32)
+    _check(L.mp_step_gicp(ctx, sp, int(scan.shape[0]), float(cov_scale)), ctx)
