@@ -283,7 +283,9 @@ __device__ __forceinline__ LkAcc lk2_half(const LkArgs& A, const Lk2Acc& S, int 
     return o;
 }
 
-template <int MINB>
+// SPLIT: the scan is shared by gridDim.y CTAs per particle block (partial sums
+// added atomically); without it the loop is the plain one.
+template <int MINB, bool SPLIT>
 __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A) {
     __shared__ __align__(128) float4 buf[2][3 * LK_CHUNK];
     __shared__ __align__(8) uint64_t bar[2];
@@ -313,8 +315,8 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
     const int nv = *A.nvalid;
     const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
     // scan split: this CTA takes chunks blockIdx.y, blockIdx.y + split, ...
-    const int split = A.split, by = blockIdx.y;
-    const int nmine = by < nchunks ? (nchunks - by + split - 1) / split : 0;
+    const int split = SPLIT ? A.split : 1, by = SPLIT ? (int)blockIdx.y : 0;
+    const int nmine = SPLIT ? (by < nchunks ? (nchunks - by + split - 1) / split : 0) : nchunks;
     if (blockIdx.x == 0 && by == 0 && threadIdx.x == 0)
         atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
     if (threadIdx.x == 0) {
@@ -396,12 +398,12 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
     if (acta) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rs[k] = R[k].x;
-        lk_store(A, Rs, lk2_half(A, S, 0, nv_mine), pa, split > 1);
+        lk_store(A, Rs, lk2_half(A, S, 0, SPLIT ? nv_mine : nv), pa, SPLIT);
     }
     if (actb) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) Rs[k] = R[k].y;
-        lk_store(A, Rs, lk2_half(A, S, 1, nv_mine), pb, split > 1);
+        lk_store(A, Rs, lk2_half(A, S, 1, SPLIT ? nv_mine : nv), pb, SPLIT);
     }
 }
 
@@ -725,8 +727,12 @@ int mp_launch_likelihood(mp_ctx* c) {
         // the scan split (a tuning knob for small particle counts): partial
         // sums of each CTA are added into a zeroed output
         A.split = c->lk_split > 1 ? c->lk_split : 1;
-        if (A.split > 1) MP_CUDA(c, cudaMemsetAsync(c->gn, 0, sizeof(float) * MP_GN * (size_t)c->cap, c->stream));
-        k_likelihood<LK_MINB><<<dim3(grid, A.split), LK_THREADS, 0, c->stream>>>(A);
+        if (A.split > 1) {
+            MP_CUDA(c, cudaMemsetAsync(c->gn, 0, sizeof(float) * MP_GN * (size_t)c->cap, c->stream));
+            k_likelihood<LK_MINB, true><<<dim3(grid, A.split), LK_THREADS, 0, c->stream>>>(A);
+        } else {
+            k_likelihood<LK_MINB, false><<<grid, LK_THREADS, 0, c->stream>>>(A);
+        }
     }
     MP_LAUNCHED(c);
     return MP_OK;

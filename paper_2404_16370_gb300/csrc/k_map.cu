@@ -59,8 +59,11 @@ __global__ void k_cell_fill(const int32_t* __restrict__ cell_of, int64_t n, cons
     items[start[c] + pos] = (int32_t)i;
 }
 
-// Sorted insertion of (d, j) into the MP_COVK smallest pairs seen so far.
+// Sorted insertion of (d, j) into the MP_COVK smallest pairs seen so far
+// (order: d, then j). A pair that does not precede the current last one
+// cannot enter, and is rejected before the insertion chain.
 __device__ __forceinline__ void topk_insert(float (&D)[MP_COVK], int (&J)[MP_COVK], float d, int j) {
+    if (!(d < D[MP_COVK - 1] || (d == D[MP_COVK - 1] && j < J[MP_COVK - 1]))) return;
 #pragma unroll
     for (int s = 0; s < MP_COVK; ++s) {
         bool lt = (d < D[s]) || (d == D[s] && j < J[s]);
@@ -188,8 +191,11 @@ __global__ void k_map_normals(const float4* __restrict__ pts, int64_t n, CellGri
 }
 
 // Scan points: brute force over the whole scan, staged through shared memory.
+// 64 threads a CTA: a scan of a few thousand points then spreads over as many
+// CTAs as the GPU has SMs.
 #define SCAN_TILE 1024
-__global__ void __launch_bounds__(256) k_scan_normals(const float* __restrict__ raw, int n, float r2, int k, int kmin,
+#define SCAN_CTA 64
+__global__ void __launch_bounds__(SCAN_CTA) k_scan_normals(const float* __restrict__ raw, int n, float r2, int k, int kmin,
                                                       float4* __restrict__ tmp_pts, float* __restrict__ normals,
                                                       uint8_t* __restrict__ valid) {
     __shared__ float sx[SCAN_TILE], sy[SCAN_TILE], sz[SCAN_TILE];
@@ -521,7 +527,7 @@ int mp_launch_scan_prepare(mp_ctx* c) {
     k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(c->scan_raw, n, tmp);
     MP_LAUNCHED(c);
     float r2 = c->p.r_cov * c->p.r_cov;
-    k_scan_normals<<<grid_for(n, 256), 256, 0, c->stream>>>(c->scan_raw, n, r2, c->p.cov_k, c->p.cov_min, tmp,
+    k_scan_normals<<<grid_for(n, SCAN_CTA), SCAN_CTA, 0, c->stream>>>(c->scan_raw, n, r2, c->p.cov_k, c->p.cov_min, tmp,
                                                              c->scan_normals, c->scan_valid);
     MP_LAUNCHED(c);
     k_scan_compact<<<1, 1024, 0, c->stream>>>(c->scan_raw, c->scan_normals, c->scan_valid, n, c->scan_pair,
@@ -537,8 +543,8 @@ int mp_launch_point_gaussians(mp_ctx* c, const float* raw_dev, int n, float4* tm
     k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(raw_dev, n, tmp4);
     MP_LAUNCHED(c);
     float r2 = c->p.r_cov * c->p.r_cov;
-    k_scan_normals<<<grid_for(n, 256), 256, 0, c->stream>>>(raw_dev, n, r2, c->p.cov_k, c->p.cov_min, tmp4, normals,
-                                                             valid);
+    k_scan_normals<<<grid_for(n, SCAN_CTA), SCAN_CTA, 0, c->stream>>>(raw_dev, n, r2, c->p.cov_k, c->p.cov_min, tmp4,
+                                                                       normals, valid);
     MP_LAUNCHED(c);
     return MP_OK;
 }

@@ -1,8 +1,9 @@
 // Posterior propagation on the neighbour-particle graph (Sec. III-D, Eq. 11)
 // and the representative state:
 //   l_i = log prior_i + log p(P | x_i); p_i = exp(l_i - max l) (FP64);
-//   post_iters Jacobi sweeps p'_i = sum_j k_ij p_j / sum_j k_ij over the list
-//   of i (one thread per particle, FP64 fused multiply-adds);
+//   post_iters Jacobi sweeps p'_i = sum_j w_ij p_j over the list of i with
+//   w_ij = k_ij / sum_j k_ij fixed for the step (one thread per particle, FP64
+//   fused multiply-adds);
 //   normalise; best = argmax (smallest index on ties); log prior <- log p'.
 // Grid-wide max / sum / argmax are two-level (block partials, one final
 // block), so results do not depend on atomics' order.
@@ -90,37 +91,53 @@ __global__ void __launch_bounds__(1024) k_reduce_sum(const double* __restrict__ 
     }
 }
 
-// 1 / sum_j k_ij (FP64), fixed for the sweeps of a step
-__global__ void k_post_invden(int64_t n, int K, const int32_t* __restrict__ ids, const float* __restrict__ kk,
-                              double* __restrict__ inv_den) {
+// Normalised weights w_ij = k_ij / sum_j k_ij (FP64) and 1 / sum_j k_ij,
+// fixed for the sweeps of a step: a sweep entry is then one FP64 fused
+// multiply-add (GB300's FP64 rate is low, so the division and the FP32 -> FP64
+// conversion are taken out of the ten sweeps).
+__global__ void k_post_weights(int64_t n, int K, const int32_t* __restrict__ ids, const float* __restrict__ kk,
+                               double* __restrict__ w, double* __restrict__ inv_den) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     double den = 0.0;
     for (int l = 0; l < K; ++l)
         if (ids[i * K + l] >= 0) den += (double)kk[i * K + l];
-    inv_den[i] = den > 0.0 ? 1.0 / den : 0.0;
+    const double inv = den > 0.0 ? 1.0 / den : 0.0;
+    for (int l = 0; l < K; ++l) w[i * K + l] = ids[i * K + l] >= 0 ? (double)kk[i * K + l] * inv : 0.0;
+    inv_den[i] = inv;
 }
 
-// One Jacobi sweep of Eq. 11, one thread per particle: FP64 fused
-// multiply-adds over the list (GB300's FP64 rate is low, so the list is not
-// spread over lanes: that would cost a shuffle-add tree per particle).
+// One Jacobi sweep of Eq. 11, one thread per particle: p'_i = sum_j w_ij p_j
+// with FP64 fused multiply-adds over the list (rows read with 16-byte loads
+// when the list length is a multiple of 4); a particle whose kernel weights
+// sum to zero keeps its value.
 template <int KT>
 __global__ void __launch_bounds__(256) k_post_sweep(const double* __restrict__ pin, double* __restrict__ pout, int64_t n,
                                                     int Krt, const int32_t* __restrict__ ids,
-                                                    const float* __restrict__ kk, const double* __restrict__ inv_den) {
+                                                    const double* __restrict__ w, const double* __restrict__ inv_den) {
     const int K = KT > 0 ? KT : Krt;   // compile-time list length for the common sizes
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int32_t* row = ids + i * K;
-    const float* kr = kk + i * K;
     double num = 0.0;
-#pragma unroll 8
-    for (int l = 0; l < K; ++l) {
-        int j = __ldg(row + l);
-        if (j >= 0) num = fma((double)__ldg(kr + l), __ldg(pin + j), num);
+    if (KT > 0 && KT % 4 == 0) {
+        const int4* row = reinterpret_cast<const int4*>(ids + i * KT);
+        const double2* wr = reinterpret_cast<const double2*>(w + i * KT);
+#pragma unroll
+        for (int q = 0; q < KT / 4; ++q) {
+            const int4 j4 = __ldg(row + q);
+            const double2 w0 = __ldg(wr + 2 * q), w1 = __ldg(wr + 2 * q + 1);
+            if (j4.x >= 0) num = fma(w0.x, __ldg(pin + j4.x), num);
+            if (j4.y >= 0) num = fma(w0.y, __ldg(pin + j4.y), num);
+            if (j4.z >= 0) num = fma(w1.x, __ldg(pin + j4.z), num);
+            if (j4.w >= 0) num = fma(w1.y, __ldg(pin + j4.w), num);
+        }
+    } else {
+        for (int l = 0; l < K; ++l) {
+            const int j = __ldg(ids + i * K + l);
+            if (j >= 0) num = fma(__ldg(w + i * K + l), __ldg(pin + j), num);
+        }
     }
-    double inv = inv_den[i];
-    pout[i] = inv > 0.0 ? num * inv : pin[i];
+    pout[i] = inv_den[i] > 0.0 ? num : pin[i];
 }
 
 __global__ void __launch_bounds__(PB) k_post_final_part(const double* __restrict__ p, int64_t n,
@@ -214,7 +231,7 @@ template <int KT>
 int sweeps(mp_ctx* c, double*& a, double*& b, const double* inv_den) {
     for (int it = 0; it < c->p.post_iters; ++it) {
         k_post_sweep<KT><<<grid_for(c->n, 256), 256, 0, c->stream>>>(a, b, c->n, c->p.K, c->nbr_ids[c->nbr_cur],
-                                                                    c->nbr_k, inv_den);
+                                                                    c->post_w, inv_den);
         MP_LAUNCHED(c);
         double* t = a;
         a = b;
@@ -242,8 +259,8 @@ int mp_launch_posterior(mp_ctx* c) {
     MP_LAUNCHED(c);
     k_reduce_sum<<<1, 1024, 0, c->stream>>>(part, nb, &c->scalars[1]);
     MP_LAUNCHED(c);
-    k_post_invden<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->p.K, c->nbr_ids[c->nbr_cur], c->nbr_k,
-                                                           c->post_invden);
+    k_post_weights<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->p.K, c->nbr_ids[c->nbr_cur], c->nbr_k, c->post_w,
+                                                            c->post_invden);
     MP_LAUNCHED(c);
     double* a = c->post_tmp;
     double* b = c->post;

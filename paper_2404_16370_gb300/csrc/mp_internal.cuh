@@ -65,6 +65,7 @@ struct mp_ctx {
     double* post_tmp;
     double* post_init;      // unnormalised initial posterior exp(l - max l)
     double* post_invden;    // 1 / sum_j k_ij of the current lists
+    double* post_w;         // K per particle: k_ij / sum_j k_ij (FP64), fixed for a step's sweeps
     float* loglik;
     int32_t* n_in;
     uint32_t* keys;
