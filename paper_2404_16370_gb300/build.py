@@ -1,7 +1,13 @@
 """Builds libmp.so (the CUDA library behind include/megaparticles.h) in-tree
 for sm_103a: one nvcc job per translation unit, in parallel, then a shared
 link. Host code is compiled without floating-point contraction (the NNF
-geometry is an FP32 decision sequence)."""
+geometry is an FP32 decision sequence).
+
+build(checked=True) (or `python -m paper_2404_16370_gb300.build --checked`)
+makes libmp_checked.so with -DMP_CHECKED instead: kernels bound-check the
+indices they read from data and every launch is synchronised, so that a fault
+is reported at the kernel that caused it. mp.py loads it when MP_CHECKED=1 is
+set in the environment. It is a debugging aid, several times slower."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -15,6 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmp.so")
+LIB_CHECKED = os.path.join(HERE, "libmp_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", os.path.join(os.path.dirname(HERE), "include")]
@@ -34,13 +41,15 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked: bool = False) -> str:
+    build_dir = BUILD + "_checked" if checked else BUILD
+    lib = LIB_CHECKED if checked else LIB
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
         glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DMP_CHECKED"] if checked else [])
 
     def compile_one(src_obj):
         src, obj = src_obj
@@ -58,16 +67,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for lg in logs:
             if lg:
                 sys.stderr.write(lg)
-    if force or ptxas_info or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or ptxas_info or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -64,6 +64,8 @@ struct LkArgs {
     long long budget;   // cycle limit of each barrier wait
     int starve;         // test knob: announce 16 bytes more than copied for chunk 0
     int split;          // CTAs sharing the scan of one particle block (gridDim.y); > 1 adds atomically
+    int64_t n_rec;      // map records (checked builds test the NNF entries against it)
+    int scan_cap;       // scan capacity in points (checked builds test the valid count against it)
     // constants as pairs (both halves equal)
     float2 inv2, offx2, offy2, offz2, magic2, m1, half2, half_a2, nhalf_a2, two_eps2, two2, quarter_a2;
 };
@@ -160,15 +162,16 @@ __device__ __forceinline__ Lk2Look lk2_lookup(const LkArgs& A, const float2 R[9]
     const float2 fx = __fadd2_rd(fma2(L.qx, A.inv2, A.offx2), A.magic2);
     const float2 fy = __fadd2_rd(fma2(L.qy, A.inv2, A.offy2), A.magic2);
     const float2 fz = __fadd2_rd(fma2(L.qz, A.inv2, A.offz2), A.magic2);
-    const int vxa = __float_as_int(fx.x) - 0x4B400000, vxb = __float_as_int(fx.y) - 0x4B400000;
-    const int vya = __float_as_int(fy.x) - 0x4B400000, vyb = __float_as_int(fy.y) - 0x4B400000;
-    const int vza = __float_as_int(fz.x) - 0x4B400000, vzb = __float_as_int(fz.y) - 0x4B400000;
-    const bool ina = (unsigned)vxa < (unsigned)A.nx && (unsigned)vya < (unsigned)A.ny && (unsigned)vza < (unsigned)A.nz;
-    const bool inb = (unsigned)vxb < (unsigned)A.nx && (unsigned)vyb < (unsigned)A.ny && (unsigned)vzb < (unsigned)A.nz;
+    // unsigned arithmetic: an out-of-range voxel wraps to a large value
+    const unsigned vxa = __float_as_uint(fx.x) - 0x4B400000u, vxb = __float_as_uint(fx.y) - 0x4B400000u;
+    const unsigned vya = __float_as_uint(fy.x) - 0x4B400000u, vyb = __float_as_uint(fy.y) - 0x4B400000u;
+    const unsigned vza = __float_as_uint(fz.x) - 0x4B400000u, vzb = __float_as_uint(fz.y) - 0x4B400000u;
+    const bool ina = vxa < (unsigned)A.nx && vya < (unsigned)A.ny && vza < (unsigned)A.nz;
+    const bool inb = vxb < (unsigned)A.nx && vyb < (unsigned)A.ny && vzb < (unsigned)A.nz;
     L.ma = -1;
     L.mb = -1;
-    if (ina) L.ma = __ldg(A.nnf + ((vza * A.ny + vya) * A.nx + vxa));
-    if (inb) L.mb = __ldg(A.nnf + ((vzb * A.ny + vyb) * A.nx + vxb));
+    if (ina) L.ma = __ldg(A.nnf + (((int)vza * A.ny + (int)vya) * A.nx + (int)vxa));
+    if (inb) L.mb = __ldg(A.nnf + (((int)vzb * A.ny + (int)vyb) * A.nx + (int)vxb));
     return L;
 }
 
@@ -183,7 +186,7 @@ __device__ __forceinline__ Lk2Look lk2_none() {
 __device__ __forceinline__ void lk2_record(const LkArgs& A, int mm, float4& r0, float2& r1) {
     r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     r1 = make_float2(0.f, 0.f);
-    if (mm >= 0) {
+    if (mm >= 0 && MP_DCHECK(mm < A.n_rec, "NNF entry beyond the map records", mm)) {
         r0 = __ldg(A.rec + 2 * mm);
         r1 = __ldg(reinterpret_cast<const float2*>(A.rec + 2 * mm + 1));
     }
@@ -295,7 +298,9 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
     const int64_t pa = (int64_t)blockIdx.x * LK_PER_CTA + threadIdx.x;
     const int64_t pb = pa + LK_THREADS;
     const bool acta = pa < A.n, actb = pb < A.n;
-    const int64_t ia = acta ? A.order[pa] : 0, ib = actb ? A.order[pb] : 0;
+    int64_t ia = acta ? A.order[pa] : 0, ib = actb ? A.order[pb] : 0;
+    if (!MP_DCHECK(ia >= 0 && ia < A.n, "particle order entry", ia)) ia = 0;
+    if (!MP_DCHECK(ib >= 0 && ib < A.n, "particle order entry", ib)) ib = 0;
     float2 R[9];
     float2 tx, ty, tz;
     {
@@ -312,7 +317,8 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
         tz = make_float2(ta[2], tb[2]);
     }
 
-    const int nv = *A.nvalid;
+    int nv = *A.nvalid;
+    if (!MP_DCHECK(nv >= 0 && nv <= A.scan_cap, "valid scan points", nv)) nv = 0;
     const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
     // scan split: this CTA takes chunks blockIdx.y, blockIdx.y + split, ...
     const int split = SPLIT ? A.split : 1, by = SPLIT ? (int)blockIdx.y : 0;
@@ -327,6 +333,8 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
     __syncthreads();
     auto issue = [&](float4* dst, uint64_t* b, int cc) {
         int m = min(LK_CHUNK, nv - cc * LK_CHUNK);
+        if (!MP_DCHECK(cc >= 0 && m > 0 && ((reinterpret_cast<uintptr_t>(A.scan) & 15) == 0), "scan chunk", cc))
+            return;
         uint32_t bytes = (uint32_t)m * 48u;
         mbar_expect_tx(b, bytes + ((A.starve && cc == 0) ? 16u : 0u));
         bulk_g2s(dst, A.scan + 3 * (int64_t)cc * LK_CHUNK, bytes, b);
@@ -469,15 +477,16 @@ __device__ __forceinline__ Lk2Look lkh_lookup(const LkArgs& A, const H2 R[9], fl
     const float2 fx = __fadd2_rd(fma2(L.qx, A.inv2, A.offx2), A.magic2);
     const float2 fy = __fadd2_rd(fma2(L.qy, A.inv2, A.offy2), A.magic2);
     const float2 fz = __fadd2_rd(fma2(L.qz, A.inv2, A.offz2), A.magic2);
-    const int vxa = __float_as_int(fx.x) - 0x4B400000, vxb = __float_as_int(fx.y) - 0x4B400000;
-    const int vya = __float_as_int(fy.x) - 0x4B400000, vyb = __float_as_int(fy.y) - 0x4B400000;
-    const int vza = __float_as_int(fz.x) - 0x4B400000, vzb = __float_as_int(fz.y) - 0x4B400000;
-    const bool ina = (unsigned)vxa < (unsigned)A.nx && (unsigned)vya < (unsigned)A.ny && (unsigned)vza < (unsigned)A.nz;
-    const bool inb = (unsigned)vxb < (unsigned)A.nx && (unsigned)vyb < (unsigned)A.ny && (unsigned)vzb < (unsigned)A.nz;
+    // unsigned arithmetic: an out-of-range voxel wraps to a large value
+    const unsigned vxa = __float_as_uint(fx.x) - 0x4B400000u, vxb = __float_as_uint(fx.y) - 0x4B400000u;
+    const unsigned vya = __float_as_uint(fy.x) - 0x4B400000u, vyb = __float_as_uint(fy.y) - 0x4B400000u;
+    const unsigned vza = __float_as_uint(fz.x) - 0x4B400000u, vzb = __float_as_uint(fz.y) - 0x4B400000u;
+    const bool ina = vxa < (unsigned)A.nx && vya < (unsigned)A.ny && vza < (unsigned)A.nz;
+    const bool inb = vxb < (unsigned)A.nx && vyb < (unsigned)A.ny && vzb < (unsigned)A.nz;
     L.ma = -1;
     L.mb = -1;
-    if (ina) L.ma = __ldg(A.nnf + ((vza * A.ny + vya) * A.nx + vxa));
-    if (inb) L.mb = __ldg(A.nnf + ((vzb * A.ny + vyb) * A.nx + vxb));
+    if (ina) L.ma = __ldg(A.nnf + (((int)vza * A.ny + (int)vya) * A.nx + (int)vxa));
+    if (inb) L.mb = __ldg(A.nnf + (((int)vzb * A.ny + (int)vyb) * A.nx + (int)vxb));
     return L;
 }
 
@@ -571,7 +580,9 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood_h(const LkArgs 
     const int64_t pa = (int64_t)blockIdx.x * LK_PER_CTA + threadIdx.x;
     const int64_t pb = pa + LK_THREADS;
     const bool acta = pa < A.n, actb = pb < A.n;
-    const int64_t ia = acta ? A.order[pa] : 0, ib = actb ? A.order[pb] : 0;
+    int64_t ia = acta ? A.order[pa] : 0, ib = actb ? A.order[pb] : 0;
+    if (!MP_DCHECK(ia >= 0 && ia < A.n, "particle order entry", ia)) ia = 0;
+    if (!MP_DCHECK(ib >= 0 && ib < A.n, "particle order entry", ib)) ib = 0;
     H2 R[9];
     float2 tx, ty, tz;
     {
@@ -588,7 +599,8 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood_h(const LkArgs 
         tz = make_float2(ta[2], tb[2]);
     }
 
-    const int nv = *A.nvalid;
+    int nv = *A.nvalid;
+    if (!MP_DCHECK(nv >= 0 && nv <= A.scan_cap, "valid scan points", nv)) nv = 0;
     const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
     if (threadIdx.x == 0) {
@@ -599,6 +611,8 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood_h(const LkArgs 
     __syncthreads();
     auto issue = [&](uint4* dst, uint64_t* b, int cc) {
         int m = min(LK_CHUNK, nv - cc * LK_CHUNK);
+        if (!MP_DCHECK(cc >= 0 && m > 0 && ((reinterpret_cast<uintptr_t>(A.scan_h) & 15) == 0), "scan chunk", cc))
+            return;
         uint32_t bytes = (uint32_t)m * 32u;
         mbar_expect_tx(b, bytes + ((A.starve && cc == 0) ? 16u : 0u));
         bulk_g2s(dst, A.scan_h + 2 * (int64_t)cc * LK_CHUNK, bytes, b);
@@ -708,6 +722,8 @@ int mp_launch_likelihood(mp_ctx* c) {
     A.quarter_a2 = pair(0.25f * a);
     A.scan_h = c->scan_h2;
     A.split = 1;
+    A.n_rec = c->n_map;
+    A.scan_cap = c->p.max_scan;
     const unsigned grid = grid_for(c->n, LK_PER_CTA);
     if (c->precision == MP_PREC_BF16 || c->precision == MP_PREC_FP16) {
         if (c->n_scan > 0) {

@@ -231,6 +231,14 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan_normals(const float* __restri
         normals[3 * i] = normals[3 * i + 1] = normals[3 * i + 2] = 0.f;
         return;
     }
+#ifdef MP_CHECKED
+    for (int s = 0; s < m; ++s)
+        if (!MP_DCHECK(J[s] >= 0 && J[s] < n, "scan neighbour index", J[s])) m = 0;
+    if (m == 0) {
+        valid[i] = 0;
+        return;
+    }
+#endif
     float nv[3];
     neighbourhood_normal(tmp_pts, J, m, nv);
     normals[3 * i] = nv[0]; normals[3 * i + 1] = nv[1]; normals[3 * i + 2] = nv[2];
@@ -267,6 +275,7 @@ __global__ void __launch_bounds__(1024) k_scan_compact(const float* __restrict__
         int base = base_s;
         if (f) {
             int o = base + off + in_warp;
+            if (!MP_DCHECK(o < n, "compacted scan index", o)) o = 0;
             const float mx = raw[3 * i], my = raw[3 * i + 1], mz = raw[3 * i + 2];
             const float nx = normals[3 * i], ny = normals[3 * i + 1], nz = normals[3 * i + 2];
             pair[3 * o] = make_float4(mx, mx, my, my);

@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
         if (idx < n) {
             uint32_t dg = (key[it] >> shift) & (MP_RADIX - 1);
             int64_t pos = (int64_t)offs[(int64_t)dg * nblocks + blockIdx.x] + wcnt[w][dg] + loc[it];
+            if (!MP_DCHECK(pos >= 0 && pos < n, "radix scatter position", pos)) continue;
             kout[pos] = key[it];
             iout[pos] = id[it];
         }
@@ -272,11 +273,15 @@ __global__ void __launch_bounds__(256) k_merge(const float4* __restrict__ poses,
     int ja = -1, jb = -1;
     if (lane < K) {
         int j = old_ids[i * K + lane];
-        if (j >= 0 && j != i) ja = j;
+        if (j >= 0 && j != i && MP_DCHECK(j < n, "previous neighbour id", j)) ja = j;
     }
     {
         uint32_t b = buckets[i];
         int lo = blo[b], hi = bhi[b], r = rank[i];
+        if (!MP_DCHECK(lo >= 0 && lo <= r && r < hi && hi <= n, "bucket segment", (long long)lo * 1000003 + hi)) {
+            lo = 0;
+            hi = 0;
+        }
         int s0 = r - C / 2;
         int smax = max(lo, hi - C);
         s0 = min(s0, smax);
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(256) k_merge(const float4* __restrict__ poses,
         int e = min(s0 + C, hi);
         if (lane < e - s0) {
             int j = sorted_ids[s0 + lane];
-            if (j != i) jb = j;
+            if (j != i && MP_DCHECK(j >= 0 && j < n, "bucket member id", j)) jb = j;
         }
     }
     float da[6], db[6], sa = 0.f, sb = 0.f;

@@ -126,15 +126,15 @@ __global__ void __launch_bounds__(256) k_post_sweep(const double* __restrict__ p
         for (int q = 0; q < KT / 4; ++q) {
             const int4 j4 = __ldg(row + q);
             const double2 w0 = __ldg(wr + 2 * q), w1 = __ldg(wr + 2 * q + 1);
-            if (j4.x >= 0) num = fma(w0.x, __ldg(pin + j4.x), num);
-            if (j4.y >= 0) num = fma(w0.y, __ldg(pin + j4.y), num);
-            if (j4.z >= 0) num = fma(w1.x, __ldg(pin + j4.z), num);
-            if (j4.w >= 0) num = fma(w1.y, __ldg(pin + j4.w), num);
+            if (j4.x >= 0 && MP_DCHECK(j4.x < n, "neighbour id", j4.x)) num = fma(w0.x, __ldg(pin + j4.x), num);
+            if (j4.y >= 0 && MP_DCHECK(j4.y < n, "neighbour id", j4.y)) num = fma(w0.y, __ldg(pin + j4.y), num);
+            if (j4.z >= 0 && MP_DCHECK(j4.z < n, "neighbour id", j4.z)) num = fma(w1.x, __ldg(pin + j4.z), num);
+            if (j4.w >= 0 && MP_DCHECK(j4.w < n, "neighbour id", j4.w)) num = fma(w1.y, __ldg(pin + j4.w), num);
         }
     } else {
         for (int l = 0; l < K; ++l) {
             const int j = __ldg(ids + i * K + l);
-            if (j >= 0) num = fma(__ldg(w + i * K + l), __ldg(pin + j), num);
+            if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(__ldg(w + i * K + l), __ldg(pin + j), num);
         }
     }
     pout[i] = inv_den[i] > 0.0 ? num : pin[i];

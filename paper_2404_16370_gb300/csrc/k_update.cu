@@ -71,6 +71,7 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n) return;
     int64_t i = order[p];
+    if (!MP_DCHECK(i >= 0 && i < n, "particle order entry", i)) return;
     double A[6][6];
     int o = 0;
 #pragma unroll
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(256) k_svgd(float4* __restrict__ poses, int64_
     if (active && l < K) {
         int64_t o = i * K + l;
         int j = ids[o];
-        if (j >= 0) {
+        if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) {
             float k = kk[o];
             const float* dj = dd + o * 6;
             const float4 p0 = *reinterpret_cast<const float4*>(psi + (int64_t)j * 8);

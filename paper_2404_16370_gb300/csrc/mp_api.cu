@@ -27,6 +27,25 @@ int mp_cuda_check(mp_ctx* c, cudaError_t e, const char* what) {
     return mp_fail(c, code, "%s: %s", what, cudaGetErrorString(e));
 }
 
+#ifdef MP_CHECKED
+int mp_checked_sync(mp_ctx* c, const char* file, int line) {
+    // MP_CHECKED_SYNC=0 keeps the device checks but not the synchronisation
+    static const int sync = [] {
+        const char* v = getenv("MP_CHECKED_SYNC");
+        return v && v[0] == '0' ? 0 : 1;
+    }();
+    if (!sync) return MP_OK;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) return MP_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "MP_CHECKED: kernel launched at %s:%d: %s\n", file, line, cudaGetErrorString(e));
+        return mp_fail(c, MP_ECUDA, "kernel launched at %s:%d: %s", file, line, cudaGetErrorString(e));
+    }
+    return MP_OK;
+}
+#endif
+
 namespace {
 
 // ---- host Philox-4x32-10 (Salmon et al., SC 2011) for the per-step LSH draw

@@ -5,7 +5,8 @@
 // odometry, the LSH draw, the step counter) are copied by the graph from
 // pinned staging slots that the host fills before the launch; two slots (two
 // graphs) let the host prepare step s + 1 while step s runs. Before the
-// capture, the likelihood's scan split of each instance is picked by timing.
+// capture, the likelihood's scan split of each instance is picked by timing:
+// alone first, then as a policy across the instances running together.
 #include "mp_internal.cuh"
 
 #include <algorithm>
@@ -91,6 +92,33 @@ int autotune_split(mp_ctx* c) {
     return rc;
 }
 
+// All instances' likelihood stages launched together (each on its own stream,
+// forked from and joined into origin), timed on origin: the stage only writes
+// per-step outputs, so the instances' state is untouched.
+int time_concurrent_likelihood(mp_batch* b, float* ms_out) {
+    cudaEvent_t e0, e1;
+    B_CUDA(cudaEventCreate(&e0));
+    B_CUDA(cudaEventCreate(&e1));
+    int rc = MP_OK;
+    B_CUDA(cudaEventRecord(e0, b->origin));
+    for (int rep = 0; rep < 3 && rc == MP_OK; ++rep) {
+        B_CUDA(cudaEventRecord(b->fork, b->origin));
+        for (int i = 0; i < b->n && rc == MP_OK; ++i) {
+            mp_ctx* c = b->ctx[i];
+            B_CUDA(cudaStreamWaitEvent(c->stream, b->fork, 0));
+            rc = mp_run_stages(c, MP_STAGE_LIKELIHOOD);
+            B_CUDA(cudaEventRecord(b->join[i], c->stream));
+            B_CUDA(cudaStreamWaitEvent(b->origin, b->join[i], 0));
+        }
+    }
+    B_CUDA(cudaEventRecord(e1, b->origin));
+    B_CUDA(cudaEventSynchronize(e1));
+    B_CUDA(cudaEventElapsedTime(ms_out, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -141,15 +169,44 @@ int mp_batch_create(mp_batch** out, mp_ctx* const* ctxs, int n, const int32_t* n
     memset(b->stage, 0, 2 * sizeof(StepDev) * n);
     memset(b->scans, 0, 2 * sizeof(float) * b->scan_floats);
 
-    // tile choice per instance
+    // tile choice: each instance's split timed alone, then three policies
+    // timed with all instances running together (alone, a split helps a small
+    // instance fill the GPU; together, the others fill it and the split's
+    // atomics may not pay): the splits timed alone, none, and the timed splits
+    // only for instances with less than one wave of particle blocks
+    std::vector<int> alone(n, 1);
+    bool tuned = tune_scans != nullptr;
     for (int i = 0; i < n; ++i) {
         mp_ctx* c = b->ctx[i];
         c->lk_split = 1;
         if (tune_scans && tune_scans[i]) {
             if ((rc = mp_set_scan(c, tune_scans[i], n_scan[i]))) return fail(rc);
             if ((rc = autotune_split(c))) return fail(rc);
+            alone[i] = c->lk_split;
+        } else {
+            tuned = false;
         }
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(MP_ECUDA);
+    }
+    if (tuned && n > 1) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        float best_ms = 1e30f;
+        int best = 0;
+        for (int pol = 0; pol < 3; ++pol) {
+            for (int i = 0; i < n; ++i) {
+                const int64_t blocks = (b->ctx[i]->n + 255) / 256;
+                b->ctx[i]->lk_split = pol == 0 ? alone[i] : pol == 1 ? 1 : (blocks < 3 * (int64_t)sms ? alone[i] : 1);
+            }
+            float ms = 0.f;
+            if ((rc = time_concurrent_likelihood(b, &ms))) return fail(rc);
+            if (ms < best_ms) { best_ms = ms; best = pol; }
+        }
+        for (int i = 0; i < n; ++i) {
+            const int64_t blocks = (b->ctx[i]->n + 255) / 256;
+            b->ctx[i]->lk_split = best == 0 ? alone[i] : best == 1 ? 1 : (blocks < 3 * (int64_t)sms ? alone[i] : 1);
+        }
     }
 
     // one graph per staging slot: every instance's full step on its own branch.

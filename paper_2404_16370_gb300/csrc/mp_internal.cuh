@@ -396,11 +396,36 @@ int mp_cuda_check(mp_ctx* c, cudaError_t e, const char* what);
         cudaError_t _e = (call);                                        \
         if (_e != cudaSuccess) return mp_cuda_check((ctx), _e, #call);  \
     } while (0)
+// Checked builds (-DMP_CHECKED; a debugging aid, see build.py): kernels test
+// the indices they take from data (neighbour ids, map indices, sort positions,
+// the scan chunk bounds) before using them, print each violation and skip the
+// access; on the host every launch outside a stream capture is synchronised,
+// so that a fault is reported at the launch that caused it. In normal builds
+// both macros compile to nothing.
+#ifdef MP_CHECKED
+#define MP_DCHECK(cond, what, v)                                                                        \
+    ((cond) ? true                                                                                      \
+            : (printf("MP_CHECKED %s:%d: %s (%lld) block %d thread %d\n", __FILE__, __LINE__, what,      \
+                      (long long)(v), (int)blockIdx.x, (int)threadIdx.x),                               \
+               false))
+int mp_checked_sync(mp_ctx* c, const char* file, int line);
+#define MP_CHECKED_SYNC(ctx)                                          \
+    do {                                                              \
+        int _r = mp_checked_sync((ctx), __FILE__, __LINE__);          \
+        if (_r) return _r;                                            \
+    } while (0)
+#else
+#define MP_DCHECK(cond, what, v) true
+#define MP_CHECKED_SYNC(ctx) \
+    do {                     \
+    } while (0)
+#endif
 #define MP_LAUNCHED(ctx)                                                           \
     do {                                                                           \
         (ctx)->launches++;                                                         \
         cudaError_t _e = cudaGetLastError();                                       \
         if (_e != cudaSuccess) return mp_cuda_check((ctx), _e, "kernel launch");   \
+        MP_CHECKED_SYNC(ctx);                                                      \
     } while (0)
 
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }

@@ -63,3 +63,16 @@ def test_presets_match_oracle_readings(built, oracle, preset, n):
              ("n_buckets_log2", "nb_log2"), ("seed", "seed")]
     for gk, ok in pairs:
         assert abs(float(getattr(g, gk)) - float(getattr(o, ok))) <= 1e-7 * max(1.0, abs(float(getattr(o, ok)))), gk
+
+
+def test_checked_build_exports_the_same_symbols(built):
+    """The checked build (bounds-checked kernels, synchronised launches) is
+    the same boundary: every declared entry point, plus nothing missing."""
+    from paper_2404_16370_gb300 import build as B
+    lib = B.build(checked=True)
+    assert lib.endswith("libmp_checked.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(mp_[a-z_0-9]+)$", out, flags=re.M))
+    missing = [n for n in declared(HEADERS) if n not in exported]
+    assert not missing, missing
+    assert "mp_checked_sync" in out   # the host side of the checks is compiled in
