@@ -252,23 +252,29 @@ int mp_gicp(mp_ctx* ctx, const float* src, int32_t n_src, const float* tgt, int3
 int mp_step_gicp(mp_ctx* ctx, const float* scan, int32_t n_scan, double cov_scale);
 
 /* ---- Batched instances ------------------------------------------------
- * Many independent contexts (each with its own map, particles and CUDA
- * stream) stepped together: mp_batch_create captures one full step of every
- * instance into a CUDA graph (each instance on its own stream branch, forked
- * from and joined into cuda_stream), twice (two pinned staging slots), and
- * mp_batch_step replays it. Per instance the scan size is fixed (n_scan[i]
- * points every step) and every step runs all stages, the prediction included
- * (identity odometry without noise is applied, not skipped). tune_scans (may
- * be NULL; else one host scan per instance) is used to pick, by timing, each
- * instance's likelihood split (mp_set_likelihood_split); the pick runs the
- * scan, LSH and sort stages of each instance once. Contexts must not use
- * cuda_stream, must not share a stream, and must not have timing enabled.
- * The batch does not own the contexts; destroy it before them. A context in
- * a batch is stepped only through the batch (mp_batch_step returns
- * MP_EINVAL otherwise); reading it (mp_get_posterior, mp_get_buffer) is fine. */
+ * Many independent contexts (each with its own map, particles and
+ * parameters; presets may differ) stepped together. mp_batch_create plans
+ * one step of all instances as about forty grouped launches, each covering
+ * the blocks of every instance (one kernel per phase: prediction, scan
+ * Gaussians, LSH keys, each radix pass, merge, likelihood, solve, SVGD, each
+ * posterior sweep ...), and captures the plan on cuda_stream into a CUDA
+ * graph, twice (two pinned staging slots); mp_batch_step replays one. Per
+ * instance the scan size is fixed (n_scan[i] points every step) and every step
+ * runs all stages, the prediction included (identity odometry without noise
+ * is applied, not skipped). tune_scans (may be NULL; else one host scan per
+ * instance) is used to pick, by timing, each instance's likelihood split
+ * (mp_set_likelihood_split): alone first, then as a policy over the grouped
+ * launch; the pick runs the scan, LSH and sort stages of each instance once on
+ * its own stream. Contexts must use the FP32 likelihood and must not have
+ * timing enabled; their streams only order other calls on them before and
+ * after batch steps (they may be cuda_stream itself). The batch does not own
+ * the contexts; destroy it before them, and do not re-initialise their
+ * particles while it exists. A context in a batch is stepped only through
+ * the batch (mp_batch_step returns MP_EINVAL otherwise); reading it
+ * (mp_get_posterior, mp_get_buffer) is fine. */
 typedef struct mp_batch mp_batch;
-/* A new non-blocking CUDA stream (one per instance of a batch) and its
- * release; *stream receives the cudaStream_t. */
+/* A new non-blocking CUDA stream and its release; *stream receives the
+ * cudaStream_t. */
 int mp_stream_create(void** stream);
 int mp_stream_destroy(void* stream);
 int mp_batch_create(mp_batch** batch, mp_ctx* const* ctxs, int n, const int32_t* n_scan,

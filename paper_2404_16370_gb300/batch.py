@@ -8,11 +8,12 @@ a seeded pose) for every step, with small odometry and noise.
 
     python -m paper_2404_16370_gb300.batch --instances 64 --steps 10
 
-times the same steps taken (a) instance by instance with mp_step (each call
-launches the step's kernels on the instance's stream; instances overlap on
-the GPU) and (b) with mp_batch_step (one CUDA-graph launch per step for all
+times the same steps taken (a) instance by instance with mp_step, one
+instance after the other on one stream, and (b) with mp_batch_step (one
+CUDA-graph launch per step: every phase one grouped kernel over all
 instances, likelihood splits picked by timing), and prints one JSON line
-with instance-steps/s and particle-point pairs/s of both.
+with instance-steps/s and particle-point pairs/s of both. All contexts and
+the batch share one stream: no two instances' kernels run concurrently.
 """
 from __future__ import annotations
 
@@ -57,25 +58,20 @@ def build_instances(n_inst, seed=0, log2_particles=(12, 18), log2_points=(10, 14
     return inst
 
 
-def make_contexts(inst):
-    """One context per instance, each on a stream of its own (torch's stream
-    pool would hand out repeated streams beyond 32)."""
-    ctxs, streams = [], []
+def make_contexts(inst, stream):
+    """One context per instance, all on `stream`."""
+    ctxs = []
     for d in inst:
-        st = mp.mp_stream_create()
         p = mp.mp_default_params(d["preset"], d["n"])
-        ctx = mp.mp_init_map(d["pts"], p, cuda_stream=st)
+        ctx = mp.mp_init_map(d["pts"], p, cuda_stream=stream)
         mp.mp_init_particles(ctx, d["n"], poses=d["parts"])
         ctxs.append(ctx)
-        streams.append(st)
-    return ctxs, streams
+    return ctxs
 
 
-def release(ctxs, streams):
+def release(ctxs):
     for c in ctxs:
         mp.mp_destroy(c)
-    for s in streams:
-        mp.mp_stream_destroy(s)
 
 
 def odometry(n, step):
@@ -108,8 +104,9 @@ def main():
            "instances": n, "maps": 8, "particles_total": int(sum(d["n"] for d in inst)),
            "scan_points_total": int(sum(len(d["scan"]) for d in inst)), "steps": a.steps, "warmup": a.warmup,
            "inputs_s": round(gen_s, 1)}
+    stream = mp.mp_stream_create()
     # (a) instance by instance
-    ctxs, streams = make_contexts(inst)
+    ctxs = make_contexts(inst, stream)
     try:
         for s in range(a.warmup):
             T, cov = odometry(n, s)
@@ -124,13 +121,12 @@ def main():
         torch.cuda.synchronize()
         t_seq = time.perf_counter() - t0
     finally:
-        release(ctxs, streams)
+        release(ctxs)
     # (b) batched
-    ctxs, streams = make_contexts(inst)
-    origin = mp.mp_stream_create()
+    ctxs = make_contexts(inst, stream)
     try:
         t0 = time.perf_counter()
-        batch = mp.mp_batch_create(ctxs, [len(s) for s in scans], origin, tune_scans=scans)
+        batch = mp.mp_batch_create(ctxs, [len(s) for s in scans], stream, tune_scans=scans)
         create_s = time.perf_counter() - t0
         try:
             for s in range(a.warmup):
@@ -147,7 +143,8 @@ def main():
         finally:
             mp.mp_batch_destroy(batch)
     finally:
-        release(ctxs, streams + [origin])
+        release(ctxs)
+        mp.mp_stream_destroy(stream)
     res.update({
         "sequential": {"instance_steps_per_s": n * a.steps / t_seq, "pairs_per_s": pairs_step * a.steps / t_seq,
                        "ms_per_step": 1e3 * t_seq / a.steps},

@@ -25,6 +25,12 @@ LIB_CHECKED = os.path.join(HERE, "libmp_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", os.path.join(os.path.dirname(HERE), "include")]
+# The filter-step kernels are built without implicit multiply-add contraction:
+# each kernel body is instantiated twice (a context's own launch and the
+# batch's grouped launch), and only explicit fma / __f*_rn operations round the
+# same way in both whatever the surrounding code. The likelihood's arithmetic
+# is explicit (packed f32x2 intrinsics, fmaf) and keeps the default flags.
+NO_FMAD = {"k_update.cu", "k_neighbors.cu", "k_map.cu", "k_posterior.cu"}
 
 
 def nvcc() -> str:
@@ -55,7 +61,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
         src, obj = src_obj
         if not force and not ptxas_info and not _stale(obj, [src] + headers):
             return ""
-        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+        fmad = ["-fmad=false"] if os.path.basename(src) in NO_FMAD else []
+        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *fmad, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")

@@ -208,8 +208,10 @@ __device__ __forceinline__ void lk2_accumulate(const LkArgs& A, Lk2Acc& S, const
     const float2 ux = fma2(R[2], nz, fma2(R[1], ny, mul2(R[0], nx)));
     const float2 uy = fma2(R[5], nz, fma2(R[4], ny, mul2(R[3], nx)));
     const float2 uz = fma2(R[8], nz, fma2(R[7], ny, mul2(R[6], nx)));
-    const float sga = copysignf(1.f, ux.x * ra0.w + uy.x * ra1.x + uz.x * ra1.y);
-    const float sgb = copysignf(1.f, ux.y * rb0.w + uy.y * rb1.x + uz.y * rb1.y);
+    // sign of u.w as an explicit fma chain (the library is built without
+    // implicit contraction, so every instantiation rounds it the same way)
+    const float sga = copysignf(1.f, fmaf(uz.x, ra1.y, fmaf(uy.x, ra1.x, ux.x * ra0.w)));
+    const float sgb = copysignf(1.f, fmaf(uz.y, rb1.y, fmaf(uy.y, rb1.x, ux.y * rb0.w)));
     const float2 swx = make_float2(sga * ra0.w, sgb * rb0.w);
     const float2 swy = make_float2(sga * ra1.x, sgb * rb1.x);
     const float2 swz = make_float2(sga * ra1.y, sgb * rb1.y);
@@ -281,21 +283,29 @@ __device__ __forceinline__ LkAcc lk2_half(const LkArgs& A, const Lk2Acc& S, int 
     const float lc = h ? S.lc.y : S.lc.x;
     const float cnt = h ? S.cnt.y : S.cnt.x;
     // log p = -(sum of inlier costs) - c_max * (points that are not inliers)
-    o.ll = -lc - A.c_max * (float)(nv - (int)cnt);
+    o.ll = fmaf(-A.c_max, (float)(nv - (int)cnt), -lc);
     o.cnt = (int)cnt;
     return o;
 }
 
-// SPLIT: the scan is shared by gridDim.y CTAs per particle block (partial sums
-// added atomically); without it the loop is the plain one.
-template <int MINB, bool SPLIT>
-__global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A) {
+// SPLIT: the scan is shared by A.split CTAs per particle block (partial sums
+// added atomically; CTA (bx, by) takes chunks by, by + split, ...); without it
+// the loop is the plain one.
+template <bool SPLIT>
+struct LkOp {
+    using Args = LkArgs;
+    static constexpr int THREADS = LK_THREADS, MINB = LK_MINB;
+    static __device__ __forceinline__ void run(const LkArgs& A, unsigned bxi, unsigned byi);
+};
+
+template <bool SPLIT>
+__device__ __forceinline__ void LkOp<SPLIT>::run(const LkArgs& A, unsigned bxi, unsigned byi) {
     __shared__ __align__(128) float4 buf[2][3 * LK_CHUNK];
     __shared__ __align__(8) uint64_t bar[2];
 
     // particles a and b of this thread sit LK_THREADS apart in sorted order,
     // so each half of a warp covers 32 consecutive sorted particles
-    const int64_t pa = (int64_t)blockIdx.x * LK_PER_CTA + threadIdx.x;
+    const int64_t pa = (int64_t)bxi * LK_PER_CTA + threadIdx.x;
     const int64_t pb = pa + LK_THREADS;
     const bool acta = pa < A.n, actb = pb < A.n;
     int64_t ia = acta ? A.order[pa] : 0, ib = actb ? A.order[pb] : 0;
@@ -321,9 +331,9 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
     if (!MP_DCHECK(nv >= 0 && nv <= A.scan_cap, "valid scan points", nv)) nv = 0;
     const int nchunks = (nv + LK_CHUNK - 1) / LK_CHUNK;
     // scan split: this CTA takes chunks blockIdx.y, blockIdx.y + split, ...
-    const int split = SPLIT ? A.split : 1, by = SPLIT ? (int)blockIdx.y : 0;
+    const int split = SPLIT ? A.split : 1, by = SPLIT ? (int)byi : 0;
     const int nmine = SPLIT ? (by < nchunks ? (nchunks - by + split - 1) / split : 0) : nchunks;
-    if (blockIdx.x == 0 && by == 0 && threadIdx.x == 0)
+    if (bxi == 0 && by == 0 && threadIdx.x == 0)
         atomicAdd(A.pairs, (unsigned long long)A.n * (unsigned long long)nv);
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -413,6 +423,11 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood(const LkArgs A)
         for (int k = 0; k < 9; ++k) Rs[k] = R[k].y;
         lk_store(A, Rs, lk2_half(A, S, 1, SPLIT ? nv_mine : nv), pb, SPLIT);
     }
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(LK_THREADS, LK_MINB) k_likelihood(const LkArgs A) {
+    LkOp<SPLIT>::run(A, blockIdx.x, blockIdx.y);
 }
 
 
@@ -691,7 +706,9 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood_h(const LkArgs 
 
 }  // namespace
 
-int mp_launch_likelihood(mp_ctx* c) {
+namespace {
+
+LkArgs lk_args(mp_ctx* c) {
     LkArgs A;
     A.poses = c->poses[c->cur];
     A.order = c->sorted_ids;
@@ -721,9 +738,17 @@ int mp_launch_likelihood(mp_ctx* c) {
     A.two2 = pair(2.f);
     A.quarter_a2 = pair(0.25f * a);
     A.scan_h = c->scan_h2;
-    A.split = 1;
+    A.split = c->lk_split > 1 ? c->lk_split : 1;
     A.n_rec = c->n_map;
     A.scan_cap = c->p.max_scan;
+    return A;
+}
+
+}  // namespace
+
+int mp_launch_likelihood(mp_ctx* c) {
+    LkArgs A = lk_args(c);
+    A.split = 1;
     const unsigned grid = grid_for(c->n, LK_PER_CTA);
     if (c->precision == MP_PREC_BF16 || c->precision == MP_PREC_FP16) {
         if (c->n_scan > 0) {
@@ -745,11 +770,43 @@ int mp_launch_likelihood(mp_ctx* c) {
         A.split = c->lk_split > 1 ? c->lk_split : 1;
         if (A.split > 1) {
             MP_CUDA(c, cudaMemsetAsync(c->gn, 0, sizeof(float) * MP_GN * (size_t)c->cap, c->stream));
-            k_likelihood<LK_MINB, true><<<dim3(grid, A.split), LK_THREADS, 0, c->stream>>>(A);
+            k_likelihood<true><<<dim3(grid, A.split), LK_THREADS, 0, c->stream>>>(A);
         } else {
-            k_likelihood<LK_MINB, false><<<grid, LK_THREADS, 0, c->stream>>>(A);
+            k_likelihood<false><<<grid, LK_THREADS, 0, c->stream>>>(A);
         }
     }
     MP_LAUNCHED(c);
     return MP_OK;
+}
+
+// Grouped likelihood (FP32): one launch for the instances without a scan
+// split, one for those with one (their sums zeroed first, block (bx, by) of
+// the map = particle block bx, scan part by).
+int mp_plan_likelihood(mp_group* G, int, std::vector<GOp>& plan) {
+    std::vector<LkArgs> tab;
+    std::vector<int64_t> blocks;
+    std::vector<int> plain, split, ys;
+    for (int i = 0; i < G->size(); ++i) {
+        mp_ctx* c = G->ctx[i];
+        tab.push_back(lk_args(c));
+        blocks.push_back((c->n + LK_PER_CTA - 1) / LK_PER_CTA);
+        ys.push_back(tab.back().split);
+        if (tab.back().split > 1) {
+            split.push_back(i);
+            plan_memset(plan, c->gn, sizeof(float) * MP_GN * (size_t)c->cap);
+        } else {
+            plain.push_back(i);
+        }
+    }
+    const LkArgs* t = G->upload(tab);
+    unsigned nblk = 0;
+    if (!plain.empty()) {
+        const GBlk* m = G->block_map(blocks, &nblk, plain);
+        plan_kernel<LkOp<false>>(plan, t, m, nblk);
+    }
+    if (!split.empty()) {
+        const GBlk* m = G->block_map(blocks, &nblk, split, ys);
+        plan_kernel<LkOp<true>>(plan, t, m, nblk);
+    }
+    return G->err;
 }

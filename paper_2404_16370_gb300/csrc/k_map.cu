@@ -195,11 +195,45 @@ __global__ void k_map_normals(const float4* __restrict__ pts, int64_t n, CellGri
 // CTAs as the GPU has SMs.
 #define SCAN_TILE 1024
 #define SCAN_CTA 64
-__global__ void __launch_bounds__(SCAN_CTA) k_scan_normals(const float* __restrict__ raw, int n, float r2, int k, int kmin,
-                                                      float4* __restrict__ tmp_pts, float* __restrict__ normals,
-                                                      uint8_t* __restrict__ valid) {
+
+// Arguments of the per-step scan kernels (raw n x 3 points in, normals,
+// validity and the compacted broadcast pairs out).
+struct ScanArgs {
+    const float* raw;
+    int n;
+    float r2;
+    int k, kmin;
+    float4* tmp4;
+    float* normals;
+    uint8_t* valid;
+    float4* pair;
+    int32_t* nvalid;
+};
+
+struct ScanF4Op {
+    using Args = ScanArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const ScanArgs& A, unsigned bx, unsigned) {
+        int i = (int)bx * THREADS + threadIdx.x;
+        if (i < A.n) A.tmp4[i] = make_float4(A.raw[3 * i], A.raw[3 * i + 1], A.raw[3 * i + 2], 0.f);
+    }
+};
+
+struct ScanNormalsOp {
+    using Args = ScanArgs;
+    static constexpr int THREADS = SCAN_CTA, MINB = 1;
+    static __device__ __forceinline__ void run(const ScanArgs& A, unsigned bx, unsigned);
+};
+
+__device__ __forceinline__ void ScanNormalsOp::run(const ScanArgs& args, unsigned bx, unsigned) {
+    const float* __restrict__ raw = args.raw;
+    const int n = args.n, k = args.k, kmin = args.kmin;
+    const float r2 = args.r2;
+    const float4* __restrict__ tmp_pts = args.tmp4;
+    float* __restrict__ normals = args.normals;
+    uint8_t* __restrict__ valid = args.valid;
     __shared__ float sx[SCAN_TILE], sy[SCAN_TILE], sz[SCAN_TILE];
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = (int)bx * THREADS + threadIdx.x;
     float px = 0, py = 0, pz = 0;
     if (i < n) { px = raw[3 * i]; py = raw[3 * i + 1]; pz = raw[3 * i + 2]; }
     float D[MP_COVK];
@@ -245,16 +279,22 @@ __global__ void __launch_bounds__(SCAN_CTA) k_scan_normals(const float* __restri
     valid[i] = 1;
 }
 
-__global__ void k_scan_to_float4(const float* __restrict__ raw, int n, float4* __restrict__ out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = make_float4(raw[3 * i], raw[3 * i + 1], raw[3 * i + 2], 0.f);
-}
-
 // Order-preserving compaction of the valid scan points into 48-byte records of
-// broadcast pairs (every value twice, the operand layout of the packed pipe).
-__global__ void __launch_bounds__(1024) k_scan_compact(const float* __restrict__ raw, const float* __restrict__ normals,
-                                                       const uint8_t* __restrict__ valid, int n,
-                                                       float4* __restrict__ pair, int32_t* __restrict__ nvalid) {
+// broadcast pairs (every value twice, the operand layout of the packed pipe);
+// one CTA per scan.
+struct ScanCompactOp {
+    using Args = ScanArgs;
+    static constexpr int THREADS = 1024, MINB = 1;
+    static __device__ __forceinline__ void run(const ScanArgs& A, unsigned, unsigned);
+};
+
+__device__ __forceinline__ void ScanCompactOp::run(const ScanArgs& args, unsigned, unsigned) {
+    const float* __restrict__ raw = args.raw;
+    const float* __restrict__ normals = args.normals;
+    const uint8_t* __restrict__ valid = args.valid;
+    const int n = args.n;
+    float4* __restrict__ pair = args.pair;
+    int32_t* __restrict__ nvalid = args.nvalid;
     __shared__ int warp_tot[32];
     __shared__ int base_s;
     if (threadIdx.x == 0) base_s = 0;
@@ -288,6 +328,10 @@ __global__ void __launch_bounds__(1024) k_scan_compact(const float* __restrict__
     }
     if (threadIdx.x == 0) *nvalid = base_s;
 }
+
+__global__ void __launch_bounds__(256) k_scan_to_float4(const ScanArgs A) { ScanF4Op::run(A, blockIdx.x, 0); }
+__global__ void __launch_bounds__(SCAN_CTA) k_scan_normals(const ScanArgs A) { ScanNormalsOp::run(A, blockIdx.x, 0); }
+__global__ void __launch_bounds__(1024) k_scan_compact(const ScanArgs A) { ScanCompactOp::run(A, 0, 0); }
 
 // NNF: nearest valid map point to each voxel centre within r_max.
 __global__ void k_nnf_build(const float4* __restrict__ pts, CellGridDev g, int nx, int ny, int64_t nvox, float ox,
@@ -524,6 +568,25 @@ int mp_launch_map_prepare(mp_ctx* c, const float* xyz_dev) {
     return MP_OK;
 }
 
+namespace {
+
+ScanArgs scan_args(mp_ctx* c, const float* raw, int n) {
+    ScanArgs A;
+    A.raw = raw;
+    A.n = n;
+    A.r2 = c->p.r_cov * c->p.r_cov;
+    A.k = c->p.cov_k;
+    A.kmin = c->p.cov_min;
+    A.tmp4 = c->scan_tmp4;
+    A.normals = c->scan_normals;
+    A.valid = c->scan_valid;
+    A.pair = c->scan_pair;
+    A.nvalid = c->scan_nvalid;
+    return A;
+}
+
+}  // namespace
+
 // Per-step scan Gaussians (brute-force radius kNN in shared-memory tiles) and
 // compaction of the valid points.
 int mp_launch_scan_prepare(mp_ctx* c) {
@@ -532,15 +595,12 @@ int mp_launch_scan_prepare(mp_ctx* c) {
         MP_CUDA(c, cudaMemsetAsync(c->scan_nvalid, 0, sizeof(int32_t), c->stream));
         return MP_OK;
     }
-    float4* tmp = c->scan_tmp4;
-    k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(c->scan_raw, n, tmp);
+    const ScanArgs A = scan_args(c, c->scan_raw, n);
+    k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
-    float r2 = c->p.r_cov * c->p.r_cov;
-    k_scan_normals<<<grid_for(n, SCAN_CTA), SCAN_CTA, 0, c->stream>>>(c->scan_raw, n, r2, c->p.cov_k, c->p.cov_min, tmp,
-                                                             c->scan_normals, c->scan_valid);
+    k_scan_normals<<<grid_for(n, SCAN_CTA), SCAN_CTA, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
-    k_scan_compact<<<1, 1024, 0, c->stream>>>(c->scan_raw, c->scan_normals, c->scan_valid, n, c->scan_pair,
-                                              c->scan_nvalid);
+    k_scan_compact<<<1, 1024, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
     return MP_OK;
 }
@@ -549,13 +609,40 @@ int mp_launch_scan_prepare(mp_ctx* c) {
 // without the compaction): normals and validity of n points raw_dev (n x 3).
 int mp_launch_point_gaussians(mp_ctx* c, const float* raw_dev, int n, float4* tmp4, float* normals, uint8_t* valid) {
     if (n == 0) return MP_OK;
-    k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(raw_dev, n, tmp4);
+    ScanArgs A = scan_args(c, raw_dev, n);
+    A.tmp4 = tmp4;
+    A.normals = normals;
+    A.valid = valid;
+    A.pair = nullptr;
+    A.nvalid = nullptr;
+    k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
-    float r2 = c->p.r_cov * c->p.r_cov;
-    k_scan_normals<<<grid_for(n, SCAN_CTA), SCAN_CTA, 0, c->stream>>>(raw_dev, n, r2, c->p.cov_k, c->p.cov_min, tmp4,
-                                                                       normals, valid);
+    k_scan_normals<<<grid_for(n, SCAN_CTA), SCAN_CTA, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
     return MP_OK;
+}
+
+// Grouped scan stage: every instance's scan is read from the batch's device
+// scan buffer; the outputs go to each instance's own scan buffers.
+int mp_plan_scan(mp_group* G, int, std::vector<GOp>& plan) {
+    std::vector<ScanArgs> tab;
+    std::vector<int64_t> b256, b64, b1;
+    for (int i = 0; i < G->size(); ++i) {
+        const int n = G->n_scan[i];
+        tab.push_back(scan_args(G->ctx[i], G->scan_dev + G->scan_off[i], n));
+        b256.push_back((n + 255) / 256);
+        b64.push_back((n + SCAN_CTA - 1) / SCAN_CTA);
+        b1.push_back(1);
+    }
+    const ScanArgs* t = G->upload(tab);
+    unsigned nblk = 0;
+    const GBlk* m = G->block_map(b256, &nblk);
+    plan_kernel<ScanF4Op>(plan, t, m, nblk);
+    m = G->block_map(b64, &nblk);
+    plan_kernel<ScanNormalsOp>(plan, t, m, nblk);
+    m = G->block_map(b1, &nblk);
+    plan_kernel<ScanCompactOp>(plan, t, m, nblk);
+    return G->err;
 }
 
 int mp_launch_nnf_query(mp_ctx* c, const int32_t* vox_dev, int64_t m, int32_t* out_dev) {

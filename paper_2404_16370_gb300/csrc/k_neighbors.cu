@@ -85,11 +85,16 @@ size_t scan_tmp_need(int64_t n) {
 struct LshArgs {
     double scale[6];   // alpha * W^K diagonal
     uint32_t mask;
+    const float4* poses;
+    int64_t n;
+    const StepDev* sd;
+    uint32_t* keys;
+    uint32_t* buckets;
 };
 
 __device__ __forceinline__ void log_se3_d(double qx, double qy, double qz, double qw, const double t[3], double xi[6]) {
     if (qw < 0) { qx = -qx; qy = -qy; qz = -qz; qw = -qw; }
-    double s2 = qx * qx + qy * qy + qz * qz;
+    double s2 = fma(qz, qz, fma(qy, qy, qx * qx));
     double f;
     if (s2 < 1e-20) f = 2.0 / qw * (1.0 - s2 / (3.0 * qw * qw));
     else {
@@ -97,7 +102,7 @@ __device__ __forceinline__ void log_se3_d(double qx, double qy, double qz, doubl
         f = 2.0 * atan2(s, qw) / s;
     }
     xi[0] = f * qx; xi[1] = f * qy; xi[2] = f * qz;
-    double th2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    double th2 = fma(xi[2], xi[2], fma(xi[1], xi[1], xi[0] * xi[0]));
     double C;
     if (th2 < 1e-4) C = 1.0 / 12.0 + th2 * (1.0 / 720.0 + th2 * (1.0 / 30240.0));
     else {
@@ -105,75 +110,124 @@ __device__ __forceinline__ void log_se3_d(double qx, double qy, double qz, doubl
         sincos(0.5 * th, &sh, &ch);
         C = (1.0 - 0.5 * th * ch / sh) / th2;
     }
-    double wt[3] = {xi[1] * t[2] - xi[2] * t[1], xi[2] * t[0] - xi[0] * t[2], xi[0] * t[1] - xi[1] * t[0]};
-    double wwt[3] = {xi[1] * wt[2] - xi[2] * wt[1], xi[2] * wt[0] - xi[0] * wt[2], xi[0] * wt[1] - xi[1] * wt[0]};
-    for (int a = 0; a < 3; ++a) xi[3 + a] = t[a] - 0.5 * wt[a] + C * wwt[a];
+    double wt[3] = {fma(xi[1], t[2], -xi[2] * t[1]), fma(xi[2], t[0], -xi[0] * t[2]), fma(xi[0], t[1], -xi[1] * t[0])};
+    double wwt[3] = {fma(xi[1], wt[2], -xi[2] * wt[1]), fma(xi[2], wt[0], -xi[0] * wt[2]),
+                     fma(xi[0], wt[1], -xi[1] * wt[0])};
+    for (int a = 0; a < 3; ++a) xi[3 + a] = fma(C, wwt[a], fma(-0.5, wt[a], t[a]));
 }
 
 // T_LSH^-1 and delta come from the device-side step values (replayable)
-__global__ void k_lsh_keys(const float4* __restrict__ poses, int64_t n, LshArgs A, const StepDev* __restrict__ sd,
-                           uint32_t* __restrict__ keys, uint32_t* __restrict__ buckets) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+struct LshOp {
+    using Args = LshArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const LshArgs& A, unsigned bx, unsigned);
+};
+
+__device__ __forceinline__ void LshOp::run(const LshArgs& A, unsigned bx, unsigned) {
+    const float4* __restrict__ poses = A.poses;
+    const StepDev* __restrict__ sd = A.sd;
+    const int64_t n = A.n;
+    int64_t i = (int64_t)bx * THREADS + threadIdx.x;
     if (i >= n) return;
     float4 a = poses[2 * i], b = poses[2 * i + 1];
     double qx = a.x, qy = a.y, qz = a.z, qw = a.w;
-    double nrm = rsqrt(qx * qx + qy * qy + qz * qz + qw * qw);
+    double nrm = rsqrt(fma(qw, qw, fma(qz, qz, fma(qy, qy, qx * qx))));
     qx *= nrm; qy *= nrm; qz *= nrm; qw *= nrm;
     // relative pose T_LSH^-1 T_i = (Lq (x) q_i, R(Lq) t_i + Lt)
     const double lx = sd->lsh_qinv[0], ly = sd->lsh_qinv[1], lz = sd->lsh_qinv[2], lw = sd->lsh_qinv[3];
-    double rw = lw * qw - lx * qx - ly * qy - lz * qz;
-    double rx = lw * qx + lx * qw + ly * qz - lz * qy;
-    double ry = lw * qy - lx * qz + ly * qw + lz * qx;
-    double rz = lw * qz + lx * qy - ly * qx + lz * qw;
-    double ti[3] = {b.x, b.y, b.z};
-    double R[9];
-    R[0] = 1 - 2 * (ly * ly + lz * lz); R[1] = 2 * (lx * ly - lw * lz); R[2] = 2 * (lx * lz + lw * ly);
-    R[3] = 2 * (lx * ly + lw * lz); R[4] = 1 - 2 * (lx * lx + lz * lz); R[5] = 2 * (ly * lz - lw * lx);
-    R[6] = 2 * (lx * lz - lw * ly); R[7] = 2 * (ly * lz + lw * lx); R[8] = 1 - 2 * (lx * lx + ly * ly);
+    double rw = fma(lw, qw, -fma(lx, qx, fma(ly, qy, lz * qz)));
+    double rx = fma(lw, qx, fma(lx, qw, fma(ly, qz, -lz * qy)));
+    double ry = fma(lw, qy, fma(-lx, qz, fma(ly, qw, lz * qx)));
+    double rz = fma(lw, qz, fma(lx, qy, fma(-ly, qx, lz * qw)));
+    const double ti[3] = {b.x, b.y, b.z};
+    const double* R = sd->lsh_R;   // rotation of the step's inverse LSH quaternion
     double t[3];
-    for (int r = 0; r < 3; ++r) t[r] = R[3 * r] * ti[0] + R[3 * r + 1] * ti[1] + R[3 * r + 2] * ti[2] + sd->lsh_tinv[r];
+    for (int r = 0; r < 3; ++r)
+        t[r] = fma(R[3 * r], ti[0], fma(R[3 * r + 1], ti[1], fma(R[3 * r + 2], ti[2], sd->lsh_tinv[r])));
     double xi[6];
     log_se3_d(rx, ry, rz, rw, t, xi);
     const uint32_t P[6] = {73856093u, 19349663u, 83492791u, 2654435761u, 805459861u, 3674653429u};
     uint32_t key = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        double z = A.scale[k] * xi[k] + sd->lsh_delta[k];
+        double z = fma(A.scale[k], xi[k], sd->lsh_delta[k]);
         int cell = (int)floor(z);
         key ^= (uint32_t)cell * P[k];
     }
-    keys[i] = key;
-    buckets[i] = key & A.mask;
+    A.keys[i] = key;
+    A.buckets[i] = key & A.mask;
 }
+
+__global__ void __launch_bounds__(256) k_lsh_keys(const LshArgs A) { LshOp::run(A, blockIdx.x, 0); }
 
 // ---------------------------------------------------------------------------
 // stable LSD radix sort of (bucket, id), 8-bit digits, 2048 elements per block
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                                                    uint32_t* __restrict__ counts, int nblocks) {
+// One instance's sort: (key, id) pairs ping-pong between keys[0]/ids[0] and
+// keys[1]/ids[1] (pass pss reads pair pss & 1); counts are the digit counts of
+// every block, digit-major.
+struct SortArgs {
+    const uint32_t* buckets;
+    uint32_t* keys[2];
+    int32_t* ids[2];
+    int64_t n;
+    uint32_t* counts;
+    int nblocks;
+    int passes;
+    int32_t* sorted_ids;
+    int32_t* rank;
+    int32_t* blo;
+    int32_t* bhi;
+};
+
+// pass pss (the block map's y index): digit counts of block bx
+struct RadixHistOp {
+    using Args = SortArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned pss);
+};
+
+__device__ __forceinline__ void RadixHistOp::run(const SortArgs& A, unsigned bx, unsigned pss) {
+    const uint32_t* __restrict__ keys = A.keys[pss & 1];
+    const int64_t n = A.n;
+    const int shift = (int)pss * MP_RADIX_BITS;
+    uint32_t* __restrict__ counts = A.counts;
+    const int nblocks = A.nblocks;
     __shared__ uint32_t h[MP_RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * MP_SORT_TILE;
+    int64_t base = (int64_t)bx * MP_SORT_TILE;
 #pragma unroll
     for (int it = 0; it < MP_SORT_TILE / 256; ++it) {
         int64_t idx = base + it * 256 + threadIdx.x;
         if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (MP_RADIX - 1)], 1u);
     }
     __syncthreads();
-    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    counts[(int64_t)threadIdx.x * nblocks + bx] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ iin,
-                                                       int64_t n, int shift, const uint32_t* __restrict__ offs,
-                                                       int nblocks, uint32_t* __restrict__ kout,
-                                                       int32_t* __restrict__ iout) {
+// pass pss: stable scatter of block bx by its digit offsets
+struct RadixScatterOp {
+    using Args = SortArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned pss);
+};
+
+__device__ __forceinline__ void RadixScatterOp::run(const SortArgs& A, unsigned bx, unsigned pss) {
+    const uint32_t* __restrict__ kin = A.keys[pss & 1];
+    const int32_t* __restrict__ iin = A.ids[pss & 1];
+    uint32_t* __restrict__ kout = A.keys[(pss & 1) ^ 1];
+    int32_t* __restrict__ iout = A.ids[(pss & 1) ^ 1];
+    const int64_t n = A.n;
+    const int shift = (int)pss * MP_RADIX_BITS;
+    const uint32_t* __restrict__ offs = A.counts;
+    const int nblocks = A.nblocks;
     constexpr int ITEMS = MP_SORT_TILE / 256;   // per lane, consecutive 32-element rows
     __shared__ uint32_t wcnt[8][MP_RADIX];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < 8 * MP_RADIX; d += 256) (&wcnt[0][0])[d] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * MP_SORT_TILE + (int64_t)w * (32 * ITEMS);
+    int64_t base = (int64_t)bx * MP_SORT_TILE + (int64_t)w * (32 * ITEMS);
     uint32_t key[ITEMS];
     int32_t id[ITEMS];
     uint32_t loc[ITEMS];
@@ -208,7 +262,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
         int64_t idx = base + it * 32 + lane;
         if (idx < n) {
             uint32_t dg = (key[it] >> shift) & (MP_RADIX - 1);
-            int64_t pos = (int64_t)offs[(int64_t)dg * nblocks + blockIdx.x] + wcnt[w][dg] + loc[it];
+            int64_t pos = (int64_t)offs[(int64_t)dg * nblocks + bx] + wcnt[w][dg] + loc[it];
             if (!MP_DCHECK(pos >= 0 && pos < n, "radix scatter position", pos)) continue;
             kout[pos] = key[it];
             iout[pos] = id[it];
@@ -216,21 +270,107 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t* __restric
     }
 }
 
+__global__ void __launch_bounds__(256) k_radix_hist(const SortArgs A, int pss) { RadixHistOp::run(A, blockIdx.x, pss); }
+__global__ void __launch_bounds__(256) k_radix_scatter(const SortArgs A, int pss) {
+    RadixScatterOp::run(A, blockIdx.x, pss);
+}
+
 __global__ void k_iota(int32_t* __restrict__ a, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) a[i] = (int32_t)i;
 }
 
+// (key, id) pairs of the first pass: (bucket_i, i)
+struct SortInitOp {
+    using Args = SortArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned) {
+        int64_t i = (int64_t)bx * THREADS + threadIdx.x;
+        if (i >= A.n) return;
+        A.ids[0][i] = (int32_t)i;
+        A.keys[0][i] = A.buckets[i];
+    }
+};
+
+// sorted ids out of the last pass's pair, sorted buckets into keys[0]
+struct SortFinishOp {
+    using Args = SortArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned) {
+        int64_t i = (int64_t)bx * THREADS + threadIdx.x;
+        if (i >= A.n) return;
+        const int src = A.passes & 1;
+        A.sorted_ids[i] = A.ids[src][i];
+        if (src) A.keys[0][i] = A.keys[1][i];
+    }
+};
+
+// Exclusive scan of one instance's digit counts (256 x nblocks), in place, by
+// one CTA: 4096 counts per round with a running carry.
+struct CountScanOp {
+    using Args = SortArgs;
+    static constexpr int THREADS = 1024, MINB = 1;
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned, unsigned) {
+        __shared__ uint32_t warp_tot[32];
+        __shared__ uint32_t carry_s;
+        const int64_t m = (int64_t)MP_RADIX * A.nblocks;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (threadIdx.x == 0) carry_s = 0;
+        __syncthreads();
+        for (int64_t base0 = 0; base0 < m; base0 += 4096) {
+            const int64_t base = base0 + 4 * threadIdx.x;
+            uint32_t v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = (base + k < m) ? A.counts[base + k] : 0u;
+            const uint32_t s0 = v[0], s1 = s0 + v[1], s2 = s1 + v[2], tot = s2 + v[3];
+            uint32_t inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) warp_tot[w] = inc;
+            __syncthreads();
+            if (w == 0) {
+                uint32_t x = warp_tot[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                warp_tot[lane] = x;
+            }
+            __syncthreads();
+            const uint32_t carry = carry_s;
+            const uint32_t excl = carry + inc - tot + (w > 0 ? warp_tot[w - 1] : 0u);
+            const uint32_t r[4] = {excl, excl + s0, excl + s1, excl + s2};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (base + k < m) A.counts[base + k] = r[k];
+            __syncthreads();
+            if (threadIdx.x == 0) carry_s = carry + warp_tot[31];
+            __syncthreads();
+        }
+    }
+};
+
 // rank of every particle; [lo, hi) of every present bucket
-__global__ void k_segments(const uint32_t* __restrict__ sk, const int32_t* __restrict__ sid, int64_t n,
-                           int32_t* __restrict__ rank, int32_t* __restrict__ blo, int32_t* __restrict__ bhi) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    uint32_t b = sk[p];
-    rank[sid[p]] = (int32_t)p;
-    if (p == 0 || sk[p - 1] != b) blo[b] = (int32_t)p;
-    if (p == n - 1 || sk[p + 1] != b) bhi[b] = (int32_t)(p + 1);
-}
+struct SegmentsOp {
+    using Args = SortArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned) {
+        const uint32_t* __restrict__ sk = A.keys[0];
+        const int64_t n = A.n;
+        int64_t p = (int64_t)bx * THREADS + threadIdx.x;
+        if (p >= n) return;
+        uint32_t b = sk[p];
+        A.rank[A.sorted_ids[p]] = (int32_t)p;
+        if (p == 0 || sk[p - 1] != b) A.blo[b] = (int32_t)p;
+        if (p == n - 1 || sk[p + 1] != b) A.bhi[b] = (int32_t)(p + 1);
+    }
+};
+
+__global__ void __launch_bounds__(256) k_segments(const SortArgs A) { SegmentsOp::run(A, blockIdx.x, 0); }
 
 // ---------------------------------------------------------------------------
 // neighbour merge: one warp per particle, 64 candidate slots (2 per lane)
@@ -250,13 +390,43 @@ __device__ __forceinline__ void cswap(uint64_t& x, uint64_t y, bool keep_min) {
     x = keep_min ? (x < y ? x : y) : (x > y ? x : y);
 }
 
-__global__ void __launch_bounds__(256) k_merge(const float4* __restrict__ poses, int64_t n, int K, int C,
-                                               const int32_t* __restrict__ old_ids, const uint32_t* __restrict__ buckets,
-                                               const int32_t* __restrict__ sorted_ids, const int32_t* __restrict__ rank,
-                                               const int32_t* __restrict__ blo, const int32_t* __restrict__ bhi,
-                                               float wr, float wt, int32_t* __restrict__ ids, float* __restrict__ kk,
-                                               float* __restrict__ dd) {
-    int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+struct MergeArgs {
+    const float4* poses;
+    int64_t n;
+    int K, C;
+    const int32_t* old_ids;
+    const uint32_t* buckets;
+    const int32_t* sorted_ids;
+    const int32_t* rank;
+    const int32_t* blo;
+    const int32_t* bhi;
+    float wr, wt;
+    int32_t* ids;
+    float* kk;
+    float* dd;
+};
+
+struct MergeOp {
+    using Args = MergeArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const MergeArgs& A, unsigned bx, unsigned);
+};
+
+__device__ __forceinline__ void MergeOp::run(const MergeArgs& args, unsigned bx, unsigned) {
+    const float4* __restrict__ poses = args.poses;
+    const int64_t n = args.n;
+    const int K = args.K, C = args.C;
+    const int32_t* __restrict__ old_ids = args.old_ids;
+    const uint32_t* __restrict__ buckets = args.buckets;
+    const int32_t* __restrict__ sorted_ids = args.sorted_ids;
+    const int32_t* __restrict__ rank = args.rank;
+    const int32_t* __restrict__ blo = args.blo;
+    const int32_t* __restrict__ bhi = args.bhi;
+    const float wr = args.wr, wt = args.wt;
+    int32_t* __restrict__ ids = args.ids;
+    float* __restrict__ kk = args.kk;
+    float* __restrict__ dd = args.dd;
+    int64_t i = ((int64_t)bx * THREADS + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (i >= n) return;
     Quat qi;
@@ -375,6 +545,8 @@ __global__ void __launch_bounds__(256) k_merge(const float4* __restrict__ poses,
     }
 }
 
+__global__ void __launch_bounds__(256) k_merge(const MergeArgs A) { MergeOp::run(A, blockIdx.x, 0); }
+
 }  // namespace
 
 int mp_launch_exclusive_scan(mp_ctx* c, const uint32_t* in, uint32_t* out, int64_t n) {
@@ -395,36 +567,82 @@ int mp_launch_exclusive_scan(mp_ctx* c, const uint32_t* in, uint32_t* out, int64
     return rc;
 }
 
-int mp_launch_lsh_keys(mp_ctx* c) {
+namespace {
+
+LshArgs lsh_args(mp_ctx* c, const StepDev* sd) {
     LshArgs A;
     for (int k = 0; k < 6; ++k) A.scale[k] = (double)c->p.alpha * (double)(k < 3 ? c->p.sigma_r : c->p.sigma_t);
     A.mask = c->p.n_buckets_log2 >= 32 ? 0xffffffffu : ((1u << c->p.n_buckets_log2) - 1u);
-    k_lsh_keys<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->poses[c->cur], c->n, A, c->step_dev, c->keys,
-                                                          c->buckets);
+    A.poses = c->poses[c->cur];
+    A.n = c->n;
+    A.sd = sd;
+    A.keys = c->keys;
+    A.buckets = c->buckets;
+    return A;
+}
+
+SortArgs sort_args(mp_ctx* c) {
+    SortArgs A;
+    A.buckets = c->buckets;
+    A.keys[0] = c->sort_keys[0];
+    A.keys[1] = c->sort_keys[1];
+    A.ids[0] = c->sort_ids[0];
+    A.ids[1] = c->sort_ids[1];
+    A.n = c->n;
+    A.counts = c->radix_counts;
+    A.nblocks = (int)((c->n + MP_SORT_TILE - 1) / MP_SORT_TILE);
+    A.passes = (c->p.n_buckets_log2 + MP_RADIX_BITS - 1) / MP_RADIX_BITS;
+    A.sorted_ids = c->sorted_ids;
+    A.rank = c->rank;
+    A.blo = c->seg;
+    A.bhi = c->seg + ((int64_t)1 << c->p.n_buckets_log2);
+    return A;
+}
+
+MergeArgs merge_args(mp_ctx* c, int cur) {
+    MergeArgs A;
+    A.poses = c->poses[c->cur];
+    A.n = c->n;
+    A.K = c->p.K;
+    A.C = c->p.C;
+    A.old_ids = c->nbr_ids[cur];
+    A.buckets = c->buckets;
+    A.sorted_ids = c->sorted_ids;
+    A.rank = c->rank;
+    A.blo = c->seg;
+    A.bhi = c->seg + ((int64_t)1 << c->p.n_buckets_log2);
+    A.wr = c->p.sigma_r;
+    A.wt = c->p.sigma_t;
+    A.ids = c->nbr_ids[cur ^ 1];
+    A.kk = c->nbr_k;
+    A.dd = c->nbr_d;
+    return A;
+}
+
+}  // namespace
+
+int mp_launch_lsh_keys(mp_ctx* c) {
+    k_lsh_keys<<<grid_for(c->n, 256), 256, 0, c->stream>>>(lsh_args(c, c->step_dev));
     MP_LAUNCHED(c);
     return MP_OK;
 }
 
 int mp_launch_sort(mp_ctx* c) {
-    int64_t n = c->n;
-    int nblocks = (int)((n + MP_SORT_TILE - 1) / MP_SORT_TILE);
+    const SortArgs A = sort_args(c);
+    const int64_t n = c->n;
     k_iota<<<grid_for(n, 256), 256, 0, c->stream>>>(c->sort_ids[0], n);
     MP_LAUNCHED(c);
     MP_CUDA(c, cudaMemcpyAsync(c->sort_keys[0], c->buckets, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
                                c->stream));
-    int passes = (c->p.n_buckets_log2 + MP_RADIX_BITS - 1) / MP_RADIX_BITS;
-    int src = 0;
-    for (int pss = 0; pss < passes; ++pss) {
-        int shift = pss * MP_RADIX_BITS;
-        k_radix_hist<<<nblocks, 256, 0, c->stream>>>(c->sort_keys[src], n, shift, c->radix_counts, nblocks);
+    for (int pss = 0; pss < A.passes; ++pss) {
+        k_radix_hist<<<A.nblocks, 256, 0, c->stream>>>(A, pss);
         MP_LAUNCHED(c);
-        int rc = mp_launch_exclusive_scan(c, c->radix_counts, c->radix_counts, (int64_t)MP_RADIX * nblocks);
+        int rc = mp_launch_exclusive_scan(c, c->radix_counts, c->radix_counts, (int64_t)MP_RADIX * A.nblocks);
         if (rc) return rc;
-        k_radix_scatter<<<nblocks, 256, 0, c->stream>>>(c->sort_keys[src], c->sort_ids[src], n, shift, c->radix_counts,
-                                                        nblocks, c->sort_keys[1 - src], c->sort_ids[1 - src]);
+        k_radix_scatter<<<A.nblocks, 256, 0, c->stream>>>(A, pss);
         MP_LAUNCHED(c);
-        src = 1 - src;
     }
+    const int src = A.passes & 1;
     MP_CUDA(c, cudaMemcpyAsync(c->sorted_ids, c->sort_ids[src], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
                                c->stream));
     if (src != 0) {
@@ -432,23 +650,73 @@ int mp_launch_sort(mp_ctx* c) {
                                    cudaMemcpyDeviceToDevice, c->stream));
     }
     // sort_keys[0] now holds the sorted buckets; seg[0..2^nb) / seg[2^nb..) hold bucket lo / hi
-    int32_t* blo = c->seg;
-    int32_t* bhi = c->seg + ((int64_t)1 << c->p.n_buckets_log2);
-    k_segments<<<grid_for(n, 256), 256, 0, c->stream>>>(c->sort_keys[0], c->sorted_ids, n, c->rank, blo, bhi);
+    k_segments<<<grid_for(n, 256), 256, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
     return MP_OK;
 }
 
 int mp_launch_merge(mp_ctx* c) {
-    int64_t n = c->n;
-    int32_t* blo = c->seg;
-    int32_t* bhi = c->seg + ((int64_t)1 << c->p.n_buckets_log2);
-    int nxt = 1 - c->nbr_cur;
-    int64_t threads = n * 32;
-    k_merge<<<grid_for(threads, 256), 256, 0, c->stream>>>(c->poses[c->cur], n, c->p.K, c->p.C, c->nbr_ids[c->nbr_cur],
-                                                           c->buckets, c->sorted_ids, c->rank, blo, bhi, c->p.sigma_r,
-                                                           c->p.sigma_t, c->nbr_ids[nxt], c->nbr_k, c->nbr_d);
+    k_merge<<<grid_for(c->n * 32, 256), 256, 0, c->stream>>>(merge_args(c, c->nbr_cur));
     MP_LAUNCHED(c);
-    c->nbr_cur = nxt;
+    c->nbr_cur ^= 1;
     return MP_OK;
+}
+
+// Grouped LSH keys and sort: every instance's keys, then the radix passes
+// (pass pss covers the instances that need it), then segments.
+int mp_plan_lsh_sort(mp_group* G, int, std::vector<GOp>& plan) {
+    std::vector<LshArgs> lt;
+    std::vector<SortArgs> st;
+    std::vector<int64_t> b256, bsort;
+    int max_passes = 0;
+    for (int i = 0; i < G->size(); ++i) {
+        mp_ctx* c = G->ctx[i];
+        lt.push_back(lsh_args(c, G->sd_dev + i));
+        st.push_back(sort_args(c));
+        b256.push_back((c->n + 255) / 256);
+        bsort.push_back(st.back().nblocks);
+        max_passes = st.back().passes > max_passes ? st.back().passes : max_passes;
+    }
+    const LshArgs* ltab = G->upload(lt);
+    const SortArgs* stab = G->upload(st);
+    unsigned nblk = 0;
+    const GBlk* m256 = G->block_map(b256, &nblk);
+    const unsigned n256 = nblk;
+    plan_kernel<LshOp>(plan, ltab, m256, n256);
+    plan_kernel<SortInitOp>(plan, stab, m256, n256);
+    for (int pss = 0; pss < max_passes; ++pss) {
+        std::vector<int> which;
+        for (int i = 0; i < G->size(); ++i)
+            if (st[i].passes > pss) which.push_back(i);
+        // the pass index rides in the block map's y field
+        std::vector<GBlk> hm, cm;
+        for (int i : which) {
+            for (int64_t b = 0; b < bsort[i]; ++b) hm.push_back(GBlk{i, (int32_t)b, pss, 0});
+            cm.push_back(GBlk{i, 0, pss, 0});
+        }
+        const unsigned nh = (unsigned)hm.size(), nc = (unsigned)cm.size();
+        const GBlk* hmap = G->upload(hm);
+        const GBlk* cmap = G->upload(cm);
+        plan_kernel<RadixHistOp>(plan, stab, hmap, nh);
+        plan_kernel<CountScanOp>(plan, stab, cmap, nc);
+        plan_kernel<RadixScatterOp>(plan, stab, hmap, nh);
+    }
+    plan_kernel<SortFinishOp>(plan, stab, m256, n256);
+    plan_kernel<SegmentsOp>(plan, stab, m256, n256);
+    return G->err;
+}
+
+// Grouped merge: graph p reads list nbr_cur ^ p and writes the other.
+int mp_plan_merge(mp_group* G, int p, std::vector<GOp>& plan) {
+    std::vector<MergeArgs> tab;
+    std::vector<int64_t> blocks;
+    for (int i = 0; i < G->size(); ++i) {
+        mp_ctx* c = G->ctx[i];
+        tab.push_back(merge_args(c, c->nbr_cur ^ p));
+        blocks.push_back((c->n * 32 + 255) / 256);
+    }
+    unsigned nblk = 0;
+    const GBlk* map = G->block_map(blocks, &nblk);
+    plan_kernel<MergeOp>(plan, G->upload(tab), map, nblk);
+    return G->err;
 }

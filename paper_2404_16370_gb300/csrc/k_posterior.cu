@@ -23,265 +23,380 @@ __device__ __forceinline__ void argmax_merge(double& v, int64_t& i, double v2, i
     if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
 }
 
-__global__ void __launch_bounds__(PB) k_post_l(const double* __restrict__ logprior, const float* __restrict__ loglik,
-                                               int64_t n, double* __restrict__ lbuf, double* __restrict__ part) {
-    __shared__ double s[PB / 32];
-    int64_t i = blockIdx.x * (int64_t)PB + threadIdx.x;
-    double l = -INFINITY;
-    if (i < n) {
-        l = logprior[i] + (double)loglik[i];
-        lbuf[i] = l;
+// One instance's posterior stage. post doubles as the buffer of l until the
+// normalisation; the sweeps alternate post_tmp -> post -> post_tmp ...
+struct PostArgs {
+    const float* loglik;
+    double* logprior;
+    int64_t n;
+    int nb;               // blocks of PB particles
+    double* post;
+    double* post_tmp;
+    double* post_init;
+    double* part;         // nb block partials (max, then sums)
+    double* part2;        // nb block maxima of the final pass
+    int64_t* part_idx;    // nb block argmaxes
+    double* scalars;      // [0] max l, [1] sum exp, [2] sum post, [3] best prob
+    int64_t* best_idx;
+    const int32_t* ids;
+    int K;
+    const float* kk;
+    double* w;            // n x K normalised weights
+    double* invden;       // 1 / sum_j k_ij
+    int iters;
+    const float4* poses;
+    float4* best_pose;
+};
+
+struct PostLOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = PB, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
+        __shared__ double s[PB / 32];
+        int64_t i = (int64_t)bx * PB + threadIdx.x;
+        double l = -INFINITY;
+        if (i < A.n) {
+            l = A.logprior[i] + (double)A.loglik[i];
+            A.post[i] = l;
+        }
+        l = warp_max(l);
+        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = l;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < PB / 32 ? s[threadIdx.x] : -INFINITY;
+            v = warp_max(v);
+            if (threadIdx.x == 0) A.part[bx] = v;
+        }
     }
-    l = warp_max(l);
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = l;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < PB / 32 ? s[threadIdx.x] : -INFINITY;
+};
+
+struct ReduceMaxOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = 1024, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned, unsigned) {
+        __shared__ double s[32];
+        double v = -INFINITY;
+        for (int k = threadIdx.x; k < A.nb; k += 1024) v = fmax(v, A.part[k]);
         v = warp_max(v);
-        if (threadIdx.x == 0) part[blockIdx.x] = v;
+        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            v = s[threadIdx.x];
+            v = warp_max(v);
+            if (threadIdx.x == 0) A.scalars[0] = v;
+        }
     }
-}
+};
 
-__global__ void __launch_bounds__(1024) k_reduce_max(const double* __restrict__ part, int nb, double* __restrict__ out) {
-    __shared__ double s[32];
-    double v = -INFINITY;
-    for (int k = threadIdx.x; k < nb; k += 1024) v = fmax(v, part[k]);
-    v = warp_max(v);
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        v = s[threadIdx.x];
-        v = warp_max(v);
-        if (threadIdx.x == 0) *out = v;
-    }
-}
-
-__global__ void __launch_bounds__(PB) k_post_exp(const double* __restrict__ lbuf, int64_t n,
-                                                 const double* __restrict__ mx, double* __restrict__ p0,
-                                                 double* __restrict__ p, double* __restrict__ part) {
-    __shared__ double s[PB / 32];
-    int64_t i = blockIdx.x * (int64_t)PB + threadIdx.x;
-    double v = 0.0;
-    if (i < n) {
-        v = exp(lbuf[i] - *mx);
-        p0[i] = v;
-        p[i] = v;
-    }
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double w = threadIdx.x < PB / 32 ? s[threadIdx.x] : 0.0;
-        w = warp_sum(w);
-        if (threadIdx.x == 0) part[blockIdx.x] = w;
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_reduce_sum(const double* __restrict__ part, int nb, double* __restrict__ out) {
-    __shared__ double s[32];
-    double v = 0.0;
-    for (int k = threadIdx.x; k < nb; k += 1024) v += part[k];
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        v = s[threadIdx.x];
+struct PostExpOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = PB, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
+        __shared__ double s[PB / 32];
+        int64_t i = (int64_t)bx * PB + threadIdx.x;
+        double v = 0.0;
+        if (i < A.n) {
+            v = exp(A.post[i] - A.scalars[0]);
+            A.post_init[i] = v;
+            A.post_tmp[i] = v;
+        }
         v = warp_sum(v);
-        if (threadIdx.x == 0) *out = v;
+        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double w = threadIdx.x < PB / 32 ? s[threadIdx.x] : 0.0;
+            w = warp_sum(w);
+            if (threadIdx.x == 0) A.part[bx] = w;
+        }
     }
-}
+};
+
+struct ReduceSumOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = 1024, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned, unsigned) {
+        __shared__ double s[32];
+        double v = 0.0;
+        for (int k = threadIdx.x; k < A.nb; k += 1024) v += A.part[k];
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            v = s[threadIdx.x];
+            v = warp_sum(v);
+            if (threadIdx.x == 0) A.scalars[1] = v;
+        }
+    }
+};
 
 // Normalised weights w_ij = k_ij / sum_j k_ij (FP64) and 1 / sum_j k_ij,
 // fixed for the sweeps of a step: a sweep entry is then one FP64 fused
 // multiply-add (GB300's FP64 rate is low, so the division and the FP32 -> FP64
 // conversion are taken out of the ten sweeps).
-__global__ void k_post_weights(int64_t n, int K, const int32_t* __restrict__ ids, const float* __restrict__ kk,
-                               double* __restrict__ w, double* __restrict__ inv_den) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double den = 0.0;
-    for (int l = 0; l < K; ++l)
-        if (ids[i * K + l] >= 0) den += (double)kk[i * K + l];
-    const double inv = den > 0.0 ? 1.0 / den : 0.0;
-    for (int l = 0; l < K; ++l) w[i * K + l] = ids[i * K + l] >= 0 ? (double)kk[i * K + l] * inv : 0.0;
-    inv_den[i] = inv;
-}
+struct PostWeightsOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
+        const int64_t n = A.n;
+        const int K = A.K;
+        const int32_t* __restrict__ ids = A.ids;
+        const float* __restrict__ kk = A.kk;
+        double* __restrict__ w = A.w;
+        int64_t i = (int64_t)bx * THREADS + threadIdx.x;
+        if (i >= n) return;
+        double den = 0.0;
+        for (int l = 0; l < K; ++l)
+            if (ids[i * K + l] >= 0) den += (double)kk[i * K + l];
+        const double inv = den > 0.0 ? 1.0 / den : 0.0;
+        for (int l = 0; l < K; ++l) w[i * K + l] = ids[i * K + l] >= 0 ? (double)kk[i * K + l] * inv : 0.0;
+        A.invden[i] = inv;
+    }
+};
 
-// One Jacobi sweep of Eq. 11, one thread per particle: p'_i = sum_j w_ij p_j
-// with FP64 fused multiply-adds over the list (rows read with 16-byte loads
-// when the list length is a multiple of 4); a particle whose kernel weights
-// sum to zero keeps its value.
+// Jacobi sweep `it` (the block map's y index) of Eq. 11, one thread per
+// particle: p'_i = sum_j w_ij p_j with FP64 fused multiply-adds over the list
+// (rows read with 16-byte loads when the list length is a multiple of 4); a
+// particle whose kernel weights sum to zero keeps its value.
 template <int KT>
-__global__ void __launch_bounds__(256) k_post_sweep(const double* __restrict__ pin, double* __restrict__ pout, int64_t n,
-                                                    int Krt, const int32_t* __restrict__ ids,
-                                                    const double* __restrict__ w, const double* __restrict__ inv_den) {
-    const int K = KT > 0 ? KT : Krt;   // compile-time list length for the common sizes
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double num = 0.0;
-    if (KT > 0 && KT % 4 == 0) {
-        const int4* row = reinterpret_cast<const int4*>(ids + i * KT);
-        const double2* wr = reinterpret_cast<const double2*>(w + i * KT);
+struct PostSweepOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned it) {
+        const double* __restrict__ pin = (it & 1) ? A.post : A.post_tmp;
+        double* __restrict__ pout = (it & 1) ? A.post_tmp : A.post;
+        const int64_t n = A.n;
+        const int32_t* __restrict__ ids = A.ids;
+        const double* __restrict__ w = A.w;
+        const int K = KT > 0 ? KT : A.K;   // compile-time list length for the common sizes
+        int64_t i = (int64_t)bx * THREADS + threadIdx.x;
+        if (i >= n) return;
+        double num = 0.0;
+        if (KT > 0 && KT % 4 == 0) {
+            const int4* row = reinterpret_cast<const int4*>(ids + i * KT);
+            const double2* wr = reinterpret_cast<const double2*>(w + i * KT);
 #pragma unroll
-        for (int q = 0; q < KT / 4; ++q) {
-            const int4 j4 = __ldg(row + q);
-            const double2 w0 = __ldg(wr + 2 * q), w1 = __ldg(wr + 2 * q + 1);
-            if (j4.x >= 0 && MP_DCHECK(j4.x < n, "neighbour id", j4.x)) num = fma(w0.x, __ldg(pin + j4.x), num);
-            if (j4.y >= 0 && MP_DCHECK(j4.y < n, "neighbour id", j4.y)) num = fma(w0.y, __ldg(pin + j4.y), num);
-            if (j4.z >= 0 && MP_DCHECK(j4.z < n, "neighbour id", j4.z)) num = fma(w1.x, __ldg(pin + j4.z), num);
-            if (j4.w >= 0 && MP_DCHECK(j4.w < n, "neighbour id", j4.w)) num = fma(w1.y, __ldg(pin + j4.w), num);
+            for (int q = 0; q < KT / 4; ++q) {
+                const int4 j4 = __ldg(row + q);
+                const double2 w0 = __ldg(wr + 2 * q), w1 = __ldg(wr + 2 * q + 1);
+                if (j4.x >= 0 && MP_DCHECK(j4.x < n, "neighbour id", j4.x)) num = fma(w0.x, __ldg(pin + j4.x), num);
+                if (j4.y >= 0 && MP_DCHECK(j4.y < n, "neighbour id", j4.y)) num = fma(w0.y, __ldg(pin + j4.y), num);
+                if (j4.z >= 0 && MP_DCHECK(j4.z < n, "neighbour id", j4.z)) num = fma(w1.x, __ldg(pin + j4.z), num);
+                if (j4.w >= 0 && MP_DCHECK(j4.w < n, "neighbour id", j4.w)) num = fma(w1.y, __ldg(pin + j4.w), num);
+            }
+        } else {
+            for (int l = 0; l < K; ++l) {
+                const int j = __ldg(ids + i * K + l);
+                if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(__ldg(w + i * K + l), __ldg(pin + j), num);
+            }
         }
-    } else {
-        for (int l = 0; l < K; ++l) {
-            const int j = __ldg(ids + i * K + l);
-            if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(__ldg(w + i * K + l), __ldg(pin + j), num);
-        }
+        pout[i] = A.invden[i] > 0.0 ? num : pin[i];
     }
-    pout[i] = inv_den[i] > 0.0 ? num : pin[i];
-}
+};
 
-__global__ void __launch_bounds__(PB) k_post_final_part(const double* __restrict__ p, int64_t n,
-                                                        double* __restrict__ part_sum, double* __restrict__ part_max,
-                                                        int64_t* __restrict__ part_idx) {
-    __shared__ double ss[PB / 32], sm[PB / 32];
-    __shared__ int64_t si[PB / 32];
-    int64_t i = blockIdx.x * (int64_t)PB + threadIdx.x;
-    double v = i < n ? p[i] : 0.0;
-    double m = i < n ? v : -INFINITY;
-    int64_t mi = i < n ? i : INT64_MAX;
-    double s = warp_sum(v);
+// the smoothed posterior after the sweeps
+__device__ __forceinline__ const double* post_smoothed(const PostArgs& A) { return (A.iters & 1) ? A.post : A.post_tmp; }
+
+struct FinalPartOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = PB, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
+        __shared__ double ss[PB / 32], sm[PB / 32];
+        __shared__ int64_t si[PB / 32];
+        const double* __restrict__ p = post_smoothed(A);
+        int64_t i = (int64_t)bx * PB + threadIdx.x;
+        double v = i < A.n ? p[i] : 0.0;
+        double m = i < A.n ? v : -INFINITY;
+        int64_t mi = i < A.n ? i : INT64_MAX;
+        double s = warp_sum(v);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double m2 = __shfl_xor_sync(0xffffffffu, m, o);
-        int64_t i2 = __shfl_xor_sync(0xffffffffu, mi, o);
-        argmax_merge(m, mi, m2, i2);
+        for (int o = 16; o > 0; o >>= 1) {
+            double m2 = __shfl_xor_sync(0xffffffffu, m, o);
+            int64_t i2 = __shfl_xor_sync(0xffffffffu, mi, o);
+            argmax_merge(m, mi, m2, i2);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            ss[threadIdx.x >> 5] = s;
+            sm[threadIdx.x >> 5] = m;
+            si[threadIdx.x >> 5] = mi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double S = 0.0, M = -INFINITY;
+            int64_t I = INT64_MAX;
+            for (int k = 0; k < PB / 32; ++k) {
+                S += ss[k];
+                argmax_merge(M, I, sm[k], si[k]);
+            }
+            A.part[bx] = S;
+            A.part2[bx] = M;
+            A.part_idx[bx] = I;
+        }
     }
-    if ((threadIdx.x & 31) == 0) {
-        ss[threadIdx.x >> 5] = s;
-        sm[threadIdx.x >> 5] = m;
-        si[threadIdx.x >> 5] = mi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+};
+
+struct FinalReduceOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = 1024, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned, unsigned) {
+        __shared__ double ss[32], sm[32];
+        __shared__ int64_t si[32];
         double S = 0.0, M = -INFINITY;
         int64_t I = INT64_MAX;
-        for (int k = 0; k < PB / 32; ++k) {
-            S += ss[k];
-            argmax_merge(M, I, sm[k], si[k]);
+        for (int k = threadIdx.x; k < A.nb; k += 1024) {
+            S += A.part[k];
+            argmax_merge(M, I, A.part2[k], A.part_idx[k]);
         }
-        part_sum[blockIdx.x] = S;
-        part_max[blockIdx.x] = M;
-        part_idx[blockIdx.x] = I;
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_post_final_reduce(const double* __restrict__ part_sum,
-                                                            const double* __restrict__ part_max,
-                                                            const int64_t* __restrict__ part_idx, int nb,
-                                                            double* __restrict__ scalars, int64_t* __restrict__ best) {
-    __shared__ double ss[32], sm[32];
-    __shared__ int64_t si[32];
-    double S = 0.0, M = -INFINITY;
-    int64_t I = INT64_MAX;
-    for (int k = threadIdx.x; k < nb; k += 1024) {
-        S += part_sum[k];
-        argmax_merge(M, I, part_max[k], part_idx[k]);
-    }
-    S = warp_sum(S);
+        S = warp_sum(S);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double m2 = __shfl_xor_sync(0xffffffffu, M, o);
-        int64_t i2 = __shfl_xor_sync(0xffffffffu, I, o);
-        argmax_merge(M, I, m2, i2);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        ss[threadIdx.x >> 5] = S;
-        sm[threadIdx.x >> 5] = M;
-        si[threadIdx.x >> 5] = I;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double S2 = 0.0, M2 = -INFINITY;
-        int64_t I2 = INT64_MAX;
-        for (int k = 0; k < 32; ++k) {
-            S2 += ss[k];
-            argmax_merge(M2, I2, sm[k], si[k]);
+        for (int o = 16; o > 0; o >>= 1) {
+            double m2 = __shfl_xor_sync(0xffffffffu, M, o);
+            int64_t i2 = __shfl_xor_sync(0xffffffffu, I, o);
+            argmax_merge(M, I, m2, i2);
         }
-        scalars[2] = S2;
-        scalars[3] = M2 / S2;
-        *best = I2;
+        if ((threadIdx.x & 31) == 0) {
+            ss[threadIdx.x >> 5] = S;
+            sm[threadIdx.x >> 5] = M;
+            si[threadIdx.x >> 5] = I;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double S2 = 0.0, M2 = -INFINITY;
+            int64_t I2 = INT64_MAX;
+            for (int k = 0; k < 32; ++k) {
+                S2 += ss[k];
+                argmax_merge(M2, I2, sm[k], si[k]);
+            }
+            A.scalars[2] = S2;
+            A.scalars[3] = M2 / S2;
+            *A.best_idx = I2;
+        }
     }
+};
+
+// normalise out of post_tmp (after an odd number of sweeps the smoothed values
+// are copied there first), store the log prior, copy the best pose
+struct NormaliseOp {
+    using Args = PostArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
+        int64_t i = (int64_t)bx * THREADS + threadIdx.x;
+        if (i >= A.n) return;
+        double v = A.post_tmp[i] / A.scalars[2];
+        A.post[i] = v;
+        A.logprior[i] = log(v);
+        if (i == *A.best_idx) {
+            A.best_pose[0] = A.poses[2 * i];
+            A.best_pose[1] = A.poses[2 * i + 1];
+        }
+    }
+};
+
+template <typename Op>
+__global__ void __launch_bounds__(Op::THREADS) k_post(const PostArgs A, int y) {
+    Op::run(A, blockIdx.x, y);
 }
 
-__global__ void k_post_normalise(const double* __restrict__ p, int64_t n, const double* __restrict__ scalars,
-                                 const int64_t* __restrict__ best, const float4* __restrict__ poses,
-                                 double* __restrict__ post, double* __restrict__ logprior, float4* __restrict__ best_pose) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double v = p[i] / scalars[2];
-    post[i] = v;
-    logprior[i] = log(v);
-    if (i == *best) {
-        best_pose[0] = poses[2 * i];
-        best_pose[1] = poses[2 * i + 1];
-    }
+PostArgs post_args(mp_ctx* c, int cur) {
+    PostArgs A;
+    A.loglik = c->loglik;
+    A.logprior = c->logprior;
+    A.n = c->n;
+    A.nb = (int)((c->n + PB - 1) / PB);
+    A.post = c->post;
+    A.post_tmp = c->post_tmp;
+    A.post_init = c->post_init;
+    A.part = c->red;
+    A.part2 = c->red + A.nb;
+    A.part_idx = (int64_t*)(c->red + 2 * (int64_t)A.nb);
+    A.scalars = c->scalars;
+    A.best_idx = c->best_idx;
+    A.ids = c->nbr_ids[cur];
+    A.K = c->p.K;
+    A.kk = c->nbr_k;
+    A.w = c->post_w;
+    A.invden = c->post_invden;
+    A.iters = c->p.post_iters;
+    A.poses = c->poses[c->cur];
+    A.best_pose = c->best_pose;
+    return A;
 }
 
 template <int KT>
-int sweeps(mp_ctx* c, double*& a, double*& b, const double* inv_den) {
-    for (int it = 0; it < c->p.post_iters; ++it) {
-        k_post_sweep<KT><<<grid_for(c->n, 256), 256, 0, c->stream>>>(a, b, c->n, c->p.K, c->nbr_ids[c->nbr_cur],
-                                                                    c->post_w, inv_den);
-        MP_LAUNCHED(c);
-        double* t = a;
-        a = b;
-        b = t;
-    }
-    return MP_OK;
+void sweeps(mp_ctx* c, const PostArgs& A) {
+    for (int it = 0; it < A.iters; ++it) k_post<PostSweepOp<KT>><<<grid_for(A.n, 256), 256, 0, c->stream>>>(A, it);
 }
-
-
 
 }  // namespace
 
 int mp_launch_posterior(mp_ctx* c) {
-    int64_t n = c->n;
-    int nb = (int)((n + PB - 1) / PB);
-    double* part = c->red;
-    double* part2 = c->red + nb;
-    int64_t* part_idx = (int64_t*)(c->red + 2 * (int64_t)nb);
-    double* lbuf = c->post;   // scratch until the final normalisation
-    k_post_l<<<nb, PB, 0, c->stream>>>(c->logprior, c->loglik, n, lbuf, part);
+    const PostArgs A = post_args(c, c->nbr_cur);
+    const unsigned nb = (unsigned)A.nb;
+    k_post<PostLOp><<<nb, PB, 0, c->stream>>>(A, 0);
     MP_LAUNCHED(c);
-    k_reduce_max<<<1, 1024, 0, c->stream>>>(part, nb, &c->scalars[0]);
+    k_post<ReduceMaxOp><<<1, 1024, 0, c->stream>>>(A, 0);
     MP_LAUNCHED(c);
-    k_post_exp<<<nb, PB, 0, c->stream>>>(lbuf, n, &c->scalars[0], c->post_init, c->post_tmp, part);
+    k_post<PostExpOp><<<nb, PB, 0, c->stream>>>(A, 0);
     MP_LAUNCHED(c);
-    k_reduce_sum<<<1, 1024, 0, c->stream>>>(part, nb, &c->scalars[1]);
+    k_post<ReduceSumOp><<<1, 1024, 0, c->stream>>>(A, 0);
     MP_LAUNCHED(c);
-    k_post_weights<<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->p.K, c->nbr_ids[c->nbr_cur], c->nbr_k, c->post_w,
-                                                            c->post_invden);
+    k_post<PostWeightsOp><<<grid_for(A.n, 256), 256, 0, c->stream>>>(A, 0);
     MP_LAUNCHED(c);
-    double* a = c->post_tmp;
-    double* b = c->post;
-    int rc;
-    if (c->p.K == 32) rc = sweeps<32>(c, a, b, c->post_invden);
-    else if (c->p.K == 16) rc = sweeps<16>(c, a, b, c->post_invden);
-    else rc = sweeps<0>(c, a, b, c->post_invden);
-    if (rc) return rc;
-    // a holds the smoothed (unnormalised) posterior
-    k_post_final_part<<<nb, PB, 0, c->stream>>>(a, n, part, part2, part_idx);
+    if (A.K == 32) sweeps<32>(c, A);
+    else if (A.K == 16) sweeps<16>(c, A);
+    else sweeps<0>(c, A);
+    c->launches += A.iters - 1;
     MP_LAUNCHED(c);
-    k_post_final_reduce<<<1, 1024, 0, c->stream>>>(part, part2, part_idx, nb, c->scalars, c->best_idx);
+    k_post<FinalPartOp><<<nb, PB, 0, c->stream>>>(A, 0);
     MP_LAUNCHED(c);
-    double* dst = c->post;
-    if (a == c->post) {
-        // normalise out of post_tmp's twin: copy a first so that post can be written
-        MP_CUDA(c, cudaMemcpyAsync(c->post_tmp, a, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
-        a = c->post_tmp;
-    }
-    k_post_normalise<<<grid_for(n, 256), 256, 0, c->stream>>>(a, n, c->scalars, c->best_idx, c->poses[c->cur], dst,
-                                                              c->logprior, c->best_pose);
+    k_post<FinalReduceOp><<<1, 1024, 0, c->stream>>>(A, 0);
+    MP_LAUNCHED(c);
+    if (A.iters & 1)
+        MP_CUDA(c, cudaMemcpyAsync(c->post_tmp, c->post, sizeof(double) * (size_t)A.n, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+    k_post<NormaliseOp><<<grid_for(A.n, 256), 256, 0, c->stream>>>(A, 0);
     MP_LAUNCHED(c);
     return MP_OK;
+}
+
+// Grouped posterior: the same launches over all instances; the sweeps of
+// instances with K = 32, 16 and other list lengths go in separate launches.
+int mp_plan_posterior(mp_group* G, int p, std::vector<GOp>& plan) {
+    std::vector<PostArgs> tab;
+    std::vector<int64_t> bpb, b1;
+    std::vector<int> odd;
+    int max_iters = 0;
+    for (int i = 0; i < G->size(); ++i) {
+        mp_ctx* c = G->ctx[i];
+        tab.push_back(post_args(c, c->nbr_cur ^ p ^ 1));   // the list the merge of this step wrote
+        bpb.push_back(tab.back().nb);
+        b1.push_back(1);
+        max_iters = tab.back().iters > max_iters ? tab.back().iters : max_iters;
+        if (tab.back().iters & 1) odd.push_back(i);
+    }
+    const PostArgs* t = G->upload(tab);
+    unsigned npb = 0, n1 = 0;
+    const GBlk* mpb = G->block_map(bpb, &npb);
+    const GBlk* m1 = G->block_map(b1, &n1);
+    plan_kernel<PostLOp>(plan, t, mpb, npb);
+    plan_kernel<ReduceMaxOp>(plan, t, m1, n1);
+    plan_kernel<PostExpOp>(plan, t, mpb, npb);
+    plan_kernel<ReduceSumOp>(plan, t, m1, n1);
+    plan_kernel<PostWeightsOp>(plan, t, mpb, npb);   // PB = 256 threads: the same blocks
+    for (int it = 0; it < max_iters; ++it) {
+        std::vector<GBlk> m32, m16, m0;
+        for (int i = 0; i < G->size(); ++i) {
+            if (tab[i].iters <= it) continue;
+            std::vector<GBlk>& m = tab[i].K == 32 ? m32 : tab[i].K == 16 ? m16 : m0;
+            for (int64_t b = 0; b < bpb[i]; ++b) m.push_back(GBlk{i, (int32_t)b, it, 0});
+        }
+        if (!m32.empty()) plan_kernel<PostSweepOp<32>>(plan, t, G->upload(m32), (unsigned)m32.size());
+        if (!m16.empty()) plan_kernel<PostSweepOp<16>>(plan, t, G->upload(m16), (unsigned)m16.size());
+        if (!m0.empty()) plan_kernel<PostSweepOp<0>>(plan, t, G->upload(m0), (unsigned)m0.size());
+    }
+    plan_kernel<FinalPartOp>(plan, t, mpb, npb);
+    plan_kernel<FinalReduceOp>(plan, t, m1, n1);
+    for (int i : odd)
+        plan_copy(plan, G->ctx[i]->post_tmp, G->ctx[i]->post, sizeof(double) * (size_t)G->ctx[i]->n);
+    plan_kernel<NormaliseOp>(plan, t, mpb, npb);
+    return G->err;
 }

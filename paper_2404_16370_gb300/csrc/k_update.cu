@@ -18,12 +18,18 @@ struct PredArgs {
     float4* poses;
     int64_t n;
     uint2 key;
+    const StepDev* sd;   // the motion dT, the noise factor and the step counter (replayable)
 };
 
-// the motion dT, the noise factor and the step counter come from the
-// device-side step values (replayable)
-__global__ void k_predict(const PredArgs A, const StepDev* __restrict__ sd) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+struct PredOp {
+    using Args = PredArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const PredArgs& A, unsigned bx, unsigned);
+};
+
+__device__ __forceinline__ void PredOp::run(const PredArgs& A, unsigned bx, unsigned) {
+    const StepDev* __restrict__ sd = A.sd;
+    int64_t i = (int64_t)bx * THREADS + threadIdx.x;
     if (i >= A.n) return;
     Quat q;
     float t[3];
@@ -65,10 +71,36 @@ __global__ void k_predict(const PredArgs A, const StepDev* __restrict__ sd) {
     store_pose(A.poses, i, q, t);
 }
 
-__global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int32_t* __restrict__ order, int64_t n,
-                        double lambda, double eps, float* __restrict__ psi, float* __restrict__ loglik,
-                        int32_t* __restrict__ n_in, float* __restrict__ pinv) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_predict(const PredArgs A) { PredOp::run(A, blockIdx.x, 0); }
+
+struct SolveArgs {
+    const float* gn;
+    int64_t stride;
+    const int32_t* order;
+    int64_t n;
+    double lambda, eps;
+    float* psi;
+    float* loglik;
+    int32_t* n_in;
+    float* pinv;   // nullptr: no inverse stored
+};
+
+struct SolveOp {
+    using Args = SolveArgs;
+    static constexpr int THREADS = 128, MINB = 1;
+    static __device__ __forceinline__ void run(const SolveArgs& A, unsigned bx, unsigned);
+};
+
+__device__ __forceinline__ void SolveOp::run(const SolveArgs& args, unsigned bx, unsigned) {
+    const float* __restrict__ gn = args.gn;
+    const int64_t stride = args.stride, n = args.n;
+    const int32_t* __restrict__ order = args.order;
+    const double lambda = args.lambda, eps = args.eps;
+    float* __restrict__ psi = args.psi;
+    float* __restrict__ loglik = args.loglik;
+    int32_t* __restrict__ n_in = args.n_in;
+    float* __restrict__ pinv = args.pinv;
+    int64_t p = (int64_t)bx * THREADS + threadIdx.x;
     if (p >= n) return;
     int64_t i = order[p];
     if (!MP_DCHECK(i >= 0 && i < n, "particle order entry", i)) return;
@@ -88,14 +120,14 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
     float ll = gn[27 * stride + p];
     int cnt = (int)gn[28 * stride + p];
 #pragma unroll
-    for (int r = 0; r < 6; ++r) A[r][r] += lambda * A[r][r] + eps;
+    for (int r = 0; r < 6; ++r) A[r][r] = A[r][r] + fma(lambda, A[r][r], eps);
     // LDL^T in place: strictly lower part holds L, diagonal holds D
     bool good = cnt >= 6;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         double d = A[j][j];
 #pragma unroll
-        for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k] * A[k][k];
+        for (int k = 0; k < j; ++k) d = fma(-A[j][k] * A[j][k], A[k][k], d);
         good = good && (d > 0.0);
         A[j][j] = d;
         double inv = good ? 1.0 / d : 0.0;
@@ -103,7 +135,7 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
         for (int r = j + 1; r < 6; ++r) {
             double s = A[r][j];
 #pragma unroll
-            for (int k = 0; k < j; ++k) s -= A[r][k] * A[j][k] * A[k][k];
+            for (int k = 0; k < j; ++k) s = fma(-A[r][k] * A[j][k], A[k][k], s);
             A[r][j] = s * inv;
         }
     }
@@ -112,7 +144,7 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
     for (int r = 0; r < 6; ++r) {
         double s = -b[r];
 #pragma unroll
-        for (int k = 0; k < r; ++k) s -= A[r][k] * x[k];
+        for (int k = 0; k < r; ++k) s = fma(-A[r][k], x[k], s);
         x[r] = s;
     }
 #pragma unroll
@@ -121,7 +153,7 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
     for (int r = 5; r >= 0; --r) {
         double s = x[r];
 #pragma unroll
-        for (int k = r + 1; k < 6; ++k) s -= A[k][r] * x[k];
+        for (int k = r + 1; k < 6; ++k) s = fma(-A[k][r], x[k], s);
         x[r] = s;
     }
 #pragma unroll
@@ -137,7 +169,7 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
             for (int r = 0; r < 6; ++r) {
                 double v = r == cc ? 1.0 : 0.0;
 #pragma unroll
-                for (int k = 0; k < r; ++k) v -= A[r][k] * z[k];
+                for (int k = 0; k < r; ++k) v = fma(-A[r][k], z[k], v);
                 z[r] = v;
             }
 #pragma unroll
@@ -146,7 +178,7 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
             for (int r = 5; r >= 0; --r) {
                 double v = z[r];
 #pragma unroll
-                for (int k = r + 1; k < 6; ++k) v -= A[k][r] * z[k];
+                for (int k = r + 1; k < 6; ++k) v = fma(-A[k][r], z[k], v);
                 z[r] = v;
             }
 #pragma unroll
@@ -157,16 +189,45 @@ __global__ void k_solve(const float* __restrict__ gn, int64_t stride, const int3
     n_in[i] = cnt;
 }
 
+__global__ void __launch_bounds__(128) k_solve(const SolveArgs A) { SolveOp::run(A, blockIdx.x, 0); }
+
+struct SvgdArgs {
+    float4* poses;
+    int64_t n;
+    int K;
+    const int32_t* ids;
+    const float* kk;
+    const float* dd;
+    const float* psi;
+    float wr, wt;
+    const float* pinv;
+    float* phi;
+};
+
 // G lanes per particle (G = power of two >= K, <= 32)
 template <int G, bool PRE>
-__global__ void __launch_bounds__(256) k_svgd(float4* __restrict__ poses, int64_t n, int K,
-                                              const int32_t* __restrict__ ids, const float* __restrict__ kk,
-                                              const float* __restrict__ dd, const float* __restrict__ psi, float wr,
-                                              float wt, const float* __restrict__ pinv, float* __restrict__ phi_out) {
+struct SvgdOp {
+    using Args = SvgdArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const SvgdArgs& A, unsigned bx, unsigned);
+};
+
+template <int G, bool PRE>
+__device__ __forceinline__ void SvgdOp<G, PRE>::run(const SvgdArgs& A, unsigned bx, unsigned) {
+    float4* __restrict__ poses = A.poses;
+    const int64_t n = A.n;
+    const int K = A.K;
+    const int32_t* __restrict__ ids = A.ids;
+    const float* __restrict__ kk = A.kk;
+    const float* __restrict__ dd = A.dd;
+    const float* __restrict__ psi = A.psi;
+    const float wr = A.wr, wt = A.wt;
+    const float* __restrict__ pinv = A.pinv;
+    float* __restrict__ phi_out = A.phi;
     // PRE: the attraction (6), the repulsion (6) and the kernel sum are
     // reduced apart, and the repulsion is multiplied by pinv_i
     constexpr int NA = PRE ? 13 : 7;
-    int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t gt = (int64_t)bx * THREADS + threadIdx.x;
     int64_t i = gt / G;
     int l = (int)(gt % G);
     bool active = i < n;
@@ -229,6 +290,9 @@ __global__ void __launch_bounds__(256) k_svgd(float4* __restrict__ poses, int64_
 #pragma unroll
     for (int a = 0; a < 6; ++a) phi_out[i * 8 + a] = xi[a];
 }
+
+template <int G, bool PRE>
+__global__ void __launch_bounds__(256) k_svgd(const SvgdArgs A) { SvgdOp<G, PRE>::run(A, blockIdx.x, 0); }
 
 struct InitArgs {
     float4* poses;
@@ -294,47 +358,140 @@ __global__ void k_gather_gn(const float* __restrict__ gn, int64_t stride, const 
 
 }  // namespace
 
-int mp_launch_predict(mp_ctx* c) {
+namespace {
+
+PredArgs pred_args(mp_ctx* c, const StepDev* sd) {
     PredArgs A;
     A.poses = c->poses[c->cur];
     A.n = c->n;
     A.key = make_uint2((uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32));
-    k_predict<<<grid_for(c->n, 256), 256, 0, c->stream>>>(A, c->step_dev);
-    MP_LAUNCHED(c);
-    return MP_OK;
+    A.sd = sd;
+    return A;
 }
 
-int mp_launch_solve(mp_ctx* c) {
-    k_solve<<<grid_for(c->n, 128), 128, 0, c->stream>>>(c->gn, c->cap, c->sorted_ids, c->n, (double)c->p.lambda,
-                                                        (double)c->p.eps, c->psi, c->loglik, c->n_in,
-                                                        c->p.svgd_precond ? c->pinv : nullptr);
+SolveArgs solve_args(mp_ctx* c) {
+    SolveArgs A;
+    A.gn = c->gn;
+    A.stride = c->cap;
+    A.order = c->sorted_ids;
+    A.n = c->n;
+    A.lambda = (double)c->p.lambda;
+    A.eps = (double)c->p.eps;
+    A.psi = c->psi;
+    A.loglik = c->loglik;
+    A.n_in = c->n_in;
+    A.pinv = c->p.svgd_precond ? c->pinv : nullptr;
+    return A;
+}
+
+SvgdArgs svgd_args(mp_ctx* c, int nbr_cur) {
+    SvgdArgs A;
+    A.poses = c->poses[c->cur];
+    A.n = c->n;
+    A.K = c->p.K;
+    A.ids = c->nbr_ids[nbr_cur];
+    A.kk = c->nbr_k;
+    A.dd = c->nbr_d;
+    A.psi = c->psi;
+    A.wr = c->p.sigma_r;
+    A.wt = c->p.sigma_t;
+    A.pinv = c->p.svgd_precond ? c->pinv : nullptr;
+    A.phi = c->phi;
+    return A;
+}
+
+// lanes per particle: the power of two >= K
+int svgd_lanes(int K) {
+    int g = 1;
+    while (g < K && g < 32) g *= 2;
+    return g;
+}
+
+template <int G>
+int launch_svgd_g(mp_ctx* c) {
+    const unsigned grid = grid_for(c->n * G, 256);
+    if (c->p.svgd_precond) k_svgd<G, true><<<grid, 256, 0, c->stream>>>(svgd_args(c, c->nbr_cur));
+    else k_svgd<G, false><<<grid, 256, 0, c->stream>>>(svgd_args(c, c->nbr_cur));
     MP_LAUNCHED(c);
     return MP_OK;
 }
 
 template <int G>
-static int launch_svgd_g(mp_ctx* c) {
-    int64_t threads = c->n * G;
-    if (c->p.svgd_precond)
-        k_svgd<G, true><<<grid_for(threads, 256), 256, 0, c->stream>>>(
-            c->poses[c->cur], c->n, c->p.K, c->nbr_ids[c->nbr_cur], c->nbr_k, c->nbr_d, c->psi, c->p.sigma_r,
-            c->p.sigma_t, c->pinv, c->phi);
-    else
-        k_svgd<G, false><<<grid_for(threads, 256), 256, 0, c->stream>>>(
-            c->poses[c->cur], c->n, c->p.K, c->nbr_ids[c->nbr_cur], c->nbr_k, c->nbr_d, c->psi, c->p.sigma_r,
-            c->p.sigma_t, nullptr, c->phi);
+void plan_svgd_g(mp_group* Gr, int p, std::vector<GOp>& plan, bool pre) {
+    std::vector<SvgdArgs> tab;
+    std::vector<int64_t> blocks;
+    std::vector<int> which;
+    for (int i = 0; i < Gr->size(); ++i) {
+        mp_ctx* c = Gr->ctx[i];
+        tab.push_back(svgd_args(c, c->nbr_cur ^ p ^ 1));   // the list the merge of this step wrote
+        blocks.push_back((c->n * G + 255) / 256);
+        if (svgd_lanes(c->p.K) == G && (c->p.svgd_precond != 0) == pre) which.push_back(i);
+    }
+    if (which.empty()) return;
+    unsigned nblk = 0;
+    const GBlk* map = Gr->block_map(blocks, &nblk, which);
+    const SvgdArgs* t = Gr->upload(tab);
+    if (pre) plan_kernel<SvgdOp<G, true>>(plan, t, map, nblk);
+    else plan_kernel<SvgdOp<G, false>>(plan, t, map, nblk);
+}
+
+}  // namespace
+
+int mp_launch_predict(mp_ctx* c) {
+    k_predict<<<grid_for(c->n, 256), 256, 0, c->stream>>>(pred_args(c, c->step_dev));
+    MP_LAUNCHED(c);
+    return MP_OK;
+}
+
+int mp_launch_solve(mp_ctx* c) {
+    k_solve<<<grid_for(c->n, 128), 128, 0, c->stream>>>(solve_args(c));
     MP_LAUNCHED(c);
     return MP_OK;
 }
 
 int mp_launch_svgd(mp_ctx* c) {
-    int K = c->p.K;
-    if (K <= 1) return launch_svgd_g<1>(c);
-    if (K <= 2) return launch_svgd_g<2>(c);
-    if (K <= 4) return launch_svgd_g<4>(c);
-    if (K <= 8) return launch_svgd_g<8>(c);
-    if (K <= 16) return launch_svgd_g<16>(c);
-    return launch_svgd_g<32>(c);
+    switch (svgd_lanes(c->p.K)) {
+        case 1: return launch_svgd_g<1>(c);
+        case 2: return launch_svgd_g<2>(c);
+        case 4: return launch_svgd_g<4>(c);
+        case 8: return launch_svgd_g<8>(c);
+        case 16: return launch_svgd_g<16>(c);
+        default: return launch_svgd_g<32>(c);
+    }
+}
+
+int mp_plan_predict(mp_group* G, int, std::vector<GOp>& plan) {
+    std::vector<PredArgs> tab;
+    std::vector<int64_t> blocks;
+    for (int i = 0; i < G->size(); ++i) {
+        tab.push_back(pred_args(G->ctx[i], G->sd_dev + i));
+        blocks.push_back((G->ctx[i]->n + 255) / 256);
+    }
+    unsigned nblk = 0;
+    const GBlk* map = G->block_map(blocks, &nblk);
+    plan_kernel<PredOp>(plan, G->upload(tab), map, nblk);
+    return G->err;
+}
+
+int mp_plan_solve_svgd(mp_group* G, int p, std::vector<GOp>& plan) {
+    std::vector<SolveArgs> tab;
+    std::vector<int64_t> blocks;
+    for (int i = 0; i < G->size(); ++i) {
+        tab.push_back(solve_args(G->ctx[i]));
+        blocks.push_back((G->ctx[i]->n + 127) / 128);
+    }
+    unsigned nblk = 0;
+    const GBlk* map = G->block_map(blocks, &nblk);
+    plan_kernel<SolveOp>(plan, G->upload(tab), map, nblk);
+    for (int pre = 0; pre < 2; ++pre) {
+        plan_svgd_g<1>(G, p, plan, pre);
+        plan_svgd_g<2>(G, p, plan, pre);
+        plan_svgd_g<4>(G, p, plan, pre);
+        plan_svgd_g<8>(G, p, plan, pre);
+        plan_svgd_g<16>(G, p, plan, pre);
+        plan_svgd_g<32>(G, p, plan, pre);
+    }
+    return G->err;
 }
 
 int mp_launch_init_uniform(mp_ctx* c, const float lo[6], const float hi[6]) {

@@ -107,6 +107,9 @@ void fill_step_host(mp_ctx* c, StepDev* h) {
     R[6] = 2 * (qx * qz - qw * qy); R[7] = 2 * (qy * qz + qw * qx); R[8] = 1 - 2 * (qx * qx + qy * qy);
     for (int r = 0; r < 3; ++r)
         h->lsh_tinv[r] = -(R[r] * c->lsh_t[0] + R[3 + r] * c->lsh_t[1] + R[6 + r] * c->lsh_t[2]);
+    // rotation of the inverse quaternion: R^T
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) h->lsh_R[3 * r + k] = R[3 * k + r];
     for (int k = 0; k < 6; ++k) h->lsh_delta[k] = c->lsh_delta[k];
     for (int k = 0; k < 4; ++k) h->dq[k] = c->odom_q[k];
     for (int k = 0; k < 3; ++k) h->dt[k] = c->odom_t[k];

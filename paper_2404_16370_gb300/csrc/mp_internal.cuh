@@ -9,6 +9,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "../../include/megaparticles.h"
 
@@ -29,7 +30,7 @@
 // T_LSH^-1 and the offset delta, Eq. 10) and the prediction's motion dT, noise
 // factor and counter (Eq. 1).
 struct StepDev {
-    double lsh_qinv[4], lsh_tinv[3], lsh_delta[6];
+    double lsh_qinv[4], lsh_R[9], lsh_tinv[3], lsh_delta[6];   // lsh_R: rotation of lsh_qinv, row-major
     float dq[4], dt[3], L[21];
     int32_t noise;
     uint32_t step;
@@ -458,3 +459,103 @@ int mp_launch_unpack_poses(mp_ctx* c, const float4* src, float* dst7_dev);
 int mp_launch_gather_gn(mp_ctx* c, float* dst_dev);
 // k_posterior.cu
 int mp_launch_posterior(mp_ctx* c);
+
+// ---------------------------------------------------------------------------
+// grouped launches (batched instances, mp_batch_*): one kernel over the blocks
+// of many instances. Block b of a grouped launch runs block (map[b].bx,
+// map[b].by) of instance map[b].inst with that instance's argument record
+// tab[map[b].inst], through the same body (Op::run) as the instance's own
+// launch, so a grouped phase computes what the per-instance launches compute.
+// ---------------------------------------------------------------------------
+struct GBlk {
+    int32_t inst, bx, by, pad;
+};
+
+template <typename Op>
+__global__ void __launch_bounds__(Op::THREADS, Op::MINB) k_group(const typename Op::Args* __restrict__ tab,
+                                                               const GBlk* __restrict__ map) {
+    const GBlk g = map[blockIdx.x];
+    Op::run(tab[g.inst], (unsigned)g.bx, (unsigned)g.by);
+}
+
+// One operation of a batch step's plan: a grouped kernel (func = k_group<Op>,
+// arguments tab and map, grid blocks of block threads), a device memset or a
+// device-to-device copy. The plan is captured into a CUDA graph.
+struct GOp {
+    enum Kind { KERNEL, MEMSET, COPY } kind;
+    const void* func;
+    unsigned grid, block;
+    const void* tab;
+    const GBlk* map;
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+
+// The instances of a batch as the planners see them: contexts, the device
+// copies of the step inputs (all scans in one buffer, one StepDev each), and
+// the device tables the plans point to (freed with the group).
+struct mp_group {
+    std::vector<mp_ctx*> ctx;
+    std::vector<int32_t> n_scan;
+    std::vector<int64_t> scan_off;   // floats into scan_dev
+    float* scan_dev = nullptr;
+    StepDev* sd_dev = nullptr;
+    std::vector<void*> arena;
+    int err = 0;                     // first allocation / copy error (MP_ENOMEM / MP_ECUDA)
+
+    int size() const { return (int)ctx.size(); }
+    // device copy of a host array (nullptr and err set on failure)
+    const void* upload(const void* host, size_t bytes);
+    template <typename T>
+    const T* upload(const std::vector<T>& v) {
+        return static_cast<const T*>(upload(v.data(), sizeof(T) * v.size()));
+    }
+    // block map over the instances in `which` (all when empty): instance i
+    // gets blocks[i] x ysplit[i] blocks (ysplit empty = 1); *nblk = total
+    const GBlk* block_map(const std::vector<int64_t>& blocks, unsigned* nblk, const std::vector<int>& which = {},
+                          const std::vector<int>& ysplit = {});
+    void release();
+};
+
+// Appends a grouped kernel to a plan (nothing when no instance has blocks).
+template <typename Op>
+inline void plan_kernel(std::vector<GOp>& plan, const typename Op::Args* tab, const GBlk* map, unsigned nblk) {
+    if (nblk == 0 || !tab || !map) return;
+    GOp o{};
+    o.kind = GOp::KERNEL;
+    o.func = reinterpret_cast<const void*>(&k_group<Op>);
+    o.grid = nblk;
+    o.block = Op::THREADS;
+    o.tab = tab;
+    o.map = map;
+    plan.push_back(o);
+}
+inline void plan_memset(std::vector<GOp>& plan, void* dst, size_t bytes) {
+    GOp o{};
+    o.kind = GOp::MEMSET;
+    o.dst = dst;
+    o.bytes = bytes;
+    plan.push_back(o);
+}
+inline void plan_copy(std::vector<GOp>& plan, void* dst, const void* src, size_t bytes) {
+    GOp o{};
+    o.kind = GOp::COPY;
+    o.dst = dst;
+    o.src = src;
+    o.bytes = bytes;
+    plan.push_back(o);
+}
+
+// Planners: the grouped launches of one stage for neighbour-list parity p.
+// They run while every context still has the list index nbr_cur0 it had when
+// the batch was created: graph p's merge reads list nbr_cur0 ^ p and writes
+// nbr_cur0 ^ p ^ 1, which SVGD and the posterior then read. Each returns
+// MP_OK or the group's error.
+int mp_plan_predict(mp_group* G, int p, std::vector<GOp>& plan);
+int mp_plan_scan(mp_group* G, int p, std::vector<GOp>& plan);
+int mp_plan_lsh_sort(mp_group* G, int p, std::vector<GOp>& plan);
+int mp_plan_merge(mp_group* G, int p, std::vector<GOp>& plan);
+int mp_plan_likelihood(mp_group* G, int p, std::vector<GOp>& plan);
+int mp_plan_solve_svgd(mp_group* G, int p, std::vector<GOp>& plan);
+int mp_plan_posterior(mp_group* G, int p, std::vector<GOp>& plan);

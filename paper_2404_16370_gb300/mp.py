@@ -427,7 +427,7 @@ def _batch_lib():
 
 
 def mp_batch_create(ctxs, n_scan, cuda_stream, tune_scans=None):
-    """ctxs: contexts (each on its own stream); n_scan: fixed scan size of each;
+    """ctxs: contexts (their streams may be cuda_stream itself); n_scan: fixed scan size of each;
     tune_scans: list of (n_scan[i], 3) float32 arrays or None."""
     n = len(ctxs)
     arr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])

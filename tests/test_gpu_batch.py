@@ -46,19 +46,19 @@ def test_likelihood_split_matches_unsplit():
         assert np.all(np.abs(out[split] - ref) <= 2e-5 * scale)
 
 
-def _instances(torch, specs):
+def _instances(stream, specs):
+    """Box-room instances; every context on `stream` (instances never run
+    concurrently: the batch and the eager steps are ordered on one stream)."""
     from paper_2404_16370_gb300 import mp
-    ctxs, streams, data = [], [], []
+    ctxs, data = [], []
     for seed, n_part, n_rays in specs:
         room, sc, parts = _room_instance(seed, n_part, n_rays)
-        st = mp.mp_stream_create()
         ctx = mp.mp_init_map(room.map_points, mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, n_part),
-                             cuda_stream=st)
+                             cuda_stream=stream)
         mp.mp_init_particles(ctx, n_part, poses=parts)
         ctxs.append(ctx)
-        streams.append(st)
         data.append((sc, parts))
-    return ctxs, streams, data
+    return ctxs, data
 
 
 SPECS = [(1, 1024, 512), (2, 3000, 700), (3, 4096, 512)]
@@ -72,12 +72,24 @@ def _odometry(n, step):
     return T, cov
 
 
-def test_batch_step_equals_sequential_steps(torch):
+def _compare(A, B):
     from paper_2404_16370_gb300 import mp
-    A, sa, data = _instances(torch, SPECS)
-    B, sb, _ = _instances(torch, SPECS)
-    origin = mp.mp_stream_create()
-    batch = mp.mp_batch_create(A, [len(d[0]) for d in data], origin)
+    for i in range(len(A)):
+        pa, prob_a = mp.mp_get_posterior(A[i])
+        pb, prob_b = mp.mp_get_posterior(B[i])
+        for which in (mp.MP_BUF_POSES, mp.MP_BUF_POST, mp.MP_BUF_NBR_IDS, mp.MP_BUF_GN):
+            assert np.array_equal(mp.mp_get_buffer(A[i], which), mp.mp_get_buffer(B[i], which)), (i, which)
+        assert np.array_equal(pa, pb) and prob_a == prob_b
+
+
+def test_batch_step_equals_sequential_steps(torch):
+    """Three instances stepped by the grouped batch graph equal the same
+    instances stepped one by one with mp_step, bit for bit."""
+    from paper_2404_16370_gb300 import mp
+    st = mp.mp_stream_create()
+    A, data = _instances(st, SPECS)
+    B, _ = _instances(st, SPECS)
+    batch = mp.mp_batch_create(A, [len(d[0]) for d in data], st)
     try:
         for step in range(3):
             T, cov = _odometry(len(SPECS), step)
@@ -86,25 +98,58 @@ def test_batch_step_equals_sequential_steps(torch):
                 mp.mp_step(ctx, data[i][0], T[i], cov[i])
         for i in range(len(SPECS)):
             assert mp.mp_batch_split(batch, i) == 1
-            pa, prob_a = mp.mp_get_posterior(A[i])
-            pb, prob_b = mp.mp_get_posterior(B[i])
-            for which in (mp.MP_BUF_POSES, mp.MP_BUF_POST, mp.MP_BUF_NBR_IDS):
-                assert np.array_equal(mp.mp_get_buffer(A[i], which), mp.mp_get_buffer(B[i], which)), (i, which)
-            assert np.array_equal(pa, pb) and prob_a == prob_b
+        _compare(A, B)
     finally:
         mp.mp_batch_destroy(batch)
         for c in A + B:
             mp.mp_destroy(c)
-        for st in sa + sb + [origin]:
-            mp.mp_stream_destroy(st)
+        mp.mp_stream_destroy(st)
+
+
+def test_batch_mixed_presets_equal_sequential_steps(torch):
+    """Instances of different presets and list lengths (a box room with
+    K = 16 and an outdoor scene with K = 32, one with an odd number of
+    posterior sweeps) in one batch: bit for bit the eager steps."""
+    from paper_2404_16370_gb300 import mp
+    st = mp.mp_stream_create()
+    sc_out = synth.outdoor(21, n_map=60_000)
+    gt = synth.outdoor_trajectory(1, 0, seed=22, scene=sc_out)[0]
+    scan_out = synth.scan(sc_out, gt, synth.lidar_dirs(16, 128), 0.03, 23, dropout=0.1, max_range=60.0).astype(np.float32)
+    parts_out = synth.outdoor_particles(sc_out, 2500, 24)
+    room, scan_room, parts_room = _room_instance(5, 2048, 600)
+
+    def make():
+        p_room = mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, 2048)
+        p_room.post_iters = 7
+        c1 = mp.mp_init_map(room.map_points, p_room, cuda_stream=st)
+        mp.mp_init_particles(c1, 2048, poses=parts_room)
+        c2 = mp.mp_init_map(sc_out.map_points, mp.mp_default_params(mp.MP_PRESET_OUTDOOR, 2500), cuda_stream=st)
+        mp.mp_init_particles(c2, 2500, poses=parts_out)
+        return [c1, c2]
+
+    A, B = make(), make()
+    scans = [scan_room, scan_out]
+    batch = mp.mp_batch_create(A, [len(s) for s in scans], st)
+    try:
+        for step in range(3):
+            T, cov = _odometry(2, step)
+            mp.mp_batch_step(batch, scans, T, cov)
+            for i, ctx in enumerate(B):
+                mp.mp_step(ctx, scans[i], T[i], cov[i])
+        _compare(A, B)
+    finally:
+        mp.mp_batch_destroy(batch)
+        for c in A + B:
+            mp.mp_destroy(c)
+        mp.mp_stream_destroy(st)
 
 
 def test_autotuned_batch_runs(torch):
     from paper_2404_16370_gb300 import mp
     specs = [(4, 2048, 4096), (5, 8192, 2048), (6, 1024, 512)]
-    A, sa, data = _instances(torch, specs)
-    origin = mp.mp_stream_create()
-    batch = mp.mp_batch_create(A, [len(d[0]) for d in data], origin, tune_scans=[d[0] for d in data])
+    st = mp.mp_stream_create()
+    A, data = _instances(st, specs)
+    batch = mp.mp_batch_create(A, [len(d[0]) for d in data], st, tune_scans=[d[0] for d in data])
     try:
         splits = [mp.mp_batch_split(batch, i) for i in range(len(specs))]
         assert all(s in (1, 2, 4, 8, 16) for s in splits)
@@ -118,5 +163,23 @@ def test_autotuned_batch_runs(torch):
         mp.mp_batch_destroy(batch)
         for c in A:
             mp.mp_destroy(c)
-        for st in sa + [origin]:
-            mp.mp_stream_destroy(st)
+        mp.mp_stream_destroy(st)
+
+
+def test_batch_refuses_outside_steps(torch):
+    """A batched context stepped with mp_step is refused by the next batch
+    step (its neighbour-list index no longer matches the captured graph)."""
+    from paper_2404_16370_gb300 import mp
+    st = mp.mp_stream_create()
+    A, data = _instances(st, SPECS[:2])
+    batch = mp.mp_batch_create(A, [len(d[0]) for d in data], st)
+    try:
+        mp.mp_batch_step(batch, [d[0] for d in data])
+        mp.mp_step(A[0], data[0][0])
+        with pytest.raises(mp.MPError):
+            mp.mp_batch_step(batch, [d[0] for d in data])
+    finally:
+        mp.mp_batch_destroy(batch)
+        for c in A:
+            mp.mp_destroy(c)
+        mp.mp_stream_destroy(st)
