@@ -190,11 +190,17 @@ __global__ void k_map_normals(const float4* __restrict__ pts, int64_t n, CellGri
     valid[i] = 1;
 }
 
-// Scan points: brute force over the whole scan, staged through shared memory.
-// 64 threads a CTA: a scan of a few thousand points then spreads over as many
-// CTAs as the GPU has SMs.
+// Scan points: brute force over the whole scan, staged through shared memory
+// in tiles. SCAN_PARTS threads share a point, each scanning every
+// SCAN_PARTS-th candidate of a tile with its own top-k, so that a scan of a
+// few thousand points still keeps every SM busy; the lists and counts are then
+// merged in shared memory (the top-k by (d, j) and the count do not depend on
+// the order in which candidates are seen), and one thread per point computes
+// the normal.
 #define SCAN_TILE 1024
-#define SCAN_CTA 64
+#define SCAN_PARTS 8
+#define SCAN_CTA 256
+#define SCAN_PTS (SCAN_CTA / SCAN_PARTS)
 
 // Arguments of the per-step scan kernels (raw n x 3 points in, normals,
 // validity and the compacted broadcast pairs out).
@@ -233,7 +239,11 @@ __device__ __forceinline__ void ScanNormalsOp::run(const ScanArgs& args, unsigne
     float* __restrict__ normals = args.normals;
     uint8_t* __restrict__ valid = args.valid;
     __shared__ float sx[SCAN_TILE], sy[SCAN_TILE], sz[SCAN_TILE];
-    int i = (int)bx * THREADS + threadIdx.x;
+    __shared__ float Ds[SCAN_PTS][SCAN_PARTS][MP_COVK];
+    __shared__ int Js[SCAN_PTS][SCAN_PARTS][MP_COVK];
+    __shared__ int cs[SCAN_PTS][SCAN_PARTS];
+    const int part = threadIdx.x % SCAN_PARTS, pl = threadIdx.x / SCAN_PARTS;
+    const int i = (int)bx * SCAN_PTS + pl;
     float px = 0, py = 0, pz = 0;
     if (i < n) { px = raw[3 * i]; py = raw[3 * i + 1]; pz = raw[3 * i + 2]; }
     float D[MP_COVK];
@@ -243,13 +253,13 @@ __device__ __forceinline__ void ScanNormalsOp::run(const ScanArgs& args, unsigne
     int cnt = 0;
     for (int base = 0; base < n; base += SCAN_TILE) {
         __syncthreads();
-        for (int t = threadIdx.x; t < SCAN_TILE && base + t < n; t += blockDim.x) {
+        for (int t = threadIdx.x; t < SCAN_TILE && base + t < n; t += SCAN_CTA) {
             sx[t] = raw[3 * (base + t)]; sy[t] = raw[3 * (base + t) + 1]; sz[t] = raw[3 * (base + t) + 2];
         }
         __syncthreads();
-        int m = min(SCAN_TILE, n - base);
+        const int m = min(SCAN_TILE, n - base);
         if (i < n) {
-            for (int t = 0; t < m; ++t) {
+            for (int t = part; t < m; t += SCAN_PARTS) {
                 float d2 = dist2_exact(px, py, pz, sx[t], sy[t], sz[t]);
                 if (d2 <= r2) {
                     cnt++;
@@ -258,25 +268,43 @@ __device__ __forceinline__ void ScanNormalsOp::run(const ScanArgs& args, unsigne
             }
         }
     }
-    if (i >= n) return;
+#pragma unroll
+    for (int s = 0; s < MP_COVK; ++s) { Ds[pl][part][s] = D[s]; Js[pl][part][s] = J[s]; }
+    cs[pl][part] = cnt;
+    __syncthreads();
+    // one thread per point (a dense warp) merges the parts and takes the normal
+    if (threadIdx.x >= SCAN_PTS) return;
+    const int q = threadIdx.x, iq = (int)bx * SCAN_PTS + q;
+    if (iq >= n) return;
+#pragma unroll
+    for (int s = 0; s < MP_COVK; ++s) { D[s] = Ds[q][0][s]; J[s] = Js[q][0][s]; }
+    cnt = cs[q][0];
+    for (int pp = 1; pp < SCAN_PARTS; ++pp) {
+        cnt += cs[q][pp];
+        for (int s = 0; s < MP_COVK; ++s) {
+            const float d = Ds[q][pp][s];
+            if (!(d < INFINITY)) break;   // a part's list is sorted: the rest is empty
+            topk_insert(D, J, d, Js[q][pp][s]);
+        }
+    }
     int m = min(cnt, k);
     if (m < kmin) {
-        valid[i] = 0;
-        normals[3 * i] = normals[3 * i + 1] = normals[3 * i + 2] = 0.f;
+        valid[iq] = 0;
+        normals[3 * iq] = normals[3 * iq + 1] = normals[3 * iq + 2] = 0.f;
         return;
     }
 #ifdef MP_CHECKED
     for (int s = 0; s < m; ++s)
         if (!MP_DCHECK(J[s] >= 0 && J[s] < n, "scan neighbour index", J[s])) m = 0;
     if (m == 0) {
-        valid[i] = 0;
+        valid[iq] = 0;
         return;
     }
 #endif
     float nv[3];
     neighbourhood_normal(tmp_pts, J, m, nv);
-    normals[3 * i] = nv[0]; normals[3 * i + 1] = nv[1]; normals[3 * i + 2] = nv[2];
-    valid[i] = 1;
+    normals[3 * iq] = nv[0]; normals[3 * iq + 1] = nv[1]; normals[3 * iq + 2] = nv[2];
+    valid[iq] = 1;
 }
 
 // Order-preserving compaction of the valid scan points into 48-byte records of
@@ -598,7 +626,7 @@ int mp_launch_scan_prepare(mp_ctx* c) {
     const ScanArgs A = scan_args(c, c->scan_raw, n);
     k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
-    k_scan_normals<<<grid_for(n, SCAN_CTA), SCAN_CTA, 0, c->stream>>>(A);
+    k_scan_normals<<<grid_for(n, SCAN_PTS), SCAN_CTA, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
     k_scan_compact<<<1, 1024, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
@@ -617,7 +645,7 @@ int mp_launch_point_gaussians(mp_ctx* c, const float* raw_dev, int n, float4* tm
     A.nvalid = nullptr;
     k_scan_to_float4<<<grid_for(n, 256), 256, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
-    k_scan_normals<<<grid_for(n, SCAN_CTA), SCAN_CTA, 0, c->stream>>>(A);
+    k_scan_normals<<<grid_for(n, SCAN_PTS), SCAN_CTA, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
     return MP_OK;
 }
@@ -631,7 +659,7 @@ int mp_plan_scan(mp_group* G, int, std::vector<GOp>& plan) {
         const int n = G->n_scan[i];
         tab.push_back(scan_args(G->ctx[i], G->scan_dev + G->scan_off[i], n));
         b256.push_back((n + 255) / 256);
-        b64.push_back((n + SCAN_CTA - 1) / SCAN_CTA);
+        b64.push_back((n + SCAN_PTS - 1) / SCAN_PTS);
         b1.push_back(1);
     }
     const ScanArgs* t = G->upload(tab);

@@ -41,7 +41,8 @@ struct PostArgs {
     const int32_t* ids;
     int K;
     const float* kk;
-    double* w;            // n x K normalised weights
+    double* w;            // normalised weights, slot-major: w[l * n + i]
+    int32_t* ids_t;       // the ids, slot-major: ids_t[l * n + i]
     double* invden;       // 1 / sum_j k_ij
     int iters;
     const float4* poses;
@@ -132,7 +133,8 @@ struct ReduceSumOp {
 // Normalised weights w_ij = k_ij / sum_j k_ij (FP64) and 1 / sum_j k_ij,
 // fixed for the sweeps of a step: a sweep entry is then one FP64 fused
 // multiply-add (GB300's FP64 rate is low, so the division and the FP32 -> FP64
-// conversion are taken out of the ten sweeps).
+// conversion are taken out of the ten sweeps). Weights and ids are written
+// slot-major ([l * n + i]) so that the sweeps' loads are coalesced.
 struct PostWeightsOp {
     using Args = PostArgs;
     static constexpr int THREADS = 256, MINB = 1;
@@ -148,15 +150,19 @@ struct PostWeightsOp {
         for (int l = 0; l < K; ++l)
             if (ids[i * K + l] >= 0) den += (double)kk[i * K + l];
         const double inv = den > 0.0 ? 1.0 / den : 0.0;
-        for (int l = 0; l < K; ++l) w[i * K + l] = ids[i * K + l] >= 0 ? (double)kk[i * K + l] * inv : 0.0;
+        for (int l = 0; l < K; ++l) {
+            const int32_t j = ids[i * K + l];
+            w[l * n + i] = j >= 0 ? (double)kk[i * K + l] * inv : 0.0;
+            A.ids_t[l * n + i] = j;
+        }
         A.invden[i] = inv;
     }
 };
 
 // Jacobi sweep `it` (the block map's y index) of Eq. 11, one thread per
 // particle: p'_i = sum_j w_ij p_j with FP64 fused multiply-adds over the list
-// (rows read with 16-byte loads when the list length is a multiple of 4); a
-// particle whose kernel weights sum to zero keeps its value.
+// in slot order (slot-major ids and weights: a warp's loads of one slot are
+// contiguous); a particle whose kernel weights sum to zero keeps its value.
 template <int KT>
 struct PostSweepOp {
     using Args = PostArgs;
@@ -165,29 +171,16 @@ struct PostSweepOp {
         const double* __restrict__ pin = (it & 1) ? A.post : A.post_tmp;
         double* __restrict__ pout = (it & 1) ? A.post_tmp : A.post;
         const int64_t n = A.n;
-        const int32_t* __restrict__ ids = A.ids;
+        const int32_t* __restrict__ ids = A.ids_t;
         const double* __restrict__ w = A.w;
         const int K = KT > 0 ? KT : A.K;   // compile-time list length for the common sizes
         int64_t i = (int64_t)bx * THREADS + threadIdx.x;
         if (i >= n) return;
         double num = 0.0;
-        if (KT > 0 && KT % 4 == 0) {
-            const int4* row = reinterpret_cast<const int4*>(ids + i * KT);
-            const double2* wr = reinterpret_cast<const double2*>(w + i * KT);
-#pragma unroll
-            for (int q = 0; q < KT / 4; ++q) {
-                const int4 j4 = __ldg(row + q);
-                const double2 w0 = __ldg(wr + 2 * q), w1 = __ldg(wr + 2 * q + 1);
-                if (j4.x >= 0 && MP_DCHECK(j4.x < n, "neighbour id", j4.x)) num = fma(w0.x, __ldg(pin + j4.x), num);
-                if (j4.y >= 0 && MP_DCHECK(j4.y < n, "neighbour id", j4.y)) num = fma(w0.y, __ldg(pin + j4.y), num);
-                if (j4.z >= 0 && MP_DCHECK(j4.z < n, "neighbour id", j4.z)) num = fma(w1.x, __ldg(pin + j4.z), num);
-                if (j4.w >= 0 && MP_DCHECK(j4.w < n, "neighbour id", j4.w)) num = fma(w1.y, __ldg(pin + j4.w), num);
-            }
-        } else {
-            for (int l = 0; l < K; ++l) {
-                const int j = __ldg(ids + i * K + l);
-                if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(__ldg(w + i * K + l), __ldg(pin + j), num);
-            }
+#pragma unroll(KT > 0 ? KT : 1)
+        for (int l = 0; l < K; ++l) {
+            const int j = __ldg(ids + l * n + i);
+            if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(__ldg(w + l * n + i), __ldg(pin + j), num);
         }
         pout[i] = A.invden[i] > 0.0 ? num : pin[i];
     }
@@ -314,6 +307,7 @@ PostArgs post_args(mp_ctx* c, int cur) {
     A.K = c->p.K;
     A.kk = c->nbr_k;
     A.w = c->post_w;
+    A.ids_t = c->post_ids;
     A.invden = c->post_invden;
     A.iters = c->p.post_iters;
     A.poses = c->poses[c->cur];

@@ -155,6 +155,7 @@ void dfree(T*& p) {
 void free_particles(mp_ctx* c) {
     dfree(c->poses[0]); dfree(c->poses[1]);
     dfree(c->logprior); dfree(c->post); dfree(c->post_tmp); dfree(c->post_init); dfree(c->post_invden); dfree(c->post_w);
+    dfree(c->post_ids);
     dfree(c->loglik); dfree(c->n_in); dfree(c->keys); dfree(c->buckets); dfree(c->sorted_ids); dfree(c->rank);
     dfree(c->seg); dfree(c->sort_keys[0]); dfree(c->sort_keys[1]); dfree(c->sort_ids[0]); dfree(c->sort_ids[1]);
     dfree(c->radix_counts); dfree(c->scan_tmp);
@@ -181,6 +182,7 @@ int alloc_particles(mp_ctx* c, int64_t n) {
 #define A_(ptr, cnt) if ((rc = dalloc(c, &(ptr), (size_t)(cnt)))) return rc
     A_(c->poses[0], 2 * n);
     A_(c->logprior, n); A_(c->post, n); A_(c->post_tmp, n); A_(c->post_init, n); A_(c->post_invden, n); A_(c->post_w, n * K);
+    A_(c->post_ids, n * K);
     A_(c->loglik, n); A_(c->n_in, n); A_(c->keys, n); A_(c->buckets, n); A_(c->sorted_ids, n); A_(c->rank, n);
     A_(c->seg, 2 * ((int64_t)1 << c->p.n_buckets_log2));
     A_(c->sort_keys[0], n); A_(c->sort_keys[1], n); A_(c->sort_ids[0], n); A_(c->sort_ids[1], n);

@@ -66,7 +66,8 @@ struct mp_ctx {
     double* post_tmp;
     double* post_init;      // unnormalised initial posterior exp(l - max l)
     double* post_invden;    // 1 / sum_j k_ij of the current lists
-    double* post_w;         // K per particle: k_ij / sum_j k_ij (FP64), fixed for a step's sweeps
+    double* post_w;         // k_ij / sum_j k_ij (FP64), fixed for a step's sweeps; slot-major: [l * n + i]
+    int32_t* post_ids;      // the lists' ids, slot-major [l * n + i] (coalesced sweeps)
     float* loglik;
     int32_t* n_in;
     uint32_t* keys;
