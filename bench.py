@@ -257,6 +257,27 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def random_read_probe(torch, mp, n_words, stream):
+    """Context for the sector roofline: the rate of independent, uniformly
+    random 4-byte reads over a buffer the size of the NNF grid (each fetches
+    one 32-byte DRAM sector), outside the timed region. The likelihood's
+    lookups are not uniform (consecutive points of a particle fall in nearby
+    voxels, often in the same DRAM row), so this is a reference below it, not a
+    ceiling; the roofline's peak stays the measured copy bandwidth."""
+    try:
+        words = torch.zeros(int(n_words), dtype=torch.int32, device=torch.cuda.current_device())
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        blocks, reads = 8 * sms, 256
+        ms = mp.mp_probe_random_reads(words, blocks, reads, repeats=5, cuda_stream=stream.cuda_stream)
+        n_reads = blocks * 256 * reads
+        del words
+        return {"buffer_bytes": 4 * int(n_words), "reads_per_run": n_reads, "ms_per_run": ms,
+                "reads_per_s": n_reads / (ms / 1e3), "sector_gbs": n_reads * 32 / (ms / 1e3) / 1e9,
+                "method": "mp_probe_random_reads: independent LCG indices, 8 CTAs of 256 threads per SM"}
+    except Exception as e:   # a measurement aid only
+        return {"error": str(e)}
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_setup("nccl")
@@ -326,8 +347,10 @@ def run_gpu(args):
         run_steps(args.warmup, n_steps, host=True)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
+        nnf_voxels = int(np.prod(mp.mp_map_info(ctx)["dims"].astype(np.int64)))
     finally:
         mp.mp_destroy(ctx)
+    probe = random_read_probe(torch, mp, nnf_voxels, stream) if rank == 0 else None
 
     if rank != 0:
         return
@@ -366,7 +389,8 @@ def run_gpu(args):
         "roofline_hbm_sector": {"bound": "hbm", "kernel": "k_likelihood", "achieved": sector_gbs, "peak": hbm_gbs,
                                 "unit": "GB/s", "frac": (sector_gbs / hbm_gbs) if sector_gbs else None,
                                 "peak_source": hbm_src,
-                                "model": "one 32-byte NNF sector from DRAM per pair (spread particles)"},
+                                "model": "one 32-byte NNF sector from DRAM per pair (spread particles)",
+                                "uniform_random_reads": probe},
         "roofline_step": {"bound_ms": step_bound, "measured_ms": 1e3 * t_max / args.steps,
                           "frac": step_bound / (1e3 * t_max / args.steps),
                           "stage_bound_ms": bounds,

@@ -529,3 +529,22 @@ def mp_step_gicp(ctx, scan, cov_scale=1.0):
         return
     sp, keep = _ptr(scan, np.float32)
     _check(L.mp_step_gicp(ctx, sp, int(scan.shape[0]), float(cov_scale)), ctx)
+
+
+# ---------------------------------------------------------------------------
+# measurement helper
+
+
+def mp_probe_random_reads(words, blocks, reads_per_thread, repeats=5, cuda_stream=None) -> float:
+    """Mean ms of one run of blocks x 256 x reads_per_thread independent random
+    4-byte reads over `words` (a device uint32 tensor)."""
+    L = lib()
+    L.mp_probe_random_reads.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                        C.POINTER(C.c_float)]
+    L.mp_probe_random_reads.restype = C.c_int
+    ms = C.c_float()
+    rc = L.mp_probe_random_reads(C.c_void_p(words.data_ptr()), int(words.numel()), int(blocks), int(reads_per_thread),
+                                 int(repeats), C.c_void_p(cuda_stream) if cuda_stream else None, C.byref(ms))
+    if rc != MP_OK:
+        raise MPError(rc, "mp_probe_random_reads failed")
+    return float(ms.value)
