@@ -45,6 +45,8 @@ constexpr int LK_THREADS = 128;
 constexpr int LK_PER_CTA = 2 * LK_THREADS;
 constexpr int LK_CHUNK = 256;   // points per stage: 256 x 48 B = 12 KB
 constexpr int LK_MINB = 3;      // CTAs per SM the register budget must allow (163 registers)
+constexpr int LKH_MINB = 4;     // the 16-bit forms: their per-pair values take half the registers, so a
+                                // fourth CTA (16 warps per SM) fits in 128 registers
 
 struct LkArgs {
     const float4* poses;
@@ -761,9 +763,9 @@ int mp_launch_likelihood(mp_ctx* c) {
             MP_LAUNCHED(c);
         }
         if (c->precision == MP_PREC_BF16)
-            k_likelihood_h<__nv_bfloat162, LK_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
+            k_likelihood_h<__nv_bfloat162, LKH_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
         else
-            k_likelihood_h<__half2, LK_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
+            k_likelihood_h<__half2, LKH_MINB><<<grid, LK_THREADS, 0, c->stream>>>(A);
     } else {
         // the scan split (a tuning knob for small particle counts): partial
         // sums of each CTA are added into a zeroed output
