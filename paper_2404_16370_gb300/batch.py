@@ -74,6 +74,16 @@ def release(ctxs):
         mp.mp_destroy(c)
 
 
+def step_all(ctxs, scans, T, cov, s):
+    """mp_step on every instance, one after the other; a failure names the
+    instance and the step."""
+    for i, c in enumerate(ctxs):
+        try:
+            mp.mp_step(c, scans[i], T[i], cov[i])
+        except mp.MPError as e:
+            raise mp.MPError(e.code, f"instance {i}, step {s}: {e}") from None
+
+
 def odometry(n, step):
     rng = np.random.default_rng(7000 + step)
     T = np.tile(np.eye(4), (n, 1, 1))
@@ -89,6 +99,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--small", action="store_true",
                     help="8 box rooms, 2^10..2^13 particles, 512..2048-point scans (the launch-bound regime)")
+    ap.add_argument("--batched-only", action="store_true", help="time only the batched steps (no mp_step baseline)")
     a = ap.parse_args()
     import torch
     t0 = time.perf_counter()
@@ -105,23 +116,23 @@ def main():
            "scan_points_total": int(sum(len(d["scan"]) for d in inst)), "steps": a.steps, "warmup": a.warmup,
            "inputs_s": round(gen_s, 1)}
     stream = mp.mp_stream_create()
+    t_seq = None
     # (a) instance by instance
-    ctxs = make_contexts(inst, stream)
-    try:
-        for s in range(a.warmup):
-            T, cov = odometry(n, s)
-            for i, c in enumerate(ctxs):
-                mp.mp_step(c, scans[i], T[i], cov[i])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for s in range(a.warmup, a.warmup + a.steps):
-            T, cov = odometry(n, s)
-            for i, c in enumerate(ctxs):
-                mp.mp_step(c, scans[i], T[i], cov[i])
-        torch.cuda.synchronize()
-        t_seq = time.perf_counter() - t0
-    finally:
-        release(ctxs)
+    if not a.batched_only:
+        ctxs = make_contexts(inst, stream)
+        try:
+            for s in range(a.warmup):
+                T, cov = odometry(n, s)
+                step_all(ctxs, scans, T, cov, s)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s in range(a.warmup, a.warmup + a.steps):
+                T, cov = odometry(n, s)
+                step_all(ctxs, scans, T, cov, s)
+            torch.cuda.synchronize()
+            t_seq = time.perf_counter() - t0
+        finally:
+            release(ctxs)
     # (b) batched
     ctxs = make_contexts(inst, stream)
     try:
@@ -146,11 +157,12 @@ def main():
         release(ctxs)
         mp.mp_stream_destroy(stream)
     res.update({
-        "sequential": {"instance_steps_per_s": n * a.steps / t_seq, "pairs_per_s": pairs_step * a.steps / t_seq,
-                       "ms_per_step": 1e3 * t_seq / a.steps},
+        "sequential": None if t_seq is None else {
+            "instance_steps_per_s": n * a.steps / t_seq, "pairs_per_s": pairs_step * a.steps / t_seq,
+            "ms_per_step": 1e3 * t_seq / a.steps},
         "batched": {"instance_steps_per_s": n * a.steps / t_bat, "pairs_per_s": pairs_step * a.steps / t_bat,
                     "ms_per_step": 1e3 * t_bat / a.steps, "create_s": round(create_s, 2)},
-        "speedup": t_seq / t_bat,
+        "speedup": None if t_seq is None else t_seq / t_bat,
         "splits": {str(k): splits.count(k) for k in sorted(set(splits))},
     })
     print(json.dumps(res), flush=True)

@@ -47,15 +47,19 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked: bool = False) -> str:
-    build_dir = BUILD + "_checked" if checked else BUILD
-    lib = LIB_CHECKED if checked else LIB
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked=False) -> str:
+    """checked: False, True (printed checks) or "lite" (checks recorded by one
+    atomic, no printf; libmp_checked_lite.so)."""
+    suffix = "_checked_lite" if checked == "lite" else "_checked" if checked else ""
+    build_dir = BUILD + suffix
+    lib = os.path.join(HERE, f"libmp{suffix}.so")
     os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
         glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
     objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DMP_CHECKED"] if checked else [])
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DMP_CHECKED"] if checked else []) + \
+        (["-DMP_CHECKED_LITE"] if checked == "lite" else [])
 
     def compile_one(src_obj):
         src, obj = src_obj
@@ -86,4 +90,4 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
-                checked="--checked" in sys.argv))
+                checked="lite" if "--checked-lite" in sys.argv else "--checked" in sys.argv))

@@ -404,7 +404,30 @@ int mp_cuda_check(mp_ctx* c, cudaError_t e, const char* what);
 // access; on the host every launch outside a stream capture is synchronised,
 // so that a fault is reported at the launch that caused it. In normal builds
 // both macros compile to nothing.
-#ifdef MP_CHECKED
+#if defined(MP_CHECKED) && defined(MP_CHECKED_LITE)
+// The light form (-DMP_CHECKED_LITE, build(checked="lite")): a violation
+// records its source line in a per-file device word with one atomic and
+// skips the access (no printf: the kernels' code stays close to the normal
+// build's); after every synchronised launch the host reads the file's word.
+static __device__ unsigned int mp_dcheck_line;
+#define MP_DCHECK(cond, what, v) ((cond) ? true : (atomicCAS(&mp_dcheck_line, 0u, (unsigned)__LINE__), false))
+int mp_checked_sync(mp_ctx* c, const char* file, int line);
+static inline int mp_dcheck_poll(mp_ctx* c, const char* file, int line) {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, mp_dcheck_line, sizeof(v)) != cudaSuccess) return MP_OK;
+    if (v) {
+        fprintf(stderr, "MP_CHECKED %s:%u: index check fired (kernel launched at line %d)\n", file, v, line);
+        return mp_fail(c, MP_ECUDA, "index check at %s:%u", file, v);
+    }
+    return MP_OK;
+}
+#define MP_CHECKED_SYNC(ctx)                                          \
+    do {                                                              \
+        int _r = mp_checked_sync((ctx), __FILE__, __LINE__);          \
+        if (!_r) _r = mp_dcheck_poll((ctx), __FILE__, __LINE__);      \
+        if (_r) return _r;                                            \
+    } while (0)
+#elif defined(MP_CHECKED)
 #define MP_DCHECK(cond, what, v)                                                                        \
     ((cond) ? true                                                                                      \
             : (printf("MP_CHECKED %s:%d: %s (%lld) block %d thread %d\n", __FILE__, __LINE__, what,      \

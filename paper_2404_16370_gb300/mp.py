@@ -13,7 +13,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 # MP_CHECKED=1: the checked build (bounds-checked kernels, every launch synchronised)
-LIB_PATH = os.path.join(_HERE, "libmp_checked.so" if os.environ.get("MP_CHECKED") == "1" else "libmp.so")
+LIB_PATH = os.path.join(_HERE, {"1": "libmp_checked.so", "lite": "libmp_checked_lite.so"}.get(
+    os.environ.get("MP_CHECKED", ""), "libmp.so"))
 
 MP_OK, MP_EINVAL, MP_ENOMEM, MP_ECUDA, MP_ETIMEOUT, MP_ENOTINIT = 0, -1, -2, -3, -4, -5
 MP_PRESET_BOX_ROOM, MP_PRESET_OUTDOOR = 0, 1
