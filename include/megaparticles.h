@@ -254,10 +254,13 @@ int mp_step_gicp(mp_ctx* ctx, const float* scan, int32_t n_scan, double cov_scal
 /* ---- Batched instances ------------------------------------------------
  * Many independent contexts (each with its own map, particles and
  * parameters; presets may differ) stepped together. mp_batch_create plans
- * one step of all instances as about forty grouped launches, each covering
+ * one step of all instances as about thirty grouped launches, each covering
  * the blocks of every instance (one kernel per phase: prediction, scan
- * Gaussians, LSH keys, each radix pass, merge, likelihood, solve, SVGD, each
- * posterior sweep ...), and captures the plan on cuda_stream into a CUDA
+ * Gaussians, LSH keys, each radix pass, merge, likelihood, solve, SVGD), and
+ * the posterior as one cooperative persistent launch over all instances
+ * (bounded grid barriers between its sub-steps; a barrier that gives up is
+ * reported as MP_ETIMEOUT by every instance), and captures the plan on
+ * cuda_stream into a CUDA
  * graph, twice (two pinned staging slots); mp_batch_step replays one. Per
  * instance the scan size is fixed (n_scan[i] points every step) and every step
  * runs all stages, the prediction included (identity odometry without noise
@@ -298,9 +301,15 @@ int mp_kernel_launches(mp_ctx* ctx, int64_t* count);
  * its first scan chunk, so that chunk's barrier never completes and the
  * bounded wait gives up; the kernel then records the error (reported as
  * MP_ETIMEOUT by the next mp_get_posterior) and returns. No copy is left in
- * flight. */
+ * flight. MP_DEBUG_STARVE_BARRIER: when non-zero, the first grid barrier of
+ * the posterior stage (one cooperative launch; in a batch, the first
+ * instance's knob and wait budget when mp_batch_create captures the step
+ * apply) waits for one CTA more than the grid has, so every
+ * CTA's bounded wait gives up; the kernel records the error for every
+ * instance it serves and returns. */
 #define MP_DEBUG_WAIT_BUDGET 1
 #define MP_DEBUG_STARVE_TX 2
+#define MP_DEBUG_STARVE_BARRIER 3
 int mp_debug_set(mp_ctx* ctx, int what, int64_t value);
 
 /* ---------------------------------------------------------------------------

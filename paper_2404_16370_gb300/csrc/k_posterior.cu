@@ -5,9 +5,21 @@
 //   w_ij = k_ij / sum_j k_ij fixed for the step (one thread per particle, FP64
 //   fused multiply-adds);
 //   normalise; best = argmax (smallest index on ties); log prior <- log p'.
-// Grid-wide max / sum / argmax are two-level (block partials, one final
-// block), so results do not depend on atomics' order.
+// Grid-wide max / sum / argmax are two-level (block partials, then one CTA
+// per instance), so results do not depend on atomics' order.
+//
+// The whole stage is one cooperative (persistent) kernel, k_post_phase: its
+// CTAs, all resident, take the particle blocks of one instance (a context's
+// own launch) or of every instance of a batch in turn, with a bounded grid
+// barrier (grid_sync) between the sub-steps: block maxima | per-instance max |
+// exp, block sums and sweep weights | per-instance sum and sweep 1 | sweeps
+// 2..iters | final block partials | per-instance sum and argmax | normalise.
+// A barrier that gives up records MP_ERR_WAIT for every instance and the
+// kernel returns. A context's launch and a batch's launch run the same code
+// per block and per instance, so they compute the same bits.
 #include "mp_internal.cuh"
+
+#include <algorithm>
 
 namespace {
 
@@ -47,234 +59,235 @@ struct PostArgs {
     int iters;
     const float4* poses;
     float4* best_pose;
+    int32_t* err;         // error bits (MP_ERR_WAIT when a grid barrier gives up)
 };
 
-struct PostLOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = PB, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
-        __shared__ double s[PB / 32];
-        int64_t i = (int64_t)bx * PB + threadIdx.x;
-        double l = -INFINITY;
-        if (i < A.n) {
-            l = A.logprior[i] + (double)A.loglik[i];
-            A.post[i] = l;
-        }
-        l = warp_max(l);
-        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = l;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double v = threadIdx.x < PB / 32 ? s[threadIdx.x] : -INFINITY;
-            v = warp_max(v);
-            if (threadIdx.x == 0) A.part[bx] = v;
-        }
+// block maxima of l = log prior + log likelihood (l kept in post)
+__device__ __forceinline__ void post_l(const PostArgs& A, unsigned bx) {
+    __shared__ double s[PB / 32];
+    int64_t i = (int64_t)bx * PB + threadIdx.x;
+    double l = -INFINITY;
+    if (i < A.n) {
+        l = A.logprior[i] + (double)A.loglik[i];
+        A.post[i] = l;
     }
-};
-
-struct ReduceMaxOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = 1024, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned, unsigned) {
-        __shared__ double s[32];
-        double v = -INFINITY;
-        for (int k = threadIdx.x; k < A.nb; k += 1024) v = fmax(v, A.part[k]);
+    l = warp_max(l);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < PB / 32 ? s[threadIdx.x] : -INFINITY;
         v = warp_max(v);
-        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            v = s[threadIdx.x];
-            v = warp_max(v);
-            if (threadIdx.x == 0) A.scalars[0] = v;
-        }
+        if (threadIdx.x == 0) A.part[bx] = v;
     }
-};
+}
 
-struct PostExpOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = PB, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
-        __shared__ double s[PB / 32];
-        int64_t i = (int64_t)bx * PB + threadIdx.x;
-        double v = 0.0;
-        if (i < A.n) {
-            v = exp(A.post[i] - A.scalars[0]);
-            A.post_init[i] = v;
-            A.post_tmp[i] = v;
-        }
-        v = warp_sum(v);
-        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double w = threadIdx.x < PB / 32 ? s[threadIdx.x] : 0.0;
-            w = warp_sum(w);
-            if (threadIdx.x == 0) A.part[bx] = w;
-        }
+// the instance's max l over its block maxima
+__device__ __forceinline__ void reduce_max(const PostArgs& A) {
+    __shared__ double s[PB / 32];
+    double v = -INFINITY;
+    for (int k = threadIdx.x; k < A.nb; k += PB) v = fmax(v, A.part[k]);
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < PB / 32 ? s[threadIdx.x] : -INFINITY;
+        v = warp_max(v);
+        if (threadIdx.x == 0) A.scalars[0] = v;
     }
-};
+}
 
-struct ReduceSumOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = 1024, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned, unsigned) {
-        __shared__ double s[32];
-        double v = 0.0;
-        for (int k = threadIdx.x; k < A.nb; k += 1024) v += A.part[k];
-        v = warp_sum(v);
-        if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            v = s[threadIdx.x];
-            v = warp_sum(v);
-            if (threadIdx.x == 0) A.scalars[1] = v;
-        }
+// p = exp(l - max l) into post_init and post_tmp (the sweeps' input); block sums
+__device__ __forceinline__ void post_exp(const PostArgs& A, unsigned bx) {
+    __shared__ double s[PB / 32];
+    int64_t i = (int64_t)bx * PB + threadIdx.x;
+    double v = 0.0;
+    if (i < A.n) {
+        v = exp(A.post[i] - A.scalars[0]);
+        A.post_init[i] = v;
+        A.post_tmp[i] = v;
     }
-};
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < PB / 32 ? s[threadIdx.x] : 0.0;
+        w = warp_sum(w);
+        if (threadIdx.x == 0) A.part[bx] = w;
+    }
+}
+
+// the instance's sum of exp(l - max l)
+__device__ __forceinline__ void reduce_sum(const PostArgs& A) {
+    __shared__ double s[PB / 32];
+    double v = 0.0;
+    for (int k = threadIdx.x; k < A.nb; k += PB) v += A.part[k];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < PB / 32 ? s[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) A.scalars[1] = v;
+    }
+}
 
 // Normalised weights w_ij = k_ij / sum_j k_ij (FP64) and 1 / sum_j k_ij,
 // fixed for the sweeps of a step: a sweep entry is then one FP64 fused
 // multiply-add (GB300's FP64 rate is low, so the division and the FP32 -> FP64
 // conversion are taken out of the ten sweeps). Weights and ids are written
-// slot-major ([l * n + i]) so that the sweeps' loads are coalesced.
-struct PostWeightsOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
-        const int64_t n = A.n;
-        const int K = A.K;
-        const int32_t* __restrict__ ids = A.ids;
-        const float* __restrict__ kk = A.kk;
-        double* __restrict__ w = A.w;
-        int64_t i = (int64_t)bx * THREADS + threadIdx.x;
-        if (i >= n) return;
-        double den = 0.0;
-        for (int l = 0; l < K; ++l)
-            if (ids[i * K + l] >= 0) den += (double)kk[i * K + l];
-        const double inv = den > 0.0 ? 1.0 / den : 0.0;
-        for (int l = 0; l < K; ++l) {
-            const int32_t j = ids[i * K + l];
-            w[l * n + i] = j >= 0 ? (double)kk[i * K + l] * inv : 0.0;
-            A.ids_t[l * n + i] = j;
+// slot-major ([l * n + i]) so that the sweeps' loads are coalesced. The lists
+// (row-major, K per particle) pass through shared memory in tiles of WT
+// particles: coalesced row loads, a per-particle sum in slot order, coalesced
+// slot-major stores.
+constexpr int WT = 32;
+__device__ __forceinline__ void post_weights(const PostArgs& A, unsigned bx) {
+    __shared__ int32_t s_id[WT * (MP_MAXK + 1)];   // row stride K + 1: conflict-free column reads
+    __shared__ float s_k[WT * (MP_MAXK + 1)];
+    __shared__ double s_inv[WT];
+    const int64_t n = A.n;
+    const int K = A.K, R = A.K + 1;
+    const int32_t* __restrict__ ids = A.ids;
+    const float* __restrict__ kk = A.kk;
+    for (int t = 0; t < PB / WT; ++t) {
+        const int64_t i0 = (int64_t)bx * PB + t * WT;
+        if (i0 >= n) break;   // block-uniform
+        const int np = n - i0 < WT ? (int)(n - i0) : WT;
+        const int E = np * K;
+        for (int e = threadIdx.x; e < E; e += PB) {
+            const int pl = e / K, l = e - pl * K;
+            s_id[pl * R + l] = ids[i0 * K + e];
+            s_k[pl * R + l] = kk[i0 * K + e];
         }
-        A.invden[i] = inv;
+        __syncthreads();
+        if (threadIdx.x < np) {
+            double den = 0.0;
+            for (int l = 0; l < K; ++l)
+                if (s_id[threadIdx.x * R + l] >= 0) den += (double)s_k[threadIdx.x * R + l];
+            const double inv = den > 0.0 ? 1.0 / den : 0.0;
+            s_inv[threadIdx.x] = inv;
+            A.invden[i0 + threadIdx.x] = inv;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < WT * K; e += PB) {
+            const int l = e / WT, pl = e - l * WT;
+            if (pl < np) {
+                const int32_t j = s_id[pl * R + l];
+                A.w[l * n + i0 + pl] = j >= 0 ? (double)s_k[pl * R + l] * s_inv[pl] : 0.0;
+                A.ids_t[l * n + i0 + pl] = j;
+            }
+        }
+        __syncthreads();
     }
-};
+}
 
-// Jacobi sweep `it` (the block map's y index) of Eq. 11, one thread per
-// particle: p'_i = sum_j w_ij p_j with FP64 fused multiply-adds over the list
-// in slot order (slot-major ids and weights: a warp's loads of one slot are
-// contiguous); a particle whose kernel weights sum to zero keeps its value.
+// Jacobi sweep `it` of Eq. 11, one thread per particle: p'_i = sum_j w_ij p_j
+// with FP64 fused multiply-adds over the list in slot order (slot-major ids
+// and weights: a warp's loads of one slot are contiguous); a particle whose
+// kernel weights sum to zero keeps its value. Ids, weights and p were written
+// earlier in the same launch by other CTAs: plain loads (not the read-only
+// path), ordered by the grid barrier's fences.
 template <int KT>
-struct PostSweepOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned it) {
-        const double* __restrict__ pin = (it & 1) ? A.post : A.post_tmp;
-        double* __restrict__ pout = (it & 1) ? A.post_tmp : A.post;
-        const int64_t n = A.n;
-        const int32_t* __restrict__ ids = A.ids_t;
-        const double* __restrict__ w = A.w;
-        const int K = KT > 0 ? KT : A.K;   // compile-time list length for the common sizes
-        int64_t i = (int64_t)bx * THREADS + threadIdx.x;
-        if (i >= n) return;
+__device__ __forceinline__ void post_sweep(const PostArgs& A, unsigned bx, int it) {
+    const double* pin = (it & 1) ? A.post : A.post_tmp;
+    double* pout = (it & 1) ? A.post_tmp : A.post;
+    const int64_t n = A.n;
+    const int32_t* ids = A.ids_t;
+    const double* w = A.w;
+    const int K = KT > 0 ? KT : A.K;   // compile-time list length for the common sizes
+    int64_t i = (int64_t)bx * PB + threadIdx.x;
+    if (i < n) {
         double num = 0.0;
 #pragma unroll(KT > 0 ? KT : 1)
         for (int l = 0; l < K; ++l) {
-            const int j = __ldg(ids + l * n + i);
-            if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(__ldg(w + l * n + i), __ldg(pin + j), num);
+            const int j = ids[l * n + i];
+            if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(w[l * n + i], pin[j], num);
         }
         pout[i] = A.invden[i] > 0.0 ? num : pin[i];
     }
-};
+}
 
 // the smoothed posterior after the sweeps
 __device__ __forceinline__ const double* post_smoothed(const PostArgs& A) { return (A.iters & 1) ? A.post : A.post_tmp; }
 
-struct FinalPartOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = PB, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
-        __shared__ double ss[PB / 32], sm[PB / 32];
-        __shared__ int64_t si[PB / 32];
-        const double* __restrict__ p = post_smoothed(A);
-        int64_t i = (int64_t)bx * PB + threadIdx.x;
-        double v = i < A.n ? p[i] : 0.0;
-        double m = i < A.n ? v : -INFINITY;
-        int64_t mi = i < A.n ? i : INT64_MAX;
-        double s = warp_sum(v);
+// block partials of the smoothed posterior: sum, max and its index
+__device__ __forceinline__ void final_part(const PostArgs& A, unsigned bx) {
+    __shared__ double ss[PB / 32], sm[PB / 32];
+    __shared__ int64_t si[PB / 32];
+    const double* p = post_smoothed(A);
+    int64_t i = (int64_t)bx * PB + threadIdx.x;
+    double v = i < A.n ? p[i] : 0.0;
+    double m = i < A.n ? v : -INFINITY;
+    int64_t mi = i < A.n ? i : INT64_MAX;
+    double s = warp_sum(v);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double m2 = __shfl_xor_sync(0xffffffffu, m, o);
-            int64_t i2 = __shfl_xor_sync(0xffffffffu, mi, o);
-            argmax_merge(m, mi, m2, i2);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            ss[threadIdx.x >> 5] = s;
-            sm[threadIdx.x >> 5] = m;
-            si[threadIdx.x >> 5] = mi;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double S = 0.0, M = -INFINITY;
-            int64_t I = INT64_MAX;
-            for (int k = 0; k < PB / 32; ++k) {
-                S += ss[k];
-                argmax_merge(M, I, sm[k], si[k]);
-            }
-            A.part[bx] = S;
-            A.part2[bx] = M;
-            A.part_idx[bx] = I;
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        double m2 = __shfl_xor_sync(0xffffffffu, m, o);
+        int64_t i2 = __shfl_xor_sync(0xffffffffu, mi, o);
+        argmax_merge(m, mi, m2, i2);
     }
-};
-
-struct FinalReduceOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = 1024, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned, unsigned) {
-        __shared__ double ss[32], sm[32];
-        __shared__ int64_t si[32];
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sm[threadIdx.x >> 5] = m;
+        si[threadIdx.x >> 5] = mi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double S = 0.0, M = -INFINITY;
         int64_t I = INT64_MAX;
-        for (int k = threadIdx.x; k < A.nb; k += 1024) {
-            S += A.part[k];
-            argmax_merge(M, I, A.part2[k], A.part_idx[k]);
+        for (int k = 0; k < PB / 32; ++k) {
+            S += ss[k];
+            argmax_merge(M, I, sm[k], si[k]);
         }
-        S = warp_sum(S);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double m2 = __shfl_xor_sync(0xffffffffu, M, o);
-            int64_t i2 = __shfl_xor_sync(0xffffffffu, I, o);
-            argmax_merge(M, I, m2, i2);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            ss[threadIdx.x >> 5] = S;
-            sm[threadIdx.x >> 5] = M;
-            si[threadIdx.x >> 5] = I;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double S2 = 0.0, M2 = -INFINITY;
-            int64_t I2 = INT64_MAX;
-            for (int k = 0; k < 32; ++k) {
-                S2 += ss[k];
-                argmax_merge(M2, I2, sm[k], si[k]);
-            }
-            A.scalars[2] = S2;
-            A.scalars[3] = M2 / S2;
-            *A.best_idx = I2;
-        }
+        A.part[bx] = S;
+        A.part2[bx] = M;
+        A.part_idx[bx] = I;
     }
-};
+}
 
-// normalise out of post_tmp (after an odd number of sweeps the smoothed values
-// are copied there first), store the log prior, copy the best pose
-struct NormaliseOp {
-    using Args = PostArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const PostArgs& A, unsigned bx, unsigned) {
-        int64_t i = (int64_t)bx * THREADS + threadIdx.x;
-        if (i >= A.n) return;
-        double v = A.post_tmp[i] / A.scalars[2];
+// the instance's sum of the smoothed posterior, its best value and index
+__device__ __forceinline__ void final_reduce(const PostArgs& A) {
+    __shared__ double ss[PB / 32], sm[PB / 32];
+    __shared__ int64_t si[PB / 32];
+    double S = 0.0, M = -INFINITY;
+    int64_t I = INT64_MAX;
+    for (int k = threadIdx.x; k < A.nb; k += PB) {
+        S += A.part[k];
+        argmax_merge(M, I, A.part2[k], A.part_idx[k]);
+    }
+    S = warp_sum(S);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double m2 = __shfl_xor_sync(0xffffffffu, M, o);
+        int64_t i2 = __shfl_xor_sync(0xffffffffu, I, o);
+        argmax_merge(M, I, m2, i2);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = S;
+        sm[threadIdx.x >> 5] = M;
+        si[threadIdx.x >> 5] = I;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S2 = 0.0, M2 = -INFINITY;
+        int64_t I2 = INT64_MAX;
+        for (int k = 0; k < PB / 32; ++k) {
+            S2 += ss[k];
+            argmax_merge(M2, I2, sm[k], si[k]);
+        }
+        A.scalars[2] = S2;
+        A.scalars[3] = M2 / S2;
+        *A.best_idx = I2;
+    }
+}
+
+// normalise (post_tmp keeps the smoothed values), store the log prior, copy
+// the best pose
+__device__ __forceinline__ void normalise(const PostArgs& A, unsigned bx) {
+    int64_t i = (int64_t)bx * PB + threadIdx.x;
+    if (i < A.n) {
+        const double sm = post_smoothed(A)[i];
+        if (A.iters & 1) A.post_tmp[i] = sm;
+        const double v = sm / A.scalars[2];
         A.post[i] = v;
         A.logprior[i] = log(v);
         if (i == *A.best_idx) {
@@ -282,11 +295,92 @@ struct NormaliseOp {
             A.best_pose[1] = A.poses[2 * i + 1];
         }
     }
+}
+
+// The launch's argument: one instance (tab null; a context's own launch) or a
+// table of instances with the list of their particle blocks (a batch).
+struct PostPhase {
+    PostArgs one;
+    const PostArgs* tab;
+    const GBlk* blocks;   // (inst, bx) of every particle block; null: blocks 0..one.nb-1 of `one`
+    int n_blocks, n_inst, max_iters, starve;
+    GridBar* bar;
+    long long budget;
 };
 
-template <typename Op>
-__global__ void __launch_bounds__(Op::THREADS) k_post(const PostArgs A, int y) {
-    Op::run(A, blockIdx.x, y);
+__device__ __forceinline__ const PostArgs& phase_args(const PostPhase& P, int inst) {
+    return P.tab ? P.tab[inst] : P.one;
+}
+__device__ __forceinline__ const PostArgs& phase_item(const PostPhase& P, int w, unsigned& bx) {
+    if (!P.blocks) {
+        bx = (unsigned)w;
+        return P.one;
+    }
+    const GBlk g = P.blocks[w];
+    bx = (unsigned)g.bx;
+    return P.tab[g.inst];
+}
+
+__global__ void __launch_bounds__(PB, 8) k_post_phase(const __grid_constant__ PostPhase P) {
+    // the test knob: the first barrier waits for one CTA more than the grid
+    unsigned expect = gridDim.x + (P.starve ? 1u : 0u);
+    auto sync = [&]() {
+        const bool ok = grid_sync(P.bar, expect, P.budget);
+        expect = gridDim.x;
+        if (!ok && threadIdx.x == 0)
+            for (int k = 0; k < P.n_inst; ++k) atomicOr(phase_args(P, k).err, MP_ERR_WAIT);
+        return ok;
+    };
+    unsigned bx;
+    for (int w = blockIdx.x; w < P.n_blocks; w += gridDim.x) {
+        post_l(phase_item(P, w, bx), bx);
+        __syncthreads();
+    }
+    if (!sync()) return;
+    for (int k = blockIdx.x; k < P.n_inst; k += gridDim.x) {
+        reduce_max(phase_args(P, k));
+        __syncthreads();
+    }
+    if (!sync()) return;
+    for (int w = blockIdx.x; w < P.n_blocks; w += gridDim.x) {
+        const PostArgs& A = phase_item(P, w, bx);
+        post_exp(A, bx);
+        post_weights(A, bx);
+        __syncthreads();
+    }
+    if (!sync()) return;
+    // the sums read the block partials of post_exp; the first sweep reads
+    // post_tmp and the weights: both run after the same barrier
+    for (int k = blockIdx.x; k < P.n_inst; k += gridDim.x) {
+        reduce_sum(phase_args(P, k));
+        __syncthreads();
+    }
+    for (int it = 0; it < P.max_iters; ++it) {
+        for (int w = blockIdx.x; w < P.n_blocks; w += gridDim.x) {
+            const PostArgs& A = phase_item(P, w, bx);
+            if (it < A.iters) {
+                if (A.K == 32) post_sweep<32>(A, bx, it);
+                else if (A.K == 16) post_sweep<16>(A, bx, it);
+                else post_sweep<0>(A, bx, it);
+            }
+        }
+        if (!sync()) return;
+    }
+    if (P.max_iters == 0 && !sync()) return;   // the sums before final_part rewrites the partials
+    for (int w = blockIdx.x; w < P.n_blocks; w += gridDim.x) {
+        final_part(phase_item(P, w, bx), bx);
+        __syncthreads();
+    }
+    if (!sync()) return;
+    for (int k = blockIdx.x; k < P.n_inst; k += gridDim.x) {
+        final_reduce(phase_args(P, k));
+        __syncthreads();
+    }
+    if (!sync()) return;
+    for (int w = blockIdx.x; w < P.n_blocks; w += gridDim.x) {
+        const PostArgs& A = phase_item(P, w, bx);
+        normalise(A, bx);
+    }
 }
 
 PostArgs post_args(mp_ctx* c, int cur) {
@@ -312,85 +406,78 @@ PostArgs post_args(mp_ctx* c, int cur) {
     A.iters = c->p.post_iters;
     A.poses = c->poses[c->cur];
     A.best_pose = c->best_pose;
+    A.err = c->dev_error;
     return A;
 }
 
-template <int KT>
-void sweeps(mp_ctx* c, const PostArgs& A) {
-    for (int it = 0; it < A.iters; ++it) k_post<PostSweepOp<KT>><<<grid_for(A.n, 256), 256, 0, c->stream>>>(A, it);
+// Resident CTAs of k_post_phase on the current device: the grid of a
+// cooperative launch may not exceed it.
+unsigned post_capacity() {
+    static int cap[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cap[dev]) {
+        int sms = 0, per = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_post_phase, PB, 0) != cudaSuccess)
+            return 0;
+        cap[dev] = sms * per;
+    }
+    return (unsigned)cap[dev];
 }
+
+long long post_budget(const mp_ctx* c) { return c->wait_budget > 0 ? c->wait_budget : MP_WAIT_BUDGET; }
 
 }  // namespace
 
 int mp_launch_posterior(mp_ctx* c) {
-    const PostArgs A = post_args(c, c->nbr_cur);
-    const unsigned nb = (unsigned)A.nb;
-    k_post<PostLOp><<<nb, PB, 0, c->stream>>>(A, 0);
-    MP_LAUNCHED(c);
-    k_post<ReduceMaxOp><<<1, 1024, 0, c->stream>>>(A, 0);
-    MP_LAUNCHED(c);
-    k_post<PostExpOp><<<nb, PB, 0, c->stream>>>(A, 0);
-    MP_LAUNCHED(c);
-    k_post<ReduceSumOp><<<1, 1024, 0, c->stream>>>(A, 0);
-    MP_LAUNCHED(c);
-    k_post<PostWeightsOp><<<grid_for(A.n, 256), 256, 0, c->stream>>>(A, 0);
-    MP_LAUNCHED(c);
-    if (A.K == 32) sweeps<32>(c, A);
-    else if (A.K == 16) sweeps<16>(c, A);
-    else sweeps<0>(c, A);
-    c->launches += A.iters - 1;
-    MP_LAUNCHED(c);
-    k_post<FinalPartOp><<<nb, PB, 0, c->stream>>>(A, 0);
-    MP_LAUNCHED(c);
-    k_post<FinalReduceOp><<<1, 1024, 0, c->stream>>>(A, 0);
-    MP_LAUNCHED(c);
-    if (A.iters & 1)
-        MP_CUDA(c, cudaMemcpyAsync(c->post_tmp, c->post, sizeof(double) * (size_t)A.n, cudaMemcpyDeviceToDevice,
-                                   c->stream));
-    k_post<NormaliseOp><<<grid_for(A.n, 256), 256, 0, c->stream>>>(A, 0);
+    PostPhase P = {};
+    P.one = post_args(c, c->nbr_cur);
+    P.n_blocks = P.one.nb;
+    P.n_inst = 1;
+    P.max_iters = P.one.iters;
+    P.starve = c->starve_bar;
+    P.bar = c->post_bar;
+    P.budget = post_budget(c);
+    const unsigned cap = post_capacity();
+    if (!cap) return mp_fail(c, MP_ECUDA, "posterior: no resident CTAs for the cooperative launch");
+    MP_CUDA(c, cudaMemsetAsync(c->post_bar, 0, sizeof(GridBar), c->stream));
+    MP_CUDA(c, launch_coop((const void*)k_post_phase, std::min<unsigned>((unsigned)P.n_blocks, cap), PB, &P,
+                           c->stream));
     MP_LAUNCHED(c);
     return MP_OK;
 }
 
-// Grouped posterior: the same launches over all instances; the sweeps of
-// instances with K = 32, 16 and other list lengths go in separate launches.
+// Batched posterior: one cooperative launch over the particle blocks of all
+// instances (its barrier zeroed first).
 int mp_plan_posterior(mp_group* G, int p, std::vector<GOp>& plan) {
     std::vector<PostArgs> tab;
-    std::vector<int64_t> bpb, b1;
-    std::vector<int> odd;
+    std::vector<int64_t> bpb;
     int max_iters = 0;
     for (int i = 0; i < G->size(); ++i) {
         mp_ctx* c = G->ctx[i];
         tab.push_back(post_args(c, c->nbr_cur ^ p ^ 1));   // the list the merge of this step wrote
         bpb.push_back(tab.back().nb);
-        b1.push_back(1);
-        max_iters = tab.back().iters > max_iters ? tab.back().iters : max_iters;
-        if (tab.back().iters & 1) odd.push_back(i);
+        max_iters = std::max(max_iters, tab.back().iters);
     }
+    const GridBar zero = {};
+    GridBar* bar = static_cast<GridBar*>(const_cast<void*>(G->upload(&zero, sizeof(zero))));
     const PostArgs* t = G->upload(tab);
-    unsigned npb = 0, n1 = 0;
-    const GBlk* mpb = G->block_map(bpb, &npb);
-    const GBlk* m1 = G->block_map(b1, &n1);
-    plan_kernel<PostLOp>(plan, t, mpb, npb);
-    plan_kernel<ReduceMaxOp>(plan, t, m1, n1);
-    plan_kernel<PostExpOp>(plan, t, mpb, npb);
-    plan_kernel<ReduceSumOp>(plan, t, m1, n1);
-    plan_kernel<PostWeightsOp>(plan, t, mpb, npb);   // PB = 256 threads: the same blocks
-    for (int it = 0; it < max_iters; ++it) {
-        std::vector<GBlk> m32, m16, m0;
-        for (int i = 0; i < G->size(); ++i) {
-            if (tab[i].iters <= it) continue;
-            std::vector<GBlk>& m = tab[i].K == 32 ? m32 : tab[i].K == 16 ? m16 : m0;
-            for (int64_t b = 0; b < bpb[i]; ++b) m.push_back(GBlk{i, (int32_t)b, it, 0});
-        }
-        if (!m32.empty()) plan_kernel<PostSweepOp<32>>(plan, t, G->upload(m32), (unsigned)m32.size());
-        if (!m16.empty()) plan_kernel<PostSweepOp<16>>(plan, t, G->upload(m16), (unsigned)m16.size());
-        if (!m0.empty()) plan_kernel<PostSweepOp<0>>(plan, t, G->upload(m0), (unsigned)m0.size());
-    }
-    plan_kernel<FinalPartOp>(plan, t, mpb, npb);
-    plan_kernel<FinalReduceOp>(plan, t, m1, n1);
-    for (int i : odd)
-        plan_copy(plan, G->ctx[i]->post_tmp, G->ctx[i]->post, sizeof(double) * (size_t)G->ctx[i]->n);
-    plan_kernel<NormaliseOp>(plan, t, mpb, npb);
-    return G->err;
+    unsigned nblk = 0;
+    const GBlk* map = G->block_map(bpb, &nblk);
+    const unsigned cap = post_capacity();
+    if (G->err) return G->err;
+    if (!cap) return MP_ECUDA;
+    PostPhase P = {};
+    P.tab = t;
+    P.blocks = map;
+    P.n_blocks = (int)nblk;
+    P.n_inst = G->size();
+    P.max_iters = max_iters;
+    P.starve = G->ctx[0]->starve_bar;
+    P.bar = bar;
+    P.budget = post_budget(G->ctx[0]);
+    plan_memset(plan, bar, sizeof(GridBar));
+    plan_coop(plan, (const void*)k_post_phase, std::min(nblk, cap), PB, P);
+    return MP_OK;
 }

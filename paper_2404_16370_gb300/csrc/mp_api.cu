@@ -207,7 +207,7 @@ void destroy(mp_ctx* c) {
     dfree(c->nnf);
     dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pair); dfree(c->scan_h2); dfree(c->scan_tmp4);
     dfree(c->scan_nvalid);
-    dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->pairs);
+    dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->post_bar); dfree(c->pairs);
     dfree(c->step_dev);
     mp_gicp_free(c);
     if (c->step_host) cudaFreeHost(c->step_host);
@@ -399,6 +399,7 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
         if ((rc = dalloc(c, &c->best_idx, 1))) break;
         if ((rc = dalloc(c, &c->best_pose, 2))) break;
         if ((rc = dalloc(c, &c->dev_error, 1))) break;
+        if ((rc = dalloc(c, &c->post_bar, 1))) break;
         if ((rc = dalloc(c, &c->step_dev, 1))) break;
         cudaError_t e = cudaHostAlloc((void**)&c->step_host, 2 * sizeof(StepDev), cudaHostAllocDefault);
         if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "cudaHostAlloc"); break; }
@@ -824,6 +825,7 @@ int mp_debug_set(mp_ctx* c, int what, int64_t value) {
     switch (what) {
         case MP_DEBUG_WAIT_BUDGET: c->wait_budget = value > 0 ? (long long)value : 0; return MP_OK;
         case MP_DEBUG_STARVE_TX: c->starve_tx = value ? 1 : 0; return MP_OK;
+        case MP_DEBUG_STARVE_BARRIER: c->starve_bar = value ? 1 : 0; return MP_OK;
     }
     return mp_fail(c, MP_EINVAL, "unknown debug knob %d", what);
 }

@@ -1,8 +1,9 @@
 // Batched stepping of independent filter instances (contexts). Every phase of
 // a step is one grouped launch over the blocks of all instances (k_group<Op>:
 // a block map names the instance and block each CTA runs, a table holds each
-// instance's arguments), so a batch step is about forty launches whatever the
-// number of instances, all on the batch's stream. The launches are captured
+// instance's arguments; the posterior is one cooperative persistent launch),
+// so a batch step is about thirty launches whatever the number of instances,
+// all on the batch's stream. The launches are captured
 // once into a CUDA graph per pinned staging slot and every batch step replays
 // one; the host fills the other slot (scans, odometry, LSH draw, step
 // counter) while a step runs. Before the capture, the likelihood's scan split
@@ -109,6 +110,8 @@ int run_plan(const std::vector<GOp>& plan, cudaStream_t s) {
         if (o.kind == GOp::KERNEL) {
             void* args[2] = {(void*)&o.tab, (void*)&o.map};
             B_CUDA(cudaLaunchKernel(o.func, dim3(o.grid), dim3(o.block), args, 0, s));
+        } else if (o.kind == GOp::COOP) {
+            B_CUDA(launch_coop(o.func, o.grid, o.block, (void*)o.arg, s));
         } else if (o.kind == GOp::MEMSET) {
             B_CUDA(cudaMemsetAsync(o.dst, 0, o.bytes, s));
         } else {

@@ -142,6 +142,8 @@ struct mp_ctx {
     uint4* scan_h2;          // 2 per valid point: the scan as 16-bit broadcast pairs (precision != FP32)
     long long wait_budget;   // cycles; 0 = MP_WAIT_BUDGET
     int starve_tx;
+    int starve_bar;          // the posterior's first grid barrier waits for one CTA more than the grid
+    struct GridBar* post_bar;   // the persistent posterior's grid barrier (zeroed before each launch)
 };
 
 // ---------------------------------------------------------------------------
@@ -388,6 +390,56 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 #define MP_WAIT_BUDGET (4000000000LL)   // ~2 s at 2 GHz
 #define MP_ERR_WAIT 1
 
+// Grid-wide barrier of a cooperative (persistent) launch, whose CTAs are all
+// resident at once. Thread 0 of each CTA reads the generation, arrives on the
+// counter and, unless it is the last to arrive, spins until the generation
+// moves on; the last arrival resets the counter and advances the generation.
+// The spin is bounded by `budget` SM cycles and also ends when another CTA has
+// given up (abort); grid_sync then returns false and the caller records the
+// error and returns. Zero the barrier before every launch.
+struct GridBar {
+    unsigned int count, gen;
+    int abort, pad;
+};
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned expected, long long budget) {
+    __shared__ int ok_s;
+    __syncthreads();   // the CTA's share of the sub-step is done
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire_u32(&gb->gen);
+        __threadfence();   // this CTA's writes before its arrival
+        if (atomicAdd(&gb->count, 1u) + 1u == expected) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_u32(&gb->gen) == g) {
+                if (ld_relaxed_s32(&gb->abort) != 0 || clock64() - t0 > budget) {
+                    ok = 0;
+                    atomicExch(&gb->abort, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();   // the other CTAs' writes after the barrier
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
 // ---------------------------------------------------------------------------
 // host-side helpers
 // ---------------------------------------------------------------------------
@@ -503,10 +555,12 @@ __global__ void __launch_bounds__(Op::THREADS, Op::MINB) k_group(const typename 
 }
 
 // One operation of a batch step's plan: a grouped kernel (func = k_group<Op>,
-// arguments tab and map, grid blocks of block threads), a device memset or a
-// device-to-device copy. The plan is captured into a CUDA graph.
+// arguments tab and map, grid blocks of block threads), a cooperative
+// persistent kernel (func with one by-value argument of arg_bytes in arg), a
+// device memset or a device-to-device copy. The plan is captured into a CUDA
+// graph.
 struct GOp {
-    enum Kind { KERNEL, MEMSET, COPY } kind;
+    enum Kind { KERNEL, COOP, MEMSET, COPY } kind;
     const void* func;
     unsigned grid, block;
     const void* tab;
@@ -514,6 +568,8 @@ struct GOp {
     void* dst;
     const void* src;
     size_t bytes;
+    size_t arg_bytes;
+    alignas(16) unsigned char arg[512];
 };
 
 // The instances of a batch as the planners see them: contexts, the device
@@ -554,6 +610,35 @@ inline void plan_kernel(std::vector<GOp>& plan, const typename Op::Args* tab, co
     o.tab = tab;
     o.map = map;
     plan.push_back(o);
+}
+// Appends a cooperative launch of func(arg) (grid <= the resident CTAs).
+template <typename T>
+inline void plan_coop(std::vector<GOp>& plan, const void* func, unsigned grid, unsigned block, const T& arg) {
+    static_assert(sizeof(T) <= sizeof(GOp::arg), "argument too large");
+    if (grid == 0) return;
+    GOp o{};
+    o.kind = GOp::COOP;
+    o.func = func;
+    o.grid = grid;
+    o.block = block;
+    o.arg_bytes = sizeof(T);
+    memcpy(o.arg, &arg, sizeof(T));
+    plan.push_back(o);
+}
+// A cooperative launch on a stream (also inside a stream capture).
+inline cudaError_t launch_coop(const void* func, unsigned grid, unsigned block, void* arg, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void* args[1] = {arg};
+    return cudaLaunchKernelExC(&cfg, func, args);
 }
 inline void plan_memset(std::vector<GOp>& plan, void* dst, size_t bytes) {
     GOp o{};

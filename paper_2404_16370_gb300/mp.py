@@ -267,7 +267,7 @@ def mp_stage_times(ctx):
     return dict(zip(STAGE_NAMES, ms.tolist())), dict(zip(STAGE_NAMES, runs.tolist())), int(pairs.value)
 
 
-MP_DEBUG_WAIT_BUDGET, MP_DEBUG_STARVE_TX = 1, 2
+MP_DEBUG_WAIT_BUDGET, MP_DEBUG_STARVE_TX, MP_DEBUG_STARVE_BARRIER = 1, 2, 3
 
 
 def mp_debug_set(ctx, what, value):

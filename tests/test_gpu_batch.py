@@ -1,7 +1,8 @@
 """Batched instances (mp_batch_*) and the likelihood's scan split: the split
 sums equal the unsplit ones up to summation order; a batch step equals the
 same step taken instance by instance with mp_step (bit for bit with split 1);
-the autotuned batch runs with valid splits and posteriors."""
+the autotuned batch runs with valid splits and posteriors; a starved grid
+barrier in the batched posterior is reported for every instance."""
 import numpy as np
 import pytest
 
@@ -178,6 +179,30 @@ def test_batch_refuses_outside_steps(torch):
         mp.mp_step(A[0], data[0][0])
         with pytest.raises(mp.MPError):
             mp.mp_batch_step(batch, [d[0] for d in data])
+    finally:
+        mp.mp_batch_destroy(batch)
+        for c in A:
+            mp.mp_destroy(c)
+        mp.mp_stream_destroy(st)
+
+
+def test_batch_grid_barrier_timeout_reported_for_every_instance(torch):
+    """The batched posterior is one cooperative launch over all instances.
+    With the first instance's barrier knob set when the batch is created, its
+    first grid barrier waits for one CTA more than the grid: every CTA gives
+    up, and every instance reports MP_ETIMEOUT."""
+    from paper_2404_16370_gb300 import mp
+    st = mp.mp_stream_create()
+    A, data = _instances(st, SPECS)
+    mp.mp_debug_set(A[0], mp.MP_DEBUG_WAIT_BUDGET, 2_000_000)
+    mp.mp_debug_set(A[0], mp.MP_DEBUG_STARVE_BARRIER, 1)
+    batch = mp.mp_batch_create(A, [len(d[0]) for d in data], st)
+    try:
+        mp.mp_batch_step(batch, [d[0] for d in data])
+        for ctx in A:
+            with pytest.raises(mp.MPError) as e:
+                mp.mp_get_posterior(ctx)
+            assert e.value.code == mp.MP_ETIMEOUT
     finally:
         mp.mp_batch_destroy(batch)
         for c in A:

@@ -2,8 +2,9 @@
 the C ABI: a single particle, ragged sizes (particles and scan points not
 multiples of the block/chunk sizes), a scan whose points are all invalid, the
 largest scan, a blackout step (empty scan), device-pointer inputs on a caller
-stream, invalid arguments, and a bounded device wait made to give up (a test
-knob withholds 16 announced bytes; nothing faults or hangs)."""
+stream, invalid arguments, and bounded device waits made to give up (test
+knobs withhold 16 announced bytes of a bulk copy, or make a grid barrier wait
+for one CTA more than the grid has; nothing faults or hangs)."""
 import numpy as np
 import pytest
 
@@ -208,3 +209,61 @@ def test_bounded_wait_gives_up_and_context_recovers(room, oracle):
     ref = oracle.likelihood(room["om"], room["w"].particles[:n], sc, sn, sv, P, amb_tol=1e-4)
     msg = check_sums(gn, ref)
     assert not msg, msg
+
+
+def test_ragged_posterior_odd_sweeps(room, oracle):
+    """The posterior stage (one cooperative launch, grid barriers between its
+    sub-steps) on a ragged particle count with an odd number of sweeps,
+    against the oracle's Eq. 11."""
+    from paper_2404_16370_gb300 import mp
+    n, K = 4099, 16
+    rng = np.random.default_rng(31)
+    ids = rng.integers(0, n, (n, K)).astype(np.int32)
+    ids[rng.random((n, K)) < 0.3] = -1
+    ids[:, 0] = np.arange(n)
+    kk = rng.uniform(0.05, 1.0, (n, K)).astype(np.float32)
+    kk[:, 0] = 1
+    loglik = (-rng.uniform(0, 80, n)).astype(np.float32)
+    logprior = -rng.uniform(0, 5, n)
+    ctx = make_ctx(mp, room, n, post_iters=7)
+    try:
+        mp.mp_set_buffer(ctx, mp.MP_BUF_NBR_IDS, ids)
+        mp.mp_set_buffer(ctx, mp.MP_BUF_NBR_K, kk)
+        mp.mp_set_buffer(ctx, mp.MP_BUF_LOGLIK, loglik)
+        mp.mp_set_buffer(ctx, mp.MP_BUF_LOG_PRIOR, logprior)
+        mp.mp_run_stages(ctx, mp.MP_STAGE_POSTERIOR)
+        post = mp.mp_get_buffer(ctx, mp.MP_BUF_POST)
+        best, best_p = mp.mp_get_posterior(ctx)
+    finally:
+        mp.mp_destroy(ctx)
+    _, p_ref, b_ref = oracle.posterior(logprior, loglik.astype(np.float64), ids, kk.astype(np.float64), 7)
+    assert np.allclose(post, p_ref, rtol=1e-10, atol=1e-300)
+    assert abs(post.sum() - 1) < 1e-12
+    assert np.array_equal(best, room["w"].particles[b_ref]) and abs(best_p - p_ref[b_ref]) < 1e-12
+
+
+def test_grid_barrier_gives_up_and_context_recovers(room):
+    """A starved grid barrier (the posterior's first barrier waits for one CTA
+    more than the grid): every CTA's bounded wait gives up after ~1 ms of SM
+    clock, the kernel records the error and returns, and the host sees
+    MP_ETIMEOUT; with the knob cleared the next step is normal."""
+    from paper_2404_16370_gb300 import mp
+    n = 4096
+    sc = room["w"].scans[0]
+    ctx = make_ctx(mp, room, n)
+    try:
+        mp.mp_debug_set(ctx, mp.MP_DEBUG_WAIT_BUDGET, 2_000_000)
+        mp.mp_debug_set(ctx, mp.MP_DEBUG_STARVE_BARRIER, 1)
+        mp.mp_step(ctx, sc)
+        with pytest.raises(mp.MPError) as e:
+            mp.mp_get_posterior(ctx)
+        assert e.value.code == mp.MP_ETIMEOUT
+        mp.mp_debug_set(ctx, mp.MP_DEBUG_STARVE_BARRIER, 0)
+        mp.mp_debug_set(ctx, mp.MP_DEBUG_WAIT_BUDGET, 0)
+        mp.mp_set_buffer(ctx, mp.MP_BUF_LOG_PRIOR, np.zeros(n))
+        mp.mp_step(ctx, sc)
+        best, best_p = mp.mp_get_posterior(ctx)   # error flag was cleared: no exception
+        post = mp.mp_get_buffer(ctx, mp.MP_BUF_POST)
+    finally:
+        mp.mp_destroy(ctx)
+    assert np.isfinite(post).all() and abs(post.sum() - 1) < 1e-12 and 0 < best_p <= 1
