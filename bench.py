@@ -84,8 +84,9 @@ def stage_bounds_ms(n, K, pairs_per_step, hbm_gbs):
         "solve": (n * (29 * 4 + 32) / bw, n * 250 / f64),
         # list ids, k, d (K x 32 B) + K psi gathers (32 B) + pose in/out + phi
         "svgd": (n * (K * 64 + 96) / bw, n * K * 30 / f32),
-        # 10 sweeps x K x (id 4 + k 4 + p 8) + normalisation passes (5 x 8 B)
-        "posterior": (n * (10 * (K * 16 + 8) + 40) / bw, 0.0),
+        # 10 sweeps x K x (id 4 + k 4 + p 8) + normalisation passes (5 x 8 B);
+        # FP64: 10 sweeps x K FMAs, the weights (K adds, K multiplies), exp and log
+        "posterior": (n * (10 * (K * 16 + 8) + 40) / bw, n * (20 * K + 2 * K + 70) / f64),
     }
     out = {k: 1e3 * max(v) for k, v in b.items()}
     out["likelihood"] = 1e3 * max(pairs_per_step * LK_SECTOR_BYTES_PER_PAIR / bw,
