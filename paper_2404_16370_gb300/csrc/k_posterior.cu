@@ -142,7 +142,7 @@ __device__ __forceinline__ void reduce_sum(const PostArgs& A) {
 constexpr int WT = 32;
 __device__ __forceinline__ void post_weights(const PostArgs& A, unsigned bx) {
     __shared__ int32_t s_id[WT * (MP_MAXK + 1)];   // row stride K + 1: conflict-free column reads
-    __shared__ float s_k[WT * (MP_MAXK + 1)];
+    __shared__ double s_k[WT * (MP_MAXK + 1)];     // k_ij converted to FP64 once
     __shared__ double s_inv[WT];
     const int64_t n = A.n;
     const int K = A.K, R = A.K + 1;
@@ -156,13 +156,13 @@ __device__ __forceinline__ void post_weights(const PostArgs& A, unsigned bx) {
         for (int e = threadIdx.x; e < E; e += PB) {
             const int pl = e / K, l = e - pl * K;
             s_id[pl * R + l] = ids[i0 * K + e];
-            s_k[pl * R + l] = kk[i0 * K + e];
+            s_k[pl * R + l] = (double)kk[i0 * K + e];
         }
         __syncthreads();
         if (threadIdx.x < np) {
             double den = 0.0;
             for (int l = 0; l < K; ++l)
-                if (s_id[threadIdx.x * R + l] >= 0) den += (double)s_k[threadIdx.x * R + l];
+                if (s_id[threadIdx.x * R + l] >= 0) den += s_k[threadIdx.x * R + l];
             const double inv = den > 0.0 ? 1.0 / den : 0.0;
             s_inv[threadIdx.x] = inv;
             A.invden[i0 + threadIdx.x] = inv;
@@ -172,7 +172,7 @@ __device__ __forceinline__ void post_weights(const PostArgs& A, unsigned bx) {
             const int l = e / WT, pl = e - l * WT;
             if (pl < np) {
                 const int32_t j = s_id[pl * R + l];
-                A.w[l * n + i0 + pl] = j >= 0 ? (double)s_k[pl * R + l] * s_inv[pl] : 0.0;
+                A.w[l * n + i0 + pl] = j >= 0 ? s_k[pl * R + l] * s_inv[pl] : 0.0;
                 A.ids_t[l * n + i0 + pl] = j;
             }
         }
@@ -184,8 +184,9 @@ __device__ __forceinline__ void post_weights(const PostArgs& A, unsigned bx) {
 // with FP64 fused multiply-adds over the list in slot order (slot-major ids
 // and weights: a warp's loads of one slot are contiguous); a particle whose
 // kernel weights sum to zero keeps its value. Ids, weights and p were written
-// earlier in the same launch by other CTAs: plain loads (not the read-only
-// path), ordered by the grid barrier's fences.
+// earlier in the same launch by other CTAs: L2-coherent loads (ld.global.cg,
+// not the read-only path), ordered by the grid barrier's fences; the random
+// gathers of p do not allocate in L1.
 template <int KT>
 __device__ __forceinline__ void post_sweep(const PostArgs& A, unsigned bx, int it) {
     const double* pin = (it & 1) ? A.post : A.post_tmp;
@@ -199,10 +200,10 @@ __device__ __forceinline__ void post_sweep(const PostArgs& A, unsigned bx, int i
         double num = 0.0;
 #pragma unroll(KT > 0 ? KT : 1)
         for (int l = 0; l < K; ++l) {
-            const int j = ids[l * n + i];
-            if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(w[l * n + i], pin[j], num);
+            const int j = __ldcg(ids + l * n + i);
+            if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) num = fma(__ldcg(w + l * n + i), __ldcg(pin + j), num);
         }
-        pout[i] = A.invden[i] > 0.0 ? num : pin[i];
+        pout[i] = __ldcg(A.invden + i) > 0.0 ? num : __ldcg(pin + i);
     }
 }
 
