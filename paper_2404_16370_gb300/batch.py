@@ -2,18 +2,20 @@
 
 Workload: 64 instances on 8 seeded maps (4 box rooms of 20k points, 4
 outdoor scenes of 100k, 250k, 500k and 1M points), particle counts
-log-uniform in 2^12..2^18, scans of 1024..16384 points (log-uniform), every
-instance on its own CUDA stream. Each instance keeps one scan (ray-cast from
-a seeded pose) for every step, with small odometry and noise.
+log-uniform in 2^12..2^18, scans of 1024..16384 points (log-uniform). Each
+instance keeps one scan (ray-cast from a seeded pose) for every step, with
+small odometry and noise.
 
     python -m paper_2404_16370_gb300.batch --instances 64 --steps 10
 
 times the same steps taken (a) instance by instance with mp_step, one
 instance after the other on one stream, and (b) with mp_batch_step (one
 CUDA-graph launch per step: every phase one grouped kernel over all
-instances, likelihood splits picked by timing), and prints one JSON line
-with instance-steps/s and particle-point pairs/s of both. All contexts and
-the batch share one stream: no two instances' kernels run concurrently.
+instances, the posterior one persistent cooperative kernel, likelihood
+splits picked by timing), and prints one JSON line with instance-steps/s and
+particle-point pairs/s of both and how many instances end with a finite,
+normalised posterior. All contexts and the batch share one stream: no two
+instances' kernels run concurrently.
 """
 from __future__ import annotations
 
@@ -151,6 +153,12 @@ def main():
             torch.cuda.synchronize()
             t_bat = time.perf_counter() - t0
             splits = [mp.mp_batch_split(batch, i) for i in range(n)]
+            # every instance's posterior after the batched steps: finite and normalised
+            post_ok = 0
+            for c in ctxs:
+                mp.mp_get_posterior(c)
+                post = mp.mp_get_buffer(c, mp.MP_BUF_POST)
+                post_ok += int(bool(np.isfinite(post).all()) and abs(float(post.sum()) - 1.0) < 1e-9)
         finally:
             mp.mp_batch_destroy(batch)
     finally:
@@ -164,6 +172,7 @@ def main():
                     "ms_per_step": 1e3 * t_bat / a.steps, "create_s": round(create_s, 2)},
         "speedup": None if t_seq is None else t_seq / t_bat,
         "splits": {str(k): splits.count(k) for k in sorted(set(splits))},
+        "posteriors_normalised": f"{post_ok}/{n}",
     })
     print(json.dumps(res), flush=True)
 
