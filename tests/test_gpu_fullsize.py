@@ -3,8 +3,10 @@
 benchmark's launch configuration, against the oracle on samples it computes
 one by one: every map point's validity and sampled normals, 500k sampled NNF
 voxels, every particle's LSH key and the whole bucket order, sampled
-neighbour lists and sampled likelihood sums. Properties that hold at any
-size are checked for the rest (stable sort validity, posterior normalisation,
+neighbour lists and sampled likelihood sums, and the whole posterior (Eq. 11,
+one cooperative launch whose CTAs each take several particle blocks per
+sub-step at this size) element by element. Properties that hold at any size
+are checked for the rest (stable sort validity, posterior normalisation,
 argmax)."""
 import numpy as np
 import pytest
@@ -140,3 +142,26 @@ def test_posterior_properties_fullsize(stepped):
     b = int(np.argmax(post))
     assert np.array_equal(stepped["best"], stepped["poses"][b]) and stepped["best_p"] == post[b]
     assert np.all(np.isfinite(stepped["psi"])) and np.all(np.isfinite(stepped["poses"]))
+
+
+def test_posterior_fullsize_matches_oracle(big, stepped, oracle):
+    """Eq. 11 at 2^20 particles on the step's own neighbour lists, kernel
+    weights and log-likelihoods, with a random log prior (some zero prior
+    mass): every particle's smoothed posterior within 1e-10 relative of the
+    oracle's FP64 sweeps, and the same representative particle. Runs last:
+    it rewrites the context's posterior buffers."""
+    mp, ctx, P = big["mp"], big["ctx"], big["P"]
+    loglik = mp.mp_get_buffer(ctx, mp.MP_BUF_LOGLIK)
+    ids, kk = stepped["ids"], stepped["k"]
+    rng = np.random.default_rng(5)
+    logprior = -rng.uniform(0, 5, N)
+    logprior[::1009] = -np.inf
+    mp.mp_set_buffer(ctx, mp.MP_BUF_LOG_PRIOR, logprior)
+    mp.mp_run_stages(ctx, mp.MP_STAGE_POSTERIOR)
+    post = mp.mp_get_buffer(ctx, mp.MP_BUF_POST)
+    best, best_p = mp.mp_get_posterior(ctx)
+    _, p_ref, b_ref = oracle.posterior(logprior, loglik.astype(np.float64), ids, kk.astype(np.float64),
+                                       P.post_iters)
+    assert np.allclose(post, p_ref, rtol=1e-10, atol=1e-300)
+    assert abs(post.sum() - 1) < 1e-12
+    assert abs(best_p - p_ref[b_ref]) < 1e-12 and post[b_ref] == best_p
