@@ -3,7 +3,8 @@
 benchmark's launch configuration, against the oracle on samples it computes
 one by one: every map point's validity and sampled normals, 500k sampled NNF
 voxels, every particle's LSH key and the whole bucket order, sampled
-neighbour lists and sampled likelihood sums, and the whole posterior (Eq. 11,
+neighbour lists, sampled likelihood sums, sampled Gauss-Newton steps and
+SVGD updates, and the whole posterior (Eq. 11,
 one cooperative launch whose CTAs each take several particle blocks per
 sub-step at this size) element by element. Properties that hold at any size
 are checked for the rest (stable sort validity, posterior normalisation,
@@ -75,7 +76,8 @@ def stepped(big):
     best, best_p = mp.mp_get_posterior(ctx)
     names = {"keys": mp.MP_BUF_KEYS, "buckets": mp.MP_BUF_BUCKETS, "sid": mp.MP_BUF_SORTED_IDS,
              "seg": mp.MP_BUF_SEGMENTS, "ids": mp.MP_BUF_NBR_IDS, "k": mp.MP_BUF_NBR_K, "gn": mp.MP_BUF_GN,
-             "post": mp.MP_BUF_POST, "psi": mp.MP_BUF_PSI, "poses": mp.MP_BUF_POSES}
+             "post": mp.MP_BUF_POST, "psi": mp.MP_BUF_PSI, "poses": mp.MP_BUF_POSES, "d": mp.MP_BUF_NBR_D,
+             "phi": mp.MP_BUF_PHI}
     out = {k: mp.mp_get_buffer(ctx, b) for k, b in names.items()}
     out.update(best=best, best_p=best_p)
     return out
@@ -134,6 +136,49 @@ def test_likelihood_sampled_fullsize(big, stepped, oracle):
     assert np.array_equal(gn[ok, 28].astype(np.int64), ref["n_in"][ok])
     msg = check_sums(gn, ref)
     assert not msg, msg
+
+
+def test_solve_sampled_fullsize(big, stepped, oracle):
+    """The damped 6x6 Gauss-Newton step on the step's own sums (20000 sampled
+    particles): psi solves the oracle's system to 1e-4 backward error, matches
+    the oracle's FP64 solve where the scaled system is well conditioned, and
+    is zero below 6 inliers."""
+    P = big["P"]
+    rng = np.random.default_rng(6)
+    sub = rng.choice(N, 20000, replace=False)
+    gn = stepped["gn"][sub].astype(np.float64)
+    psi = stepped["psi"][sub].astype(np.float64)
+    n_in = stepped["gn"][sub, 28].astype(np.int32)
+    Hf = oracle.h_full(gn[:, :21])
+    A = Hf + P.lam * (np.eye(6) * np.diagonal(Hf, axis1=1, axis2=2)[:, :, None]) + P.eps_damp * np.eye(6)
+    ok = n_in >= 6
+    res = np.einsum("nij,nj->ni", A, psi) + gn[:, 21:27]
+    scale = np.linalg.norm(A, axis=(1, 2)) * np.linalg.norm(psi, axis=1) + np.linalg.norm(gn[:, 21:27], axis=1)
+    r = np.linalg.norm(res, axis=1) / np.maximum(scale, 1e-30)
+    assert ok.sum() > 1000 and r[ok].max() < 1e-4, r[ok].max()
+    psi_ref, _ = oracle.gn_solve(gn[:, :21], gn[:, 21:27], n_in, P)
+    d = np.sqrt(np.diagonal(A, axis1=1, axis2=2))
+    cond = np.linalg.cond(A / d[:, :, None] / d[:, None, :])
+    good = ok & (cond < 1e3)
+    rel = np.linalg.norm(psi - psi_ref, axis=1) / np.maximum(np.linalg.norm(psi_ref, axis=1), 1e-12)
+    assert good.sum() > 1000 and np.percentile(rel[good], 99) < 1e-3
+    assert np.all(psi[~ok] == 0)
+
+
+def test_svgd_sampled_fullsize(big, stepped, oracle):
+    """Eq. 5-6 and the SE(3) retraction at 2^20 particles (20000 sampled), on
+    the step's own lists, kernel values, cached differences and psi."""
+    from gpu_util import pose_error
+    P = big["P"]
+    rng = np.random.default_rng(7)
+    sub = rng.choice(N, 20000, replace=False)
+    phi_ref, new_ref = oracle.svgd(big["w"].particles[sub], stepped["ids"][sub], stepped["k"][sub].astype(np.float64),
+                                   stepped["d"][sub].astype(np.float64), stepped["psi"].astype(np.float64), P)
+    phi = stepped["phi"][sub, :6].astype(np.float64)
+    assert np.allclose(phi, phi_ref, rtol=1e-5, atol=1e-6)
+    ang, dist = pose_error(stepped["poses"][sub], new_ref)
+    mag = 1 + np.linalg.norm(phi_ref, axis=1)
+    assert np.all(ang <= 1e-5 * mag) and np.all(dist <= 2e-6 * (1 + np.abs(new_ref[:, 4:]).max(1)) * mag)
 
 
 def test_posterior_properties_fullsize(stepped):
