@@ -121,6 +121,20 @@ def test_neighbour_lists_sampled_fullsize(big, stepped, oracle):
         a, b = stepped["ids"][i], mg["ids"][r]
         if set(a[a >= 0]) != set(b[b >= 0]):
             bad += 1
+            continue
+        # the cached kernel values and log differences, matched by id. The FP32
+        # log of T_i^-1 T_j rounds at about 1e-7 of its largest component (the
+        # relative translation reaches ~90 m at this scale, and V^-1 mixes the
+        # components), hence the floor scaled by max |d|
+        slot = {j: s for s, j in enumerate(b)}
+        for s_g, j in enumerate(a):
+            if j < 0:
+                continue
+            s_r = slot[j]
+            dref = mg["d"][r, s_r]
+            assert abs(stepped["k"][i, s_g] - mg["k"][r, s_r]) <= 1e-5 * mg["k"][r, s_r] + 1e-7
+            tol = 1e-4 * np.abs(dref) + 1e-6 * (1 + np.abs(dref).max())
+            assert np.all(np.abs(stepped["d"][i, s_g] - dref) <= tol), (i, j, stepped["d"][i, s_g], dref)
     assert bad == 0
 
 
