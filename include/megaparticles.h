@@ -17,7 +17,8 @@
  *  - Pointers may be host or device memory; the library asks the CUDA runtime
  *    (cudaPointerGetAttributes) and copies accordingly. Device pointers must
  *    belong to the device that was current at mp_init_map.
- *  - Ownership: the context owns all device state. Inputs are copied before the
+ *  - Ownership: the context owns all device state (a map shared through
+ *    mp_init_map_shared: jointly with the other contexts on it). Inputs are copied before the
  *    call returns (or enqueued on the context stream, for device pointers: the
  *    caller keeps them alive until the stream reaches that point). Outputs go
  *    to caller-allocated buffers.
@@ -95,6 +96,21 @@ int mp_default_params(mp_params* p, int preset, int64_t n_particles);
  * memory. Errors: MP_EINVAL (NULL/empty input, bad params, grid too large),
  * MP_ENOMEM, MP_ECUDA; *ctx is NULL on error. */
 int mp_init_map(mp_ctx** ctx, const float* xyz, int64_t n_map, const mp_params* p, void* cuda_stream);
+
+/* A context on the map of another (no counterpart in the paper: several
+ * filters localising in one map, e.g. the instances of a batch). *ctx gets its
+ * own particles, scan buffers, parameters and stream, and reads src's device
+ * map (points, normals, records, NNF) without a copy; the map's device memory
+ * is freed with the last context that uses it, whichever is destroyed last.
+ * The map is read-only after mp_init_map, so contexts sharing it may step on
+ * different streams. p may differ from src's parameters except in those that
+ * define the map: nnf_res, r_max, r_cov, cov_k and cov_min must be equal.
+ * Synchronises src's stream and cuda_stream. Errors: MP_EINVAL (NULL
+ * argument, src without a map, map parameters that differ, another device
+ * than src's), MP_ENOMEM, MP_ECUDA; *ctx is NULL on error. Creating and
+ * destroying contexts that share a map is thread-safe with respect to the
+ * count of its users. */
+int mp_init_map_shared(mp_ctx** ctx, mp_ctx* src, const mp_params* p, void* cuda_stream);
 
 /* Particle set X_t (Sec. III-A), uniform prior, neighbour lists = {self}.
  * With poses_or_null (n x 7 float32) the poses are copied; otherwise each

@@ -4,7 +4,8 @@ Workload: 64 instances on 8 seeded maps (4 box rooms of 20k points, 4
 outdoor scenes of 100k, 250k, 500k and 1M points), particle counts
 log-uniform in 2^12..2^18, scans of 1024..16384 points (log-uniform). Each
 instance keeps one scan (ray-cast from a seeded pose) for every step, with
-small odometry and noise.
+small odometry and noise. The instances on one map share its device copy
+(mp_init_map_shared; --own-maps gives each instance its own).
 
     python -m paper_2404_16370_gb300.batch --instances 64 --steps 10
 
@@ -60,12 +61,17 @@ def build_instances(n_inst, seed=0, log2_particles=(12, 18), log2_points=(10, 14
     return inst
 
 
-def make_contexts(inst, stream):
-    """One context per instance, all on `stream`."""
-    ctxs = []
+def make_contexts(inst, stream, share_maps=True):
+    """One context per instance, all on `stream`; with share_maps the
+    instances on one map use one device copy of it (mp_init_map_shared)."""
+    ctxs, first = [], {}
     for d in inst:
         p = mp.mp_default_params(d["preset"], d["n"])
-        ctx = mp.mp_init_map(d["pts"], p, cuda_stream=stream)
+        if share_maps and d["map"] in first:
+            ctx = mp.mp_init_map_shared(first[d["map"]], p, cuda_stream=stream)
+        else:
+            ctx = mp.mp_init_map(d["pts"], p, cuda_stream=stream)
+            first[d["map"]] = ctx
         mp.mp_init_particles(ctx, d["n"], poses=d["parts"])
         ctxs.append(ctx)
     return ctxs
@@ -102,6 +108,8 @@ def main():
     ap.add_argument("--small", action="store_true",
                     help="8 box rooms, 2^10..2^13 particles, 512..2048-point scans (the launch-bound regime)")
     ap.add_argument("--batched-only", action="store_true", help="time only the batched steps (no mp_step baseline)")
+    ap.add_argument("--own-maps", action="store_true",
+                    help="one device copy of the map per instance (default: the instances on one map share it)")
     a = ap.parse_args()
     import torch
     t0 = time.perf_counter()
@@ -114,6 +122,7 @@ def main():
     scans = [d["scan"] for d in inst]
     pairs_step = float(sum(d["n"] * len(d["scan"]) for d in inst))
     res = {"workload": "small box-room instances" if a.small else "64 instances, 8 box-room/outdoor maps",
+           "device_maps": "one per instance" if a.own_maps else "one per map, shared by its instances",
            "instances": n, "maps": 8, "particles_total": int(sum(d["n"] for d in inst)),
            "scan_points_total": int(sum(len(d["scan"]) for d in inst)), "steps": a.steps, "warmup": a.warmup,
            "inputs_s": round(gen_s, 1)}
@@ -121,7 +130,7 @@ def main():
     t_seq = None
     # (a) instance by instance
     if not a.batched_only:
-        ctxs = make_contexts(inst, stream)
+        ctxs = make_contexts(inst, stream, not a.own_maps)
         try:
             for s in range(a.warmup):
                 T, cov = odometry(n, s)
@@ -136,7 +145,7 @@ def main():
         finally:
             release(ctxs)
     # (b) batched
-    ctxs = make_contexts(inst, stream)
+    ctxs = make_contexts(inst, stream, not a.own_maps)
     try:
         t0 = time.perf_counter()
         batch = mp.mp_batch_create(ctxs, [len(s) for s in scans], stream, tune_scans=scans)

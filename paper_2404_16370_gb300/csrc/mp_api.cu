@@ -203,8 +203,16 @@ void destroy(mp_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_particles(c);
-    dfree(c->map_pts); dfree(c->map_normals); dfree(c->map_valid); dfree(c->map_rec); dfree(c->map_perm);
-    dfree(c->nnf);
+    // the map buffers go with the last context that uses them
+    if (c->map_refs && c->map_refs->fetch_sub(1) > 1) {
+        c->map_pts = nullptr; c->map_normals = nullptr; c->map_valid = nullptr; c->map_rec = nullptr;
+        c->map_perm = nullptr; c->nnf = nullptr;
+    } else {
+        delete c->map_refs;
+        dfree(c->map_pts); dfree(c->map_normals); dfree(c->map_valid); dfree(c->map_rec); dfree(c->map_perm);
+        dfree(c->nnf);
+    }
+    c->map_refs = nullptr;
     dfree(c->scan_raw); dfree(c->scan_normals); dfree(c->scan_valid); dfree(c->scan_pair); dfree(c->scan_h2); dfree(c->scan_tmp4);
     dfree(c->scan_nvalid);
     dfree(c->scalars); dfree(c->best_idx); dfree(c->best_pose); dfree(c->dev_error); dfree(c->post_bar); dfree(c->pairs);
@@ -360,6 +368,45 @@ int mp_default_params(mp_params* p, int preset, int64_t n_particles) {
 
 const char* mp_last_error(const mp_ctx* ctx) { return ctx ? ctx->err : g_null_ctx_msg; }
 
+// Everything of a context but its map: scan buffers, step scalars, staging,
+// events.
+static int ctx_setup(mp_ctx* c) {
+    int rc = MP_OK;
+    do {
+        int64_t ms = c->p.max_scan;
+        if ((rc = dalloc(c, &c->scan_raw, 3 * ms))) break;
+        if ((rc = dalloc(c, &c->scan_normals, 3 * ms))) break;
+        if ((rc = dalloc(c, &c->scan_valid, ms))) break;
+        if ((rc = dalloc(c, &c->scan_pair, 3 * ms))) break;
+        if ((rc = dalloc(c, &c->scan_h2, 2 * ms))) break;
+        if ((rc = dalloc(c, &c->scan_tmp4, ms))) break;
+        if ((rc = dalloc(c, &c->scan_nvalid, 1))) break;
+        if ((rc = dalloc(c, &c->scalars, 8))) break;
+        if ((rc = dalloc(c, &c->best_idx, 1))) break;
+        if ((rc = dalloc(c, &c->best_pose, 2))) break;
+        if ((rc = dalloc(c, &c->dev_error, 1))) break;
+        if ((rc = dalloc(c, &c->post_bar, 1))) break;
+        if ((rc = dalloc(c, &c->step_dev, 1))) break;
+        if ((rc = dalloc(c, &c->pairs, 1))) break;
+        cudaError_t e = cudaHostAlloc((void**)&c->step_host, 2 * sizeof(StepDev), cudaHostAllocDefault);
+        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "cudaHostAlloc"); break; }
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&c->step_ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "cudaEventCreate"); break; }
+        e = cudaMemsetAsync(c->dev_error, 0, sizeof(int32_t), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->scan_nvalid, 0, sizeof(int32_t), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->stream);
+        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "memset"); break; }
+        for (int r = 0; r < MP_EV_RING && !rc; ++r)
+            for (int s = 0; s < MP_NSTAGES && !rc; ++s)
+                for (int k = 0; k < 2 && !rc; ++k) {
+                    e = cudaEventCreate(&c->ev[r][s][k]);
+                    if (e != cudaSuccess) rc = mp_cuda_check(c, e, "event");
+                }
+    } while (0);
+    c->odom_q[3] = 1.f;
+    return rc;
+}
+
 int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* p, void* cuda_stream) {
     if (!out) return MP_EINVAL;
     *out = nullptr;
@@ -381,51 +428,22 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
     c->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&c->device);
     c->n_map = n_map;
+    c->map_refs = new (std::nothrow) std::atomic<int>(1);
+    if (!c->map_refs) { destroy(c); return MP_ENOMEM; }
     float* xyz_dev = nullptr;
     do {
         if ((rc = dalloc(c, &c->map_pts, n_map))) break;
         if ((rc = dalloc(c, &c->map_normals, 3 * n_map))) break;
         if ((rc = dalloc(c, &c->map_valid, n_map))) break;
         if ((rc = dalloc(c, &c->map_rec, 2 * n_map))) break;
-        int64_t ms = c->p.max_scan;
-        if ((rc = dalloc(c, &c->scan_raw, 3 * ms))) break;
-        if ((rc = dalloc(c, &c->scan_normals, 3 * ms))) break;
-        if ((rc = dalloc(c, &c->scan_valid, ms))) break;
-        if ((rc = dalloc(c, &c->scan_pair, 3 * ms))) break;
-        if ((rc = dalloc(c, &c->scan_h2, 2 * ms))) break;
-        if ((rc = dalloc(c, &c->scan_tmp4, ms))) break;
-        if ((rc = dalloc(c, &c->scan_nvalid, 1))) break;
-        if ((rc = dalloc(c, &c->scalars, 8))) break;
-        if ((rc = dalloc(c, &c->best_idx, 1))) break;
-        if ((rc = dalloc(c, &c->best_pose, 2))) break;
-        if ((rc = dalloc(c, &c->dev_error, 1))) break;
-        if ((rc = dalloc(c, &c->post_bar, 1))) break;
-        if ((rc = dalloc(c, &c->step_dev, 1))) break;
-        cudaError_t e = cudaHostAlloc((void**)&c->step_host, 2 * sizeof(StepDev), cudaHostAllocDefault);
-        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "cudaHostAlloc"); break; }
-        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&c->step_ev[k], cudaEventDisableTiming);
-        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "cudaEventCreate"); break; }
-        e = cudaMemsetAsync(c->dev_error, 0, sizeof(int32_t), c->stream);
-        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "memset"); break; }
-        e = cudaMemsetAsync(c->scan_nvalid, 0, sizeof(int32_t), c->stream);
-        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "memset"); break; }
+        if ((rc = ctx_setup(c))) break;
         if ((rc = dalloc(c, &xyz_dev, 3 * n_map))) break;
-        e = cudaMemcpyAsync(xyz_dev, xyz, sizeof(float) * 3 * (size_t)n_map, cudaMemcpyDefault, c->stream);
+        cudaError_t e = cudaMemcpyAsync(xyz_dev, xyz, sizeof(float) * 3 * (size_t)n_map, cudaMemcpyDefault, c->stream);
         if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "map upload"); break; }
         rc = mp_launch_map_prepare(c, xyz_dev);
         if (rc) break;
         e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "map preprocessing"); break; }
-        if ((rc = dalloc(c, &c->pairs, 1))) break;
-        e = cudaMemsetAsync(c->pairs, 0, sizeof(unsigned long long), c->stream);
-        if (e != cudaSuccess) { rc = mp_cuda_check(c, e, "memset"); break; }
-        for (int r = 0; r < MP_EV_RING && !rc; ++r)
-            for (int s = 0; s < MP_NSTAGES && !rc; ++s)
-                for (int k = 0; k < 2 && !rc; ++k) {
-                    e = cudaEventCreate(&c->ev[r][s][k]);
-                    if (e != cudaSuccess) rc = mp_cuda_check(c, e, "event");
-                }
-        if (rc) break;
     } while (0);
     if (xyz_dev) cudaFree(xyz_dev);
     if (rc) {
@@ -433,7 +451,65 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
         destroy(c);
         return rc;
     }
-    c->odom_q[3] = 1.f;
+    *out = c;
+    return MP_OK;
+}
+
+int mp_init_map_shared(mp_ctx** out, mp_ctx* src, const mp_params* p, void* cuda_stream) {
+    if (!out) return MP_EINVAL;
+    *out = nullptr;
+    if (!src || !p || !src->map_refs || src->n_map <= 0) return MP_EINVAL;
+    mp_ctx* c = new (std::nothrow) mp_ctx();
+    if (!c) return MP_ENOMEM;
+    memset((void*)c, 0, sizeof(*c));
+    int rc = check_params(c, p);
+    const mp_params& q = src->p;
+    if (!rc && (p->nnf_res != q.nnf_res || p->r_max != q.r_max || p->r_cov != q.r_cov || p->cov_k != q.cov_k ||
+                p->cov_min != q.cov_min))
+        rc = mp_fail(c, MP_EINVAL, "mp_init_map_shared: nnf_res, r_max, r_cov, cov_k and cov_min must equal the "
+                                   "source context's (they define the map)");
+    cudaGetDevice(&c->device);
+    if (!rc && c->device != src->device)
+        rc = mp_fail(c, MP_EINVAL, "mp_init_map_shared: the source context belongs to device %d, not %d", src->device,
+                     c->device);
+    if (rc) {
+        fprintf(stderr, "%s\n", c->err);
+        destroy(c);
+        return rc;
+    }
+    c->p = *p;
+    c->stream = (cudaStream_t)cuda_stream;
+    // the map: the source's device buffers (read only from here on) and its geometry
+    c->n_map = src->n_map;
+    c->n_map_valid = src->n_map_valid;
+    c->map_pts = src->map_pts;
+    c->map_normals = src->map_normals;
+    c->map_valid = src->map_valid;
+    c->map_rec = src->map_rec;
+    c->map_perm = src->map_perm;
+    c->nnf = src->nnf;
+    memcpy(c->nnf_dims, src->nnf_dims, sizeof(c->nnf_dims));
+    c->nnf_voxels = src->nnf_voxels;
+    memcpy(c->nnf_origin, src->nnf_origin, sizeof(c->nnf_origin));
+    c->nnf_inv_res = src->nnf_inv_res;
+    memcpy(c->nnf_off, src->nnf_off, sizeof(c->nnf_off));
+    memcpy(c->map_lo, src->map_lo, sizeof(c->map_lo));
+    memcpy(c->map_hi, src->map_hi, sizeof(c->map_hi));
+    src->map_refs->fetch_add(1);
+    c->map_refs = src->map_refs;
+    if ((rc = ctx_setup(c))) {
+        fprintf(stderr, "mp_init_map_shared: %s\n", c->err);
+        destroy(c);
+        return rc;
+    }
+    // the source's map preprocessing ran on its own stream
+    cudaError_t e = cudaStreamSynchronize(src->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        rc = mp_cuda_check(c, e, "mp_init_map_shared");
+        destroy(c);
+        return rc;
+    }
     *out = c;
     return MP_OK;
 }

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -55,6 +56,7 @@ struct mp_ctx {
     int64_t nnf_voxels;
     float nnf_origin[3], nnf_inv_res, nnf_off[3];
     double map_lo[3], map_hi[3];
+    std::atomic<int>* map_refs;   // contexts using these map buffers (mp_init_map_shared); the last frees them
 
     // particles
     int64_t n;              // particles (0 = not initialised)

@@ -78,6 +78,7 @@ def lib():
         V, P, I64, I32, U32, U64, D = C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_uint32, C.c_uint64, C.c_double
         L.mp_default_params.argtypes = [C.POINTER(mp_params), C.c_int, I64]
         L.mp_init_map.argtypes = [C.POINTER(V), P, I64, C.POINTER(mp_params), V]
+        L.mp_init_map_shared.argtypes = [C.POINTER(V), V, C.POINTER(mp_params), V]
         L.mp_init_particles.argtypes = [V, I64, P, P, P, P]
         L.mp_step.argtypes = [V, P, I32, P, P]
         L.mp_get_posterior.argtypes = [V, P, P, P, P]
@@ -97,7 +98,7 @@ def lib():
         L.mp_stage_times.argtypes = [V, P, P, C.POINTER(I64)]
         L.mp_kernel_launches.argtypes = [V, C.POINTER(I64)]
         L.mp_set_precision.argtypes = [V, C.c_int]
-        for f in ("mp_default_params", "mp_init_map", "mp_init_particles", "mp_step", "mp_get_posterior", "mp_destroy",
+        for f in ("mp_default_params", "mp_init_map", "mp_init_map_shared", "mp_init_particles", "mp_step", "mp_get_posterior", "mp_destroy",
                   "mp_set_scan", "mp_set_odometry", "mp_run_stages", "mp_set_step_index", "mp_buffer_size",
                   "mp_get_buffer", "mp_set_buffer", "mp_nnf_query", "mp_map_info", "mp_set_timing",
                   "mp_stage_times", "mp_kernel_launches", "mp_set_precision"):
@@ -144,6 +145,15 @@ def mp_init_map(xyz, params: mp_params, cuda_stream=None):
     rc = lib().mp_init_map(C.byref(ctx), ptr, n, C.byref(params), C.c_void_p(cuda_stream) if cuda_stream else None)
     if rc != MP_OK:
         raise MPError(rc, "mp_init_map failed (details on stderr)")
+    return ctx
+
+
+def mp_init_map_shared(src, params: mp_params, cuda_stream=None):
+    """A context on src's device map (no copy; freed with the last context on it)."""
+    ctx = C.c_void_p()
+    rc = lib().mp_init_map_shared(C.byref(ctx), src, C.byref(params), C.c_void_p(cuda_stream) if cuda_stream else None)
+    if rc != MP_OK:
+        raise MPError(rc, "mp_init_map_shared failed (details on stderr)")
     return ctx
 
 

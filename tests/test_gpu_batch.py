@@ -2,7 +2,10 @@
 sums equal the unsplit ones up to summation order; a batch step equals the
 same step taken instance by instance with mp_step (bit for bit with split 1);
 the autotuned batch runs with valid splits and posteriors; a starved grid
-barrier in the batched posterior is reported for every instance."""
+barrier in the batched posterior is reported for every instance; contexts
+sharing one device map (mp_init_map_shared) compute what contexts with their
+own copies compute, outlive the context that built the map, and refuse map
+parameters that differ."""
 import numpy as np
 import pytest
 
@@ -206,5 +209,87 @@ def test_batch_grid_barrier_timeout_reported_for_every_instance(torch):
     finally:
         mp.mp_batch_destroy(batch)
         for c in A:
+            mp.mp_destroy(c)
+        mp.mp_stream_destroy(st)
+
+
+def _room_params(n, **over):
+    from paper_2404_16370_gb300 import mp
+    return mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, n, **over)
+
+
+def test_shared_map_equals_own_map_and_outlives_its_source():
+    """Two contexts on one device map (the second made by mp_init_map_shared,
+    with other K and particle count) against two contexts with their own
+    copies: bit for bit after 3 steps, with the map's source destroyed before
+    the shared context steps."""
+    from paper_2404_16370_gb300 import mp
+    room, sc, parts = _room_instance(7, 3000, 700)
+    p1, p2 = _room_params(3000), _room_params(2048, K=8, C=8)
+    src = mp.mp_init_map(room.map_points, p1)
+    shared = mp.mp_init_map_shared(src, p2)
+    own = mp.mp_init_map(room.map_points, p2)
+    try:
+        assert np.array_equal(mp.mp_get_buffer(shared, mp.MP_BUF_MAP_NORMALS),
+                              mp.mp_get_buffer(own, mp.MP_BUF_MAP_NORMALS))
+        mp.mp_destroy(src)
+        src = None
+        for c in (shared, own):
+            mp.mp_init_particles(c, 2048, poses=parts[:2048])
+        for step in range(3):
+            T, cov = _odometry(1, step)
+            for c in (shared, own):
+                mp.mp_step(c, sc, T[0], cov[0])
+        _compare([shared], [own])
+    finally:
+        for c in (src, shared, own):
+            if c is not None:
+                mp.mp_destroy(c)
+
+
+def test_shared_map_refuses_other_map_parameters():
+    from paper_2404_16370_gb300 import mp
+    room, _, _ = _room_instance(8, 512, 256)
+    src = mp.mp_init_map(room.map_points, _room_params(512))
+    try:
+        for over in ({"nnf_res": 0.2}, {"r_max": 0.5}, {"r_cov": 0.5}, {"cov_k": 8}):
+            with pytest.raises(mp.MPError) as e:
+                mp.mp_init_map_shared(src, _room_params(512, **over))
+            assert e.value.code == mp.MP_EINVAL
+    finally:
+        mp.mp_destroy(src)
+
+
+def test_batch_on_shared_maps_equals_sequential_steps(torch):
+    """A batch whose instances share device maps (two per map) equals the same
+    instances with their own maps stepped one by one, bit for bit."""
+    from paper_2404_16370_gb300 import mp
+    st = mp.mp_stream_create()
+    specs = [(1, 1024, 512), (1, 2000, 600), (2, 1500, 512), (2, 4096, 700)]
+    data = [_room_instance(*sp) for sp in specs]
+    A, B = [], []
+    try:
+        for k, (room, sc, parts) in enumerate(data):
+            n = specs[k][1]
+            if k % 2 == 0:
+                A.append(mp.mp_init_map(room.map_points, _room_params(n), cuda_stream=st))
+            else:
+                A.append(mp.mp_init_map_shared(A[k - 1], _room_params(n), cuda_stream=st))
+            B.append(mp.mp_init_map(room.map_points, _room_params(n), cuda_stream=st))
+            for c in (A[k], B[k]):
+                mp.mp_init_particles(c, n, poses=parts)
+        scans = [d[1] for d in data]
+        batch = mp.mp_batch_create(A, [len(s) for s in scans], st)
+        try:
+            for step in range(3):
+                T, cov = _odometry(len(specs), step)
+                mp.mp_batch_step(batch, scans, T, cov)
+                for i, c in enumerate(B):
+                    mp.mp_step(c, scans[i], T[i], cov[i])
+            _compare(A, B)
+        finally:
+            mp.mp_batch_destroy(batch)
+    finally:
+        for c in A + B:
             mp.mp_destroy(c)
         mp.mp_stream_destroy(st)
