@@ -184,14 +184,21 @@ __device__ __forceinline__ Lk2Look lk2_none() {
     return L;
 }
 
+// One 32-byte map record (a 32-byte-aligned pair of float4, read-only in the
+// kernel) in one 256-bit load: (mu.xyz, w.x) and (w.y, w.z); the last two
+// words are padding.
+__device__ __forceinline__ void ld_record(const float4* p, float4& r0, float2& r1) {
+    float pad0, pad1;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r0.x), "=f"(r0.y), "=f"(r0.z), "=f"(r0.w), "=f"(r1.x), "=f"(r1.y), "=f"(pad0), "=f"(pad1)
+        : "l"(p));
+}
+
 // Map record of index mm: (mu.xyz, w.x) and (w.y, w.z).
 __device__ __forceinline__ void lk2_record(const LkArgs& A, int mm, float4& r0, float2& r1) {
     r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     r1 = make_float2(0.f, 0.f);
-    if (mm >= 0 && MP_DCHECK(mm < A.n_rec, "NNF entry beyond the map records", mm)) {
-        r0 = __ldg(A.rec + 2 * mm);
-        r1 = __ldg(reinterpret_cast<const float2*>(A.rec + 2 * mm + 1));
-    }
+    if (mm >= 0 && MP_DCHECK(mm < A.n_rec, "NNF entry beyond the map records", mm)) ld_record(A.rec + 2 * mm, r0, r1);
 }
 
 __device__ __forceinline__ void lk2_accumulate(const LkArgs& A, Lk2Acc& S, const float2 R[9], float2 tx, float2 ty,
