@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(256) k_segments(const SortArgs A) { SegmentsOp
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cand_eval(const float4* __restrict__ poses, int j, const Quat& qic, const float Rit[9],
                                           const float ti[3], const float W[2], float d[6], float& s) {
-    float4 a = poses[2 * (int64_t)j], b = poses[2 * (int64_t)j + 1];
+    float4 a, b;
+    ld_nc_2x4(poses + 2 * (int64_t)j, a, b);   // the candidate's pose: one 32-byte load
     Quat qr = qmul(qic, Quat{a.x, a.y, a.z, a.w});
     float dt[3] = {b.x - ti[0], b.y - ti[1], b.z - ti[2]};
     float tr[3];

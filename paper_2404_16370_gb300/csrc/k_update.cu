@@ -240,8 +240,8 @@ __device__ __forceinline__ void SvgdOp<G, PRE>::run(const SvgdArgs& A, unsigned 
         if (j >= 0 && MP_DCHECK(j < n, "neighbour id", j)) {
             float k = kk[o];
             const float* dj = dd + o * 6;
-            const float4 p0 = *reinterpret_cast<const float4*>(psi + (int64_t)j * 8);
-            const float2 p1 = *reinterpret_cast<const float2*>(psi + (int64_t)j * 8 + 4);
+            float4 p0, p1;
+            ld_nc_2x4(reinterpret_cast<const float4*>(psi + (int64_t)j * 8), p0, p1);   // psi_j: one 32-byte load
             const float ps[6] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y};
 #pragma unroll
             for (int a = 0; a < 6; ++a) {

@@ -316,6 +316,13 @@ __device__ __forceinline__ void load_pose(const float4* poses, int64_t i, Quat& 
     q = Quat{a.x, a.y, a.z, a.w};
     t[0] = b.x; t[1] = b.y; t[2] = b.z;
 }
+// 32 bytes (two float4, 32-byte aligned, read-only for the whole kernel) in
+// one 256-bit load.
+__device__ __forceinline__ void ld_nc_2x4(const float4* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
 __device__ __forceinline__ void store_pose(float4* poses, int64_t i, const Quat& q, const float t[3]) {
     poses[2 * i] = make_float4(q.x, q.y, q.z, q.w);
     poses[2 * i + 1] = make_float4(t[0], t[1], t[2], 0.f);
