@@ -461,8 +461,7 @@ int mp_plan_posterior(mp_group* G, int p, std::vector<GOp>& plan) {
         bpb.push_back(tab.back().nb);
         max_iters = std::max(max_iters, tab.back().iters);
     }
-    const GridBar zero = {};
-    GridBar* bar = static_cast<GridBar*>(const_cast<void*>(G->upload(&zero, sizeof(zero))));
+    GridBar* bar = static_cast<GridBar*>(G->scratch(sizeof(GridBar)));
     const PostArgs* t = G->upload(tab);
     unsigned nblk = 0;
     const GBlk* map = G->block_map(bpb, &nblk);

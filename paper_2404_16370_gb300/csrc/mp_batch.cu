@@ -34,6 +34,22 @@ const void* mp_group::upload(const void* host, size_t bytes) {
     return d;
 }
 
+void* mp_group::scratch(size_t bytes) {
+    if (err) return nullptr;
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes ? bytes : 1);
+    if (e != cudaSuccess) {
+        err = e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
+        return nullptr;
+    }
+    arena.push_back(d);
+    if (cudaMemset(d, 0, bytes ? bytes : 1) != cudaSuccess) {
+        err = MP_ECUDA;
+        return nullptr;
+    }
+    return d;
+}
+
 const GBlk* mp_group::block_map(const std::vector<int64_t>& blocks, unsigned* nblk, const std::vector<int>& which,
                                 const std::vector<int>& ysplit) {
     std::vector<GBlk> m;

@@ -596,6 +596,8 @@ struct mp_group {
     int size() const { return (int)ctx.size(); }
     // device copy of a host array (nullptr and err set on failure)
     const void* upload(const void* host, size_t bytes);
+    // zeroed device memory the plan's kernels write (nullptr and err set on failure)
+    void* scratch(size_t bytes);
     template <typename T>
     const T* upload(const std::vector<T>& v) {
         return static_cast<const T*>(upload(v.data(), sizeof(T) * v.size()));
