@@ -106,7 +106,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--small", action="store_true",
-                    help="8 box rooms, 2^10..2^13 particles, 512..2048-point scans (the launch-bound regime)")
+                    help="8 box rooms, 2^10..2^13 particles, 512..2048-point scans (many small instances)")
     ap.add_argument("--batched-only", action="store_true", help="time only the batched steps (no mp_step baseline)")
     ap.add_argument("--own-maps", action="store_true",
                     help="one device copy of the map per instance (default: the instances on one map share it)")
