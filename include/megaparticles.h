@@ -268,16 +268,16 @@ int mp_gicp(mp_ctx* ctx, const float* src, int32_t n_src, const float* tgt, int3
 int mp_step_gicp(mp_ctx* ctx, const float* scan, int32_t n_scan, double cov_scale);
 
 /* ---- Batched instances ------------------------------------------------
- * Many independent contexts (each with its own map, particles and
- * parameters; presets may differ) stepped together. mp_batch_create plans
- * one step of all instances as about thirty grouped launches, each covering
- * the blocks of every instance (one kernel per phase: prediction, scan
- * Gaussians, LSH keys, each radix pass, merge, likelihood, solve, SVGD), and
- * the posterior as one cooperative persistent launch over all instances
- * (bounded grid barriers between its sub-steps; a barrier that gives up is
- * reported as MP_ETIMEOUT by every instance), and captures the plan on
- * cuda_stream into a CUDA
- * graph, twice (two pinned staging slots); mp_batch_step replays one. Per
+ * Many independent contexts (each with its own particles and parameters;
+ * presets may differ; maps their own or shared through mp_init_map_shared)
+ * stepped together. mp_batch_create plans one step of all instances as about
+ * thirty grouped launches, each covering the blocks of every instance (one
+ * kernel per phase: prediction, scan Gaussians, LSH keys, each radix pass,
+ * merge, likelihood, solve, SVGD), and the posterior as one cooperative
+ * persistent launch over all instances (bounded grid barriers between its
+ * sub-steps; a barrier that gives up is reported as MP_ETIMEOUT by every
+ * instance). It captures the plan on cuda_stream into a CUDA graph, twice
+ * (two pinned staging slots); mp_batch_step replays one. Per
  * instance the scan size is fixed (n_scan[i] points every step) and every step
  * runs all stages, the prediction included (identity odometry without noise
  * is applied, not skipped). tune_scans (may be NULL; else one host scan per
