@@ -110,6 +110,14 @@ def workload_desc(nvalid=None):
 KIDNAP_WINDOW = (60, 100)   # the second timed window: steps 60-99, after the kidnap at step 50
 
 
+def times_after_kidnap(args):
+    """Whether the GPU arm times the second window (steps 60-99); both arms
+    then build the 100-step trajectory, so they run the same scene."""
+    n_steps = args.warmup + args.steps
+    return args.after_kidnap == "on" or (args.after_kidnap == "auto" and args.steps >= 20
+                                         and n_steps <= KIDNAP_WINDOW[0] and args.init == "uniform")
+
+
 def make_workload(n_steps, n_particles=None, init="uniform"):
     """The outdoor trajectory workload. init="tracking" replaces the uniform
     particles by a cloud around the first ground-truth pose (0.5 m, 0.05 rad):
@@ -244,7 +252,8 @@ def run_reference(args):
     if rank != 0:
         return
     n_sample = args.sample
-    wl = make_workload(args.warmup + args.steps)
+    n_steps = args.warmup + args.steps
+    wl = make_workload(max(n_steps, KIDNAP_WINDOW[1]) if times_after_kidnap(args) else n_steps)
     O, f, init_s = oracle_setup(wl, n_sample)
     for s in range(args.warmup):
         oracle_step_time(f, wl, s)
@@ -293,8 +302,7 @@ def run_gpu(args):
     from paper_2404_16370_gb300 import mp
 
     n_steps = args.warmup + args.steps
-    after_kidnap = args.after_kidnap == "on" or (args.after_kidnap == "auto" and args.steps >= 20 and n_steps <= 60
-                                                 and args.init == "uniform")
+    after_kidnap = times_after_kidnap(args)
     wl = make_workload(max(n_steps, KIDNAP_WINDOW[1]) if after_kidnap else n_steps, init=args.init)
     stream = torch.cuda.Stream()
     params = mp.mp_default_params(mp.MP_PRESET_OUTDOOR, N_PARTICLES)
