@@ -1,0 +1,39 @@
+"""Host-side rules of the benchmark (no GPU): which runs also time the
+second window after the kidnap (steps 60-99), and that both arms then build
+the same 100-step trajectory; the per-stage bound model's FP64 terms."""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _args(steps, warmup, after="auto", init="uniform"):
+    return argparse.Namespace(steps=steps, warmup=warmup, after_kidnap=after, init=init)
+
+
+def test_second_window_only_in_benchmark_runs():
+    assert bench.times_after_kidnap(_args(40, 10))                 # the default run
+    assert not bench.times_after_kidnap(_args(2, 3))               # a profiling run
+    assert not bench.times_after_kidnap(_args(40, 10, "off"))
+    assert not bench.times_after_kidnap(_args(20, 10, init="tracking"))
+    assert not bench.times_after_kidnap(_args(60, 10))             # the first window would cross the kidnap
+    assert bench.times_after_kidnap(_args(5, 3, "on"))
+    lo, hi = bench.KIDNAP_WINDOW
+    assert (lo, hi) == (60, 100)
+
+
+def test_stage_bounds_take_the_larger_of_bytes_and_flops():
+    n, K = 1 << 20, 32
+    b = bench.stage_bounds_ms(n, K, pairs_per_step=8e9, hbm_gbs=6644.1)
+    # the posterior: 10 sweeps x (K x 16 + 8) B + 40 B a particle from HBM, against
+    # 20K + 2K + 70 FP64 flops a particle at the FP64 peak
+    hbm = n * (10 * (K * 16 + 8) + 40) / 6644.1e9 * 1e3
+    fp64 = n * (20 * K + 2 * K + 70) / (bench.FP64_PEAK_TFLOPS * 1e12) * 1e3
+    assert abs(b["posterior"] - max(hbm, fp64)) < 1e-12
+    # the likelihood: one 32-byte sector a pair against 222 flops a pair
+    lk = max(8e9 * bench.LK_SECTOR_BYTES_PER_PAIR / 6644.1e9, 8e9 * bench.LK_FLOPS_PER_PAIR / (bench.ALU_PEAK_TFLOPS * 1e12))
+    assert abs(b["likelihood"] - 1e3 * lk) < 1e-9
