@@ -5,7 +5,8 @@ the autotuned batch runs with valid splits and posteriors; a starved grid
 barrier in the batched posterior is reported for every instance; contexts
 sharing one device map (mp_init_map_shared) compute what contexts with their
 own copies compute, outlive the context that built the map, and refuse map
-parameters that differ."""
+parameters that differ; an instance with the preconditioned SVGD reading
+batches bit for bit too."""
 import numpy as np
 import pytest
 
@@ -279,6 +280,42 @@ def test_batch_on_shared_maps_equals_sequential_steps(torch):
             for c in (A[k], B[k]):
                 mp.mp_init_particles(c, n, poses=parts)
         scans = [d[1] for d in data]
+        batch = mp.mp_batch_create(A, [len(s) for s in scans], st)
+        try:
+            for step in range(3):
+                T, cov = _odometry(len(specs), step)
+                mp.mp_batch_step(batch, scans, T, cov)
+                for i, c in enumerate(B):
+                    mp.mp_step(c, scans[i], T[i], cov[i])
+            _compare(A, B)
+        finally:
+            mp.mp_batch_destroy(batch)
+    finally:
+        for c in A + B:
+            mp.mp_destroy(c)
+        mp.mp_stream_destroy(st)
+
+
+def test_batch_with_preconditioned_svgd_equals_sequential_steps(torch):
+    """One instance with the preconditioned SVGD reading (svgd_precond = 1:
+    the solve stores each particle's inverse, SVGD multiplies the repulsion
+    by it) batched with one without: bit for bit the eager steps."""
+    from paper_2404_16370_gb300 import mp
+    st = mp.mp_stream_create()
+    specs = [(9, 2048, 600), (10, 3000, 512)]
+    data = [_room_instance(*sp) for sp in specs]
+
+    def make():
+        cs = []
+        for k, (room, sc, parts) in enumerate(data):
+            n = specs[k][1]
+            cs.append(mp.mp_init_map(room.map_points, _room_params(n, svgd_precond=1 - k), cuda_stream=st))
+            mp.mp_init_particles(cs[-1], n, poses=parts)
+        return cs
+
+    A, B = make(), make()
+    scans = [d[1] for d in data]
+    try:
         batch = mp.mp_batch_create(A, [len(s) for s in scans], st)
         try:
             for step in range(3):
