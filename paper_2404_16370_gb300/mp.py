@@ -107,14 +107,40 @@ def lib():
     return _lib
 
 
-def _ptr(x, dtype=None):
-    """(pointer, keep-alive) of None, a numpy array or a torch tensor."""
+_TORCH_NAME = {"float16": "torch.float16", "float32": "torch.float32", "float64": "torch.float64",
+               "int32": "torch.int32", "uint32": "torch.uint32", "int64": "torch.int64", "uint8": "torch.uint8"}
+
+
+def _ptr(x, dtype=None, shape=None, size=None, out=False):
+    """(pointer, keep-alive) of None, a numpy array or a torch tensor.
+
+    The library reads (or, out=True, writes) exactly the elements the caller
+    describes, so mismatches are refused here, before the call: dtype is the
+    element type the library uses (numpy inputs are converted to it; torch
+    tensors and every output must already have it), shape the expected shape
+    (-1 = any extent), size the expected element count. Outputs must be
+    contiguous (a converted copy would not receive the result)."""
     if x is None:
         return None, None
+    if shape is not None:
+        got = tuple(int(d) for d in x.shape)
+        if len(got) != len(shape) or any(w != -1 and w != d for w, d in zip(shape, got)):
+            raise ValueError(f"array of shape {got}: the library expects {tuple(shape)} (-1: any extent)")
+    if size is not None:
+        n = int(x.numel()) if hasattr(x, "numel") else int(np.size(x))
+        if n != size:
+            raise ValueError(f"array of {n} elements: the library expects {size}")
     if hasattr(x, "data_ptr"):               # torch tensor
+        if dtype is not None and str(x.dtype) != _TORCH_NAME[np.dtype(dtype).name]:
+            raise TypeError(f"tensor of {x.dtype}: the library uses {np.dtype(dtype).name}")
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
         return C.c_void_p(x.data_ptr()), x
+    if out:
+        if not isinstance(x, np.ndarray) or (dtype is not None and x.dtype != np.dtype(dtype)) \
+                or not x.flags.c_contiguous or not x.flags.writeable:
+            raise TypeError(f"output must be a writeable C-contiguous {np.dtype(dtype).name} array")
+        return x.ctypes.data_as(C.c_void_p), x
     a = np.ascontiguousarray(x, dtype=dtype)
     return a.ctypes.data_as(C.c_void_p), a
 
@@ -140,7 +166,7 @@ def mp_default_params(preset=MP_PRESET_BOX_ROOM, n_particles=4096, **overrides) 
 
 def mp_init_map(xyz, params: mp_params, cuda_stream=None):
     ctx = C.c_void_p()
-    ptr, keep = _ptr(xyz, np.float32)
+    ptr, keep = _ptr(xyz, np.float32, shape=(-1, 3))
     n = int(xyz.shape[0])
     rc = lib().mp_init_map(C.byref(ctx), ptr, n, C.byref(params), C.c_void_p(cuda_stream) if cuda_stream else None)
     if rc != MP_OK:
@@ -158,17 +184,18 @@ def mp_init_map_shared(src, params: mp_params, cuda_stream=None):
 
 
 def mp_init_particles(ctx, n_particles, lo=None, hi=None, poses=None, log_prior=None):
-    pl, kl = _ptr(lo, np.float32)
-    ph, kh = _ptr(hi, np.float32)
-    pp, kp = _ptr(poses, np.float32)
-    pr, kr = _ptr(log_prior, np.float64)
+    pl, kl = _ptr(lo, np.float32, size=6)
+    ph, kh = _ptr(hi, np.float32, size=6)
+    n = int(n_particles)   # n <= 0 is the library's to refuse (MP_EINVAL)
+    pp, kp = _ptr(poses, np.float32, shape=(n, 7) if n > 0 else None)
+    pr, kr = _ptr(log_prior, np.float64, size=n if n > 0 else None)
     _check(lib().mp_init_particles(ctx, int(n_particles), pl, ph, pp, pr), ctx)
 
 
 def mp_step(ctx, scan, odom_T=None, odom_cov=None):
-    ps, ks = _ptr(scan, np.float32)
-    pt, kt = _ptr(odom_T, np.float64)
-    pc, kc = _ptr(odom_cov, np.float64)
+    ps, ks = _ptr(scan, np.float32, shape=(-1, 3))
+    pt, kt = _ptr(odom_T, np.float64, size=16)
+    pc, kc = _ptr(odom_cov, np.float64, size=36)
     n = 0 if scan is None else int(scan.shape[0])
     _check(lib().mp_step(ctx, ps, n, pt, pc), ctx)
 
@@ -176,8 +203,10 @@ def mp_step(ctx, scan, odom_T=None, odom_cov=None):
 def mp_get_posterior(ctx, poses_out=None, prob_out=None):
     best = np.zeros(7, np.float32)
     bp = np.zeros(1, np.float64)
-    po, ko = _ptr(poses_out)
-    pr, kr = _ptr(prob_out)
+    if poses_out is not None or prob_out is not None:
+        n = mp_buffer_size(ctx, MP_BUF_LOG_PRIOR)
+    po, ko = _ptr(poses_out, np.float32, size=None if poses_out is None else 7 * n, out=True)
+    pr, kr = _ptr(prob_out, np.float64, size=None if prob_out is None else n, out=True)
     _check(lib().mp_get_posterior(ctx, po, pr, best.ctypes.data_as(C.c_void_p), bp.ctypes.data_as(C.c_void_p)), ctx)
     return best, float(bp[0])
 
@@ -188,13 +217,13 @@ def mp_destroy(ctx):
 
 
 def mp_set_scan(ctx, scan):
-    ps, ks = _ptr(scan, np.float32)
+    ps, ks = _ptr(scan, np.float32, shape=(-1, 3))
     _check(lib().mp_set_scan(ctx, ps, 0 if scan is None else int(scan.shape[0])), ctx)
 
 
 def mp_set_odometry(ctx, odom_T=None, odom_cov=None):
-    pt, kt = _ptr(odom_T, np.float64)
-    pc, kc = _ptr(odom_cov, np.float64)
+    pt, kt = _ptr(odom_T, np.float64, size=16)
+    pc, kc = _ptr(odom_cov, np.float64, size=36)
     _check(lib().mp_set_odometry(ctx, pt, pc), ctx)
 
 
@@ -229,7 +258,7 @@ def mp_get_buffer(ctx, which, K=None, out=None):
         out = np.empty(shape, dt)
     else:
         count = int(out.numel()) if hasattr(out, "numel") else int(out.size)
-    po, ko = _ptr(out)
+    po, ko = _ptr(out, _BUF[which][0], out=True)
     _check(lib().mp_get_buffer(ctx, int(which), po, count), ctx)
     return out
 
@@ -295,11 +324,11 @@ def mp_posterior_init_noalloc(log_prior, loglik, post_out, best_out, cuda_stream
                                                 C.c_void_p]
         L.mp_posterior_init_noalloc.restype = C.c_int
         L._noalloc_declared = True
-    lp, klp = _ptr(log_prior)
-    ll, kll = _ptr(loglik)
-    po, kpo = _ptr(post_out)
-    bo, kbo = _ptr(best_out)
     n = int(loglik.shape[0])
+    lp, klp = _ptr(log_prior, np.float64, size=n)
+    ll, kll = _ptr(loglik, np.float32, size=n)
+    po, kpo = _ptr(post_out, np.float64, size=n, out=True)
+    bo, kbo = _ptr(best_out, np.int64, size=1, out=True)
     rc = L.mp_posterior_init_noalloc(lp, ll, n, po, bo, C.c_void_p(cuda_stream) if cuda_stream else None)
     if rc != MP_OK:
         raise MPError(rc, "mp_posterior_init_noalloc failed (details on stderr)")
@@ -351,18 +380,39 @@ def _pn_check(rc, what):
         raise MPError(rc, f"{what} failed (details on stderr)")
 
 
-def _dev(t):
-    """data_ptr of a contiguous CUDA tensor."""
-    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+def _dev(t, shape=None, numel=None):
+    """data_ptr of a contiguous CUDA float32 tensor; shape (-1: any extent)
+    or numel, when given, is what the library reads or writes there."""
+    if not hasattr(t, "data_ptr"):
+        raise ValueError("expected a CUDA tensor")
+    if str(t.dtype) != "torch.float32":
+        raise TypeError(f"tensor of {t.dtype}: the library uses float32")
+    if shape is not None:
+        got = tuple(int(d) for d in t.shape)
+        if len(got) != len(shape) or any(w != -1 and w != d for w, d in zip(shape, got)):
+            raise ValueError(f"tensor of shape {got}: the library expects {tuple(shape)} (-1: any extent)")
+    if numel is not None and int(t.numel()) != numel:
+        raise ValueError(f"tensor of {int(t.numel())} elements: the library expects {numel}")
+    if not (t.is_cuda and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA tensor")
     return C.c_void_p(t.data_ptr())
 
 
+_pn_points = {}   # network pointer -> points per scan
+
+
+def _pn_scan_shape(net):
+    return (-1, _pn_points.get(net.value if isinstance(net, C.c_void_p) else net, -1), 3)
+
+
 def mp_pn_sim_box_room(boxes, half, height, poses, dirs, noise, seed, out, cuda_stream=None):
     """Ray-cast B x P box-room scans into out (B, P, 3); all tensors on the GPU."""
-    _pn_check(_pn_lib().mp_pn_sim_box_room(_dev(boxes), int(boxes.shape[0]), float(half), float(height), _dev(poses),
-                                           int(poses.shape[0]), _dev(dirs), int(dirs.shape[0]), float(noise),
-                                           int(seed) & (2 ** 64 - 1), _dev(out),
+    B, P = int(poses.shape[0]), int(dirs.shape[0])
+    pb, pp, pd = _dev(boxes, (-1, 7)), _dev(poses, (B, 7)), _dev(dirs, (P, 3))
+    po = _dev(out, (B, P, 3))
+    _pn_check(_pn_lib().mp_pn_sim_box_room(pb, int(boxes.shape[0]), float(half), float(height), pp,
+                                           B, pd, P, float(noise),
+                                           int(seed) & (2 ** 64 - 1), po,
                                            C.c_void_p(cuda_stream) if cuda_stream else None), "mp_pn_sim_box_room")
 
 
@@ -374,10 +424,12 @@ def mp_pn_create(n_points, max_batch, in_scale, scale, offset, seed=0, cuda_stre
                                      sc.ctypes.data_as(C.c_void_p), of.ctypes.data_as(C.c_void_p),
                                      int(seed) & (2 ** 64 - 1), C.c_void_p(cuda_stream) if cuda_stream else None),
               "mp_pn_create")
+    _pn_points[net.value] = int(n_points)
     return net
 
 
 def mp_pn_destroy(net):
+    _pn_points.pop(net.value if isinstance(net, C.c_void_p) else net, None)
     _pn_check(_pn_lib().mp_pn_destroy(net), "mp_pn_destroy")
 
 
@@ -388,20 +440,26 @@ def mp_pn_num_params(net) -> int:
 
 
 def mp_pn_get_params(net, out):
-    _pn_check(_pn_lib().mp_pn_get_params(net, _dev(out)), "mp_pn_get_params")
+    po = _dev(out, numel=mp_pn_num_params(net))
+    _pn_check(_pn_lib().mp_pn_get_params(net, po), "mp_pn_get_params")
 
 
 def mp_pn_set_params(net, params):
-    _pn_check(_pn_lib().mp_pn_set_params(net, _dev(params)), "mp_pn_set_params")
+    pp = _dev(params, numel=mp_pn_num_params(net))
+    _pn_check(_pn_lib().mp_pn_set_params(net, pp), "mp_pn_set_params")
 
 
 def mp_pn_forward(net, scans, out):
-    _pn_check(_pn_lib().mp_pn_forward(net, _dev(scans), int(scans.shape[0]), _dev(out)), "mp_pn_forward")
+    B = int(scans.shape[0])
+    ps, po = _dev(scans, _pn_scan_shape(net)), _dev(out, (B, MP_PN_OUT))
+    _pn_check(_pn_lib().mp_pn_forward(net, ps, B, po), "mp_pn_forward")
 
 
 def mp_pn_loss_grad(net, scans, targets, loss, grad=None):
-    _pn_check(_pn_lib().mp_pn_loss_grad(net, _dev(scans), _dev(targets), int(scans.shape[0]), _dev(loss),
-                                        _dev(grad) if grad is not None else None), "mp_pn_loss_grad")
+    B = int(scans.shape[0])
+    ps, pt, pl = _dev(scans, _pn_scan_shape(net)), _dev(targets, (B, 6)), _dev(loss, numel=1)
+    pg = _dev(grad, numel=mp_pn_num_params(net)) if grad is not None else None
+    _pn_check(_pn_lib().mp_pn_loss_grad(net, ps, pt, B, pl, pg), "mp_pn_loss_grad")
 
 
 def mp_pn_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -409,7 +467,8 @@ def mp_pn_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def mp_pn_sample(net, mix, n, seed, out):
-    _pn_check(_pn_lib().mp_pn_sample(net, _dev(mix), int(n), int(seed) & (2 ** 64 - 1), _dev(out)), "mp_pn_sample")
+    pm, po = _dev(mix, numel=MP_PN_OUT), _dev(out, (int(n), 7))
+    _pn_check(_pn_lib().mp_pn_sample(net, pm, int(n), int(seed) & (2 ** 64 - 1), po), "mp_pn_sample")
 
 
 # ---------------------------------------------------------------------------
@@ -443,12 +502,16 @@ def mp_batch_create(ctxs, n_scan, cuda_stream, tune_scans=None):
     n = len(ctxs)
     arr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
     ns = np.ascontiguousarray(n_scan, np.int32)
+    if ns.shape != (n,):
+        raise ValueError(f"n_scan holds {ns.size} sizes for {n} contexts")
     keep = []
     tp = None
     if tune_scans is not None:
+        if len(tune_scans) != n:
+            raise ValueError(f"{len(tune_scans)} tuning scans for {n} contexts")
         ptrs = []
-        for sc in tune_scans:
-            a = np.ascontiguousarray(sc, np.float32)
+        for i, sc in enumerate(tune_scans):
+            a = _batch_scan(sc, int(ns[i]), i)
             keep.append(a)
             ptrs.append(a.ctypes.data)
         tp = (C.c_void_p * n)(*ptrs)
@@ -457,12 +520,31 @@ def mp_batch_create(ctxs, n_scan, cuda_stream, tune_scans=None):
                                       C.c_void_p(cuda_stream))
     if rc != MP_OK:
         raise MPError(rc, "mp_batch_create failed (details on stderr)")
+    _batch_nscan[b.value] = [int(v) for v in ns]
     return b
+
+
+def _batch_scan(sc, n_scan, i):
+    """Instance i's host scan as the (n_scan, 3) float32 array the library copies from."""
+    if hasattr(sc, "data_ptr"):
+        raise TypeError("batched scans are host arrays (numpy)")
+    a = np.ascontiguousarray(sc, np.float32)
+    if a.shape != (n_scan, 3):
+        raise ValueError(f"instance {i}: scan of shape {a.shape}, the batch was created for ({n_scan}, 3)")
+    return a
+
+
+_batch_nscan = {}   # batch pointer -> each instance's fixed scan size
 
 
 def mp_batch_step(batch, scans, odom_T=None, odom_cov=None):
     n = len(scans)
-    keep = [np.ascontiguousarray(sc, np.float32) for sc in scans]
+    sizes = _batch_nscan.get(batch.value if isinstance(batch, C.c_void_p) else batch)
+    if sizes is None:
+        raise ValueError("not a live batch of this module")
+    if n != len(sizes):
+        raise ValueError(f"{n} scans for a batch of {len(sizes)} instances")
+    keep = [_batch_scan(sc, sizes[i], i) for i, sc in enumerate(scans)]
     ptrs = (C.c_void_p * n)(*[a.ctypes.data for a in keep])
     T = None if odom_T is None else np.ascontiguousarray(odom_T, np.float64).reshape(n, 16)
     Q = None if odom_cov is None else np.ascontiguousarray(odom_cov, np.float64).reshape(n, 36)
@@ -481,6 +563,7 @@ def mp_batch_split(batch, i) -> int:
 
 
 def mp_batch_destroy(batch):
+    _batch_nscan.pop(batch.value if isinstance(batch, C.c_void_p) else batch, None)
     rc = _batch_lib().mp_batch_destroy(batch)
     if rc != MP_OK:
         raise MPError(rc, "mp_batch_destroy failed")
@@ -518,8 +601,10 @@ def mp_gicp(ctx, src, tgt, init_T=None, max_iters=30):
     L.mp_gicp.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                           C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.mp_gicp.restype = C.c_int
-    sp, ks = _ptr(src, np.float32)
-    tp, kt = _ptr(tgt, np.float32)
+    sp, ks = _ptr(src, np.float32, shape=(-1, 3))
+    tp, kt = _ptr(tgt, np.float32, shape=(-1, 3))
+    if init_T is not None and np.size(init_T) != 16:
+        raise ValueError("init_T must hold 16 values (row-major 4x4)")
     T0 = None if init_T is None else np.ascontiguousarray(init_T, np.float64)
     T = np.zeros(16)
     cov = np.zeros(36)
@@ -538,7 +623,7 @@ def mp_step_gicp(ctx, scan, cov_scale=1.0):
     if scan is None or len(scan) == 0:
         _check(L.mp_step_gicp(ctx, None, 0, float(cov_scale)), ctx)
         return
-    sp, keep = _ptr(scan, np.float32)
+    sp, keep = _ptr(scan, np.float32, shape=(-1, 3))
     _check(L.mp_step_gicp(ctx, sp, int(scan.shape[0]), float(cov_scale)), ctx)
 
 
