@@ -443,8 +443,7 @@ def run_gpu(args):
     print(json.dumps(out), flush=True)
 
 
-def main():
-    global N_PARTICLES
+def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
@@ -461,6 +460,12 @@ def main():
                     help="also time steps 60-99 (after the kidnap at step 50); auto: when >= 20 steps are timed")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particle count (profiling runs of a smaller case; the benchmark is 2^20)")
+    return ap
+
+
+def main():
+    global N_PARTICLES
+    ap = build_parser()
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

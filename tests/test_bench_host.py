@@ -37,3 +37,22 @@ def test_stage_bounds_take_the_larger_of_bytes_and_flops():
     # the likelihood: one 32-byte sector a pair against 222 flops a pair
     lk = max(8e9 * bench.LK_SECTOR_BYTES_PER_PAIR / 6644.1e9, 8e9 * bench.LK_FLOPS_PER_PAIR / (bench.ALU_PEAK_TFLOPS * 1e12))
     assert abs(b["likelihood"] - 1e3 * lk) < 1e-9
+
+
+def test_profile_commands_parse():
+    """Every bench command a committed profile summary gives is accepted by
+    the bench's own parser (the summaries stay reproducible)."""
+    import glob
+    import shlex
+    cmds = []
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*")):
+        for line in open(path):
+            if "python bench.py" in line:
+                tail = line.split("python bench.py", 1)[1]
+                tail = tail.split(">")[0].split("&&")[0].replace("\\", " ")
+                cmds.append((os.path.basename(path), shlex.split(tail)))
+    assert len(cmds) >= 6
+    ap = bench.build_parser()
+    for name, argv in cmds:
+        a = ap.parse_args(argv)
+        assert a.warmup >= 3, (name, argv)
