@@ -131,7 +131,7 @@ def _ptr(x, dtype=None, shape=None, size=None, out=False):
         if n != size:
             raise ValueError(f"array of {n} elements: the library expects {size}")
     if hasattr(x, "data_ptr"):               # torch tensor
-        if dtype is not None and str(x.dtype) != _TORCH_NAME[np.dtype(dtype).name]:
+        if dtype is not None and str(x.dtype) != _TORCH_NAME.get(np.dtype(dtype).name):
             raise TypeError(f"tensor of {x.dtype}: the library uses {np.dtype(dtype).name}")
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
