@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(PB, 8) k_post_phase(const __grid_constant__ Po
     };
     unsigned bx;
     for (int w = blockIdx.x; w < P.n_blocks; w += gridDim.x) {
-        post_l(phase_item(P, w, bx), bx);
+        const PostArgs& A = phase_item(P, w, bx);   // sets bx: a statement of its own
+        post_l(A, bx);
         __syncthreads();
     }
     if (!sync()) return;
@@ -369,7 +370,8 @@ __global__ void __launch_bounds__(PB, 8) k_post_phase(const __grid_constant__ Po
     }
     if (P.max_iters == 0 && !sync()) return;   // the sums before final_part rewrites the partials
     for (int w = blockIdx.x; w < P.n_blocks; w += gridDim.x) {
-        final_part(phase_item(P, w, bx), bx);
+        const PostArgs& A = phase_item(P, w, bx);
+        final_part(A, bx);
         __syncthreads();
     }
     if (!sync()) return;
