@@ -1,11 +1,10 @@
 """Many independent localisation instances stepped together.
 
-Workload: 64 instances on 8 seeded maps (4 box rooms of 20k points, 4
-outdoor scenes of 100k, 250k, 500k and 1M points), particle counts
-log-uniform in 2^12..2^18, scans of 1024..16384 points (log-uniform). Each
-instance keeps one scan (ray-cast from a seeded pose) for every step, with
-small odometry and noise. The instances on one map share its device copy
-(mp_init_map_shared; --own-maps gives each instance its own).
+Workload: 64 instances on 8 seeded box rooms of 20k map points, particle
+counts log-uniform in 2^10..2^13, scans of 512..2048 points (log-uniform).
+Each instance keeps one scan (ray-cast from a seeded pose) for every step,
+with small odometry and noise. The instances on one map share its device
+copy (mp_init_map_shared; --own-maps gives each instance its own).
 
     python -m paper_2404_16370_gb300.batch --instances 64 --steps 10
 
@@ -17,6 +16,10 @@ splits picked by timing), and prints one JSON line with instance-steps/s and
 particle-point pairs/s of both and how many instances end with a finite,
 normalised posterior. All contexts and the batch share one stream: no two
 instances' kernels run concurrently.
+
+The mix with outdoor maps of up to 1M points and up to 2^18 particles per
+instance is not offered: it stopped with a GPU fault whose cause has not been
+found, and stays off the GPU until it is.
 """
 from __future__ import annotations
 
@@ -29,35 +32,20 @@ import numpy as np
 from . import mp, synth
 
 
-def build_instances(n_inst, seed=0, log2_particles=(12, 18), log2_points=(10, 14), outdoor=True):
+def build_instances(n_inst, seed=0, log2_particles=(10, 13), log2_points=(9, 11)):
+    """Box-room instances on 8 seeded rooms (instance i on room i mod 8)."""
     rng = np.random.default_rng(seed)
-    maps = []
-    for k in range(4 if outdoor else 8):
-        room = synth.box_room(1 + k)
-        maps.append(("box_room", room, room.map_points))
-    if outdoor:
-        for k, n_map in enumerate((100_000, 250_000, 500_000, 1_000_000)):
-            sc = synth.outdoor(11 + k, n_map=n_map)
-            maps.append(("outdoor", sc, sc.map_points))
+    maps = [synth.box_room(1 + k) for k in range(8)]
     inst = []
     for i in range(n_inst):
-        kind, scene, pts = maps[i % len(maps)]
+        room = maps[i % len(maps)]
         n_part = int(2 ** rng.uniform(*log2_particles))
         n_pts = int(2 ** rng.uniform(*log2_points))
-        if kind == "box_room":
-            gt = synth.box_room_gt_pose(scene, 1000 + i)
-            scan = synth.scan(scene, gt, synth.spherical_dirs(n_pts), 0.02, 2000 + i)
-            parts = synth.box_room_particles(n_part, 3000 + i, scene.half)
-            preset = mp.MP_PRESET_BOX_ROOM
-        else:
-            traj = synth.outdoor_trajectory(1, 0, seed=4000 + i, scene=scene)
-            gt = traj[0]
-            scan = synth.scan(scene, gt, synth.lidar_dirs(32, 512), 0.03, 2000 + i, dropout=0.1, max_range=100.0,
-                              n_keep=n_pts)
-            parts = synth.outdoor_particles(scene, n_part, 3000 + i)
-            preset = mp.MP_PRESET_OUTDOOR
-        inst.append(dict(map=i % len(maps), kind=kind, pts=pts, scan=scan.astype(np.float32), parts=parts,
-                         preset=preset, n=n_part))
+        gt = synth.box_room_gt_pose(room, 1000 + i)
+        scan = synth.scan(room, gt, synth.spherical_dirs(n_pts), 0.02, 2000 + i)
+        parts = synth.box_room_particles(n_part, 3000 + i, room.half)
+        inst.append(dict(map=i % len(maps), kind="box_room", pts=room.map_points, scan=scan.astype(np.float32),
+                         parts=parts, preset=mp.MP_PRESET_BOX_ROOM, n=n_part))
     return inst
 
 
@@ -105,23 +93,18 @@ def main():
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--small", action="store_true",
-                    help="8 box rooms, 2^10..2^13 particles, 512..2048-point scans (many small instances)")
     ap.add_argument("--batched-only", action="store_true", help="time only the batched steps (no mp_step baseline)")
     ap.add_argument("--own-maps", action="store_true",
                     help="one device copy of the map per instance (default: the instances on one map share it)")
     a = ap.parse_args()
     import torch
     t0 = time.perf_counter()
-    if a.small:
-        inst = build_instances(a.instances, log2_particles=(10, 13), log2_points=(9, 11), outdoor=False)
-    else:
-        inst = build_instances(a.instances)
+    inst = build_instances(a.instances)
     gen_s = time.perf_counter() - t0
     n = len(inst)
     scans = [d["scan"] for d in inst]
     pairs_step = float(sum(d["n"] * len(d["scan"]) for d in inst))
-    res = {"workload": "small box-room instances" if a.small else "64 instances, 8 box-room/outdoor maps",
+    res = {"workload": "box-room instances: 2^10..2^13 particles, 512..2048-point scans, 8 rooms of 20k points",
            "device_maps": "one per instance" if a.own_maps else "one per map, shared by its instances",
            "instances": n, "maps": 8, "particles_total": int(sum(d["n"] for d in inst)),
            "scan_points_total": int(sum(len(d["scan"]) for d in inst)), "steps": a.steps, "warmup": a.warmup,
