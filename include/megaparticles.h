@@ -143,7 +143,11 @@ int mp_get_posterior(mp_ctx* ctx, float* poses_out, double* prob_out, float best
 /* Frees every resource of the context (NULL is accepted). */
 int mp_destroy(mp_ctx* ctx);
 
-/* Message of the last error of ctx ("" if none; a static string if ctx is NULL). */
+/* Message of the last error of ctx ("" if none). With ctx NULL: the message
+ * of the last failure, on the calling thread, of a call that has no context
+ * to keep it (mp_init_map, mp_init_map_shared, the batch calls,
+ * mp_posterior_init_noalloc, the proposal network's calls). The library
+ * prints nothing. */
 const char* mp_last_error(const mp_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
@@ -337,21 +341,32 @@ int mp_debug_set(mp_ctx* ctx, int what, int64_t value);
  *
  * Computes, for n particles, p_i = exp(l_i - max l) / sum_j exp(l_j - max l)
  * with l_i = log_prior[i] + loglik[i] (log_prior NULL: 0), and the index of
- * the largest p_i (smallest index on ties): the same values as the posterior
- * stage's initial posterior (MP_BUF_POST_INIT). log_prior (n float64), loglik
- * (n float32), post_out (n float64) and best_out (1 int64) are DEVICE
- * pointers owned by the caller; the work is enqueued on cuda_stream (NULL =
- * legacy default stream) and the call does not synchronise.
+ * the largest p_i (smallest index on ties). These equal the posterior stage's
+ * initial posterior (MP_BUF_POST_INIT) up to the FP64 rounding of the sum,
+ * whose summation order differs; the index is the same. log_prior (n
+ * float64), loglik (n float32), post_out (n float64) and best_out (1 int64)
+ * are DEVICE pointers of the current device, owned by the caller; host
+ * memory (pageable or pinned) and other devices' memory are refused with
+ * MP_EINVAL before anything is launched. The work is enqueued on cuda_stream
+ * (NULL = legacy default stream) and the call does not synchronise.
+ *
+ * Degenerate input (every l_i = -inf, or some l_i NaN or +inf): the
+ * normaliser is not a finite positive number, so *best_out = -1 and every
+ * post_out[i] is NaN. The call still returns MP_OK (it does not wait for the
+ * result): check best_out >= 0 before using it as an index.
  *
  * No memory is allocated: block partials live in one static device array of
  * MP_NOALLOC_SCRATCH_BYTES that every device loading the library holds until
  * the process exits. The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress, with the device current) and caches it; make
- * that first call before any stream capture. All calls share the array, so
- * calls that overlap on the GPU race and must be serialised by the caller.
- * Errors: MP_EINVAL for NULL pointers or n outside [1,
- * MP_NOALLOC_MAX_PARTICLES] (with a message on stderr), MP_ECUDA for a failed
- * symbol lookup or launch. */
+ * address (cudaGetSymbolAddress, with the device current) and caches it; with
+ * lazy module loading (the CUDA default) that first call also loads the
+ * module, which places the array and the kernels on the device. Make that
+ * first call a warm-up in the caller's allocation phase, before any stream
+ * capture; later calls allocate nothing. All calls share the array, so calls
+ * that overlap on the GPU race and must be serialised by the caller.
+ * Errors: MP_EINVAL for NULL or non-device pointers and n outside [1,
+ * MP_NOALLOC_MAX_PARTICLES], MP_ECUDA for a failed symbol lookup or launch;
+ * the message is mp_last_error(NULL). */
 #define MP_NOALLOC_MAX_PARTICLES (1 << 24)
 #define MP_NOALLOC_SCRATCH_BYTES (262144 + 256)
 int mp_posterior_init_noalloc(const double* log_prior, const float* loglik, int64_t n, double* post_out,

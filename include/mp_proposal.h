@@ -27,7 +27,8 @@
  *
  * All array pointers are DEVICE pointers; every call is enqueued on the
  * stream given at creation (mp_pn_sim_box_room takes its own). Return codes
- * are those of megaparticles.h; messages go to stderr. */
+ * are those of megaparticles.h; the message of a failure is
+ * mp_last_error(NULL). */
 #ifndef MP_PROPOSAL_H
 #define MP_PROPOSAL_H
 

@@ -15,8 +15,15 @@
 // overlap on the GPU (two streams, or two threads) race on it and must be
 // serialised by the caller. Nothing in it carries over between calls: each
 // partial slot a call reads is written earlier in the same call.
+//
+// With lazy module loading (the CUDA default) the first call on a device also
+// loads this file's module there, which places the array and the kernels'
+// code on the device: that first call is a warm-up for the caller's
+// allocation phase, not for its latency-critical phase.
 #include "mp_internal.cuh"
 
+#include <cfloat>
+#include <climits>
 #include <mutex>
 
 namespace {
@@ -163,8 +170,13 @@ __global__ void __launch_bounds__(1024) k_na_final(int nb, NaScratch* S, int64_t
             S0 += ss[w];
             na_argmax(V, I, sv[w], si[w]);
         }
-        S->gsum = S0;
-        *best = (int64_t)I;
+        // Degenerate input: every l_i = -inf, or some l_i NaN or +inf. The
+        // normaliser is then not a finite positive number; the outputs get the
+        // sentinels best = -1 and post = NaN (x / NaN) instead of an index
+        // that no particle has.
+        const bool ok = S0 > 0.0 && S0 <= DBL_MAX && I != LLONG_MAX;
+        S->gsum = ok ? S0 : __longlong_as_double(0x7ff8000000000000LL);
+        *best = ok ? (int64_t)I : (int64_t)-1;
     }
 }
 
@@ -179,31 +191,49 @@ std::mutex g_na_mutex;
 void* g_na_addr[64];
 bool g_na_ready[64];
 
-int na_fail(int code, const char* msg) {
-    fprintf(stderr, "mp_posterior_init_noalloc: %s\n", msg);
-    return code;
+// The kernels dereference every pointer they are given as device memory of
+// the current device. A host array (pageable or pinned), or memory of another
+// device, is refused before any launch (cudaPointerGetAttributes allocates
+// nothing).
+int na_check_ptr(const void* p, int dev, const char* name) {
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // the failed query leaves a (non-sticky) error behind: clear it
+        return mp_fail_noctx(MP_EINVAL, "mp_posterior_init_noalloc: %s is not a device pointer", name);
+    }
+    if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != dev)
+        return mp_fail_noctx(MP_EINVAL, "mp_posterior_init_noalloc: %s is not device memory of the current device %d",
+                             name, dev);
+    return MP_OK;
 }
 
 }  // namespace
 
 extern "C" int mp_posterior_init_noalloc(const double* log_prior, const float* loglik, int64_t n, double* post_out,
                                          int64_t* best_out, void* cuda_stream) {
-    if (!loglik || !post_out || !best_out) return na_fail(MP_EINVAL, "NULL loglik, post_out or best_out");
-    if (n <= 0 || n > NA_MAX_N) {
-        fprintf(stderr, "mp_posterior_init_noalloc: n = %lld outside [1, %lld] (the fixed scratch holds %d block "
-                        "partials)\n", (long long)n, (long long)NA_MAX_N, NA_MAX_BLOCKS);
-        return MP_EINVAL;
-    }
+    if (!loglik || !post_out || !best_out)
+        return mp_fail_noctx(MP_EINVAL, "mp_posterior_init_noalloc: NULL loglik, post_out or best_out");
+    if (n <= 0 || n > NA_MAX_N)
+        return mp_fail_noctx(MP_EINVAL, "mp_posterior_init_noalloc: n = %lld outside [1, %lld] (the fixed scratch "
+                                        "holds %d block partials)", (long long)n, (long long)NA_MAX_N, NA_MAX_BLOCKS);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) return na_fail(MP_ECUDA, "no current CUDA device");
+    if (e != cudaSuccess || dev < 0 || dev >= 64)
+        return mp_fail_noctx(MP_ECUDA, "mp_posterior_init_noalloc: no current CUDA device");
+    int rc;
+    if ((log_prior && (rc = na_check_ptr(log_prior, dev, "log_prior"))) ||
+        (rc = na_check_ptr(loglik, dev, "loglik")) || (rc = na_check_ptr(post_out, dev, "post_out")) ||
+        (rc = na_check_ptr(best_out, dev, "best_out")))
+        return rc;
     NaScratch* S = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mutex);
         if (!g_na_ready[dev]) {
             void* ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, mp_noalloc_scratch);
-            if (e != cudaSuccess || !ptr) return na_fail(MP_ECUDA, cudaGetErrorString(e));
+            if (e != cudaSuccess || !ptr)
+                return mp_fail_noctx(MP_ECUDA, "mp_posterior_init_noalloc: scratch lookup: %s", cudaGetErrorString(e));
             g_na_addr[dev] = ptr;
             g_na_ready[dev] = true;
         }
@@ -217,6 +247,7 @@ extern "C" int mp_posterior_init_noalloc(const double* log_prior, const float* l
     k_na_final<<<1, 1024, 0, st>>>(nb, S, best_out);
     k_na_normalise<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, post_out, S);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return na_fail(MP_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        return mp_fail_noctx(MP_ECUDA, "mp_posterior_init_noalloc: launch: %s", cudaGetErrorString(e));
     return MP_OK;
 }

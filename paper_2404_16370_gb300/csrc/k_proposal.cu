@@ -361,8 +361,8 @@ struct mp_pn {
 namespace {
 
 int pn_fail(const char* what, cudaError_t e) {
-    fprintf(stderr, "mp_pn: %s: %s\n", what, cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
+    return mp_fail_noctx(e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA, "mp_pn: %s: %s", what,
+                         cudaGetErrorString(e));
 }
 
 #define PN_CUDA(x)                                   \
@@ -417,7 +417,7 @@ extern "C" {
 int mp_pn_sim_box_room(const float* boxes, int n_boxes, float half, float height, const float* poses, int64_t B,
                        const float* dirs, int P, float noise, uint64_t seed, float* out, void* cuda_stream) {
     if (n_boxes < 0 || B < 0 || P < 0 || (n_boxes > 0 && !boxes) || (B * P > 0 && (!poses || !dirs || !out)))
-        return MP_EINVAL;
+        return mp_fail_noctx(MP_EINVAL, "mp_pn_sim_box_room: invalid argument");
     if (B * P == 0) return MP_OK;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -429,8 +429,8 @@ int mp_pn_sim_box_room(const float* boxes, int n_boxes, float half, float height
 
 int mp_pn_create(mp_pn** netp, int n_points, int max_batch, float in_scale, const float scale[6],
                  const float offset[6], uint64_t seed, void* cuda_stream) {
-    if (!netp || n_points < 1 || max_batch < 1 || !(in_scale > 0.f) || !scale || !offset) return MP_EINVAL;
-    if ((int64_t)n_points * max_batch * C3 >= ((int64_t)1 << 31)) return MP_EINVAL;
+    if (!netp || n_points < 1 || max_batch < 1 || !(in_scale > 0.f) || !scale || !offset) return mp_fail_noctx(MP_EINVAL, "mp_pn_create: invalid argument");
+    if ((int64_t)n_points * max_batch * C3 >= ((int64_t)1 << 31)) return mp_fail_noctx(MP_EINVAL, "mp_pn_create: invalid argument");
     mp_pn* net = new mp_pn();
     net->P = n_points;
     net->Bmax = max_batch;
@@ -466,7 +466,7 @@ int mp_pn_create(mp_pn** netp, int n_points, int max_batch, float in_scale, cons
 }
 
 int mp_pn_destroy(mp_pn* net) {
-    if (!net) return MP_EINVAL;
+    if (!net) return mp_fail_noctx(MP_EINVAL, "mp_pn_destroy: invalid argument");
     void* bufs[] = {net->scale, net->offset, net->param, net->grad, net->am, net->av, net->xs, net->h1,
                     net->h2, net->h3, net->g, net->gi, net->h4, net->o, net->dO, net->dh4, net->dg, net->dh3,
                     net->dh2, net->dh1};
@@ -477,27 +477,27 @@ int mp_pn_destroy(mp_pn* net) {
 }
 
 int mp_pn_num_params(mp_pn* net, int64_t* n) {
-    if (!net || !n) return MP_EINVAL;
+    if (!net || !n) return mp_fail_noctx(MP_EINVAL, "mp_pn_num_params: invalid argument");
     *n = NPARAM;
     return MP_OK;
 }
 
 int mp_pn_get_params(mp_pn* net, float* out) {
-    if (!net || !out) return MP_EINVAL;
+    if (!net || !out) return mp_fail_noctx(MP_EINVAL, "mp_pn_get_params: invalid argument");
     PN_CUDA(cudaMemcpyAsync(out, net->param, sizeof(float) * NPARAM, cudaMemcpyDefault, net->stream));
     PN_CUDA(cudaStreamSynchronize(net->stream));
     return MP_OK;
 }
 
 int mp_pn_set_params(mp_pn* net, const float* in) {
-    if (!net || !in) return MP_EINVAL;
+    if (!net || !in) return mp_fail_noctx(MP_EINVAL, "mp_pn_set_params: invalid argument");
     PN_CUDA(cudaMemcpyAsync(net->param, in, sizeof(float) * NPARAM, cudaMemcpyDefault, net->stream));
     PN_CUDA(cudaStreamSynchronize(net->stream));
     return MP_OK;
 }
 
 int mp_pn_forward(mp_pn* net, const float* scans, int B, float* out) {
-    if (!net || !scans || !out || B < 1 || B > net->Bmax) return MP_EINVAL;
+    if (!net || !scans || !out || B < 1 || B > net->Bmax) return mp_fail_noctx(MP_EINVAL, "mp_pn_forward: invalid argument");
     int rc = forward(net, scans, B);
     if (rc) return rc;
     PN_CUDA(cudaMemcpyAsync(out, net->o, sizeof(float) * (size_t)B * NOUT, cudaMemcpyDefault, net->stream));
@@ -505,7 +505,7 @@ int mp_pn_forward(mp_pn* net, const float* scans, int B, float* out) {
 }
 
 int mp_pn_loss_grad(mp_pn* net, const float* scans, const float* targets, int B, float* loss_dev, float* grad_out) {
-    if (!net || !scans || !targets || !loss_dev || B < 1 || B > net->Bmax) return MP_EINVAL;
+    if (!net || !scans || !targets || !loss_dev || B < 1 || B > net->Bmax) return mp_fail_noctx(MP_EINVAL, "mp_pn_loss_grad: invalid argument");
     int rc = forward(net, scans, B);
     if (rc) return rc;
     cudaStream_t s = net->stream;
@@ -545,7 +545,7 @@ int mp_pn_loss_grad(mp_pn* net, const float* scans, const float* targets, int B,
 }
 
 int mp_pn_adam_step(mp_pn* net, float lr, float beta1, float beta2, float eps) {
-    if (!net) return MP_EINVAL;
+    if (!net) return mp_fail_noctx(MP_EINVAL, "mp_pn_adam_step: invalid argument");
     net->t += 1;
     const float c1 = 1.f / (1.f - powf(beta1, (float)net->t));
     const float c2 = 1.f / (1.f - powf(beta2, (float)net->t));
@@ -556,7 +556,7 @@ int mp_pn_adam_step(mp_pn* net, float lr, float beta1, float beta2, float eps) {
 }
 
 int mp_pn_sample(mp_pn* net, const float* mix, int64_t n, uint64_t seed, float* poses_out) {
-    if (!net || !mix || n < 0 || (n > 0 && !poses_out)) return MP_EINVAL;
+    if (!net || !mix || n < 0 || (n > 0 && !poses_out)) return mp_fail_noctx(MP_EINVAL, "mp_pn_sample: invalid argument");
     if (n == 0) return MP_OK;
     k_pn_sample<<<grid_for(n, 256), 256, 0, net->stream>>>(mix, n, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)),
                                                           net->scale, net->offset, poses_out);

@@ -10,7 +10,11 @@
 #include <new>
 #include <vector>
 
-static const char* g_null_ctx_msg = "null context";
+// Message of the last failure, on this thread, of a call that had no context
+// to keep it (a failed mp_init_map, a batch, the allocation-free posterior,
+// the proposal network): mp_last_error(NULL) returns it. The library prints
+// nothing.
+static thread_local char g_noctx_err[512];
 
 int mp_fail(mp_ctx* c, int code, const char* fmt, ...) {
     if (c) {
@@ -19,6 +23,14 @@ int mp_fail(mp_ctx* c, int code, const char* fmt, ...) {
         vsnprintf(c->err, sizeof(c->err), fmt, ap);
         va_end(ap);
     }
+    return code;
+}
+
+int mp_fail_noctx(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_noctx_err, sizeof(g_noctx_err), fmt, ap);
+    va_end(ap);
     return code;
 }
 
@@ -366,7 +378,7 @@ int mp_default_params(mp_params* p, int preset, int64_t n_particles) {
     return MP_OK;
 }
 
-const char* mp_last_error(const mp_ctx* ctx) { return ctx ? ctx->err : g_null_ctx_msg; }
+const char* mp_last_error(const mp_ctx* ctx) { return ctx ? ctx->err : g_noctx_err; }
 
 // Everything of a context but its map: scan buffers, step scalars, staging,
 // events.
@@ -408,22 +420,25 @@ static int ctx_setup(mp_ctx* c) {
 }
 
 int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* p, void* cuda_stream) {
-    if (!out) return MP_EINVAL;
+    if (!out) return mp_fail_noctx(MP_EINVAL, "mp_init_map: NULL ctx pointer");
     *out = nullptr;
     mp_ctx* c = new (std::nothrow) mp_ctx();
-    if (!c) return MP_ENOMEM;
+    if (!c) return mp_fail_noctx(MP_ENOMEM, "mp_init_map: out of host memory");
     memset((void*)c, 0, sizeof(*c));
     int rc = MP_OK;
     if (!xyz || n_map <= 0 || !p) {
-        mp_fail(c, MP_EINVAL, "mp_init_map: empty map or NULL argument");
         destroy(c);
-        return MP_EINVAL;
+        return mp_fail_noctx(MP_EINVAL, "mp_init_map: empty map or NULL argument");
     }
     if (n_map >= ((int64_t)1 << 31)) {
         destroy(c);
-        return MP_EINVAL;
+        return mp_fail_noctx(MP_EINVAL, "mp_init_map: %lld map points (at most 2^31 - 1)", (long long)n_map);
     }
-    if ((rc = check_params(c, p))) { destroy(c); return rc; }
+    if ((rc = check_params(c, p))) {
+        mp_fail_noctx(rc, "mp_init_map: %s", c->err);
+        destroy(c);
+        return rc;
+    }
     c->p = *p;
     c->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&c->device);
@@ -447,7 +462,7 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
     } while (0);
     if (xyz_dev) cudaFree(xyz_dev);
     if (rc) {
-        fprintf(stderr, "mp_init_map: %s\n", c->err);
+        mp_fail_noctx(rc, "mp_init_map: %s", c->err);
         destroy(c);
         return rc;
     }
@@ -456,11 +471,12 @@ int mp_init_map(mp_ctx** out, const float* xyz, int64_t n_map, const mp_params* 
 }
 
 int mp_init_map_shared(mp_ctx** out, mp_ctx* src, const mp_params* p, void* cuda_stream) {
-    if (!out) return MP_EINVAL;
+    if (!out) return mp_fail_noctx(MP_EINVAL, "mp_init_map_shared: NULL ctx pointer");
     *out = nullptr;
-    if (!src || !p || !src->map_refs || src->n_map <= 0) return MP_EINVAL;
+    if (!src || !p || !src->map_refs || src->n_map <= 0)
+        return mp_fail_noctx(MP_EINVAL, "mp_init_map_shared: NULL argument or a source context without a map");
     mp_ctx* c = new (std::nothrow) mp_ctx();
-    if (!c) return MP_ENOMEM;
+    if (!c) return mp_fail_noctx(MP_ENOMEM, "mp_init_map_shared: out of host memory");
     memset((void*)c, 0, sizeof(*c));
     int rc = check_params(c, p);
     const mp_params& q = src->p;
@@ -473,7 +489,7 @@ int mp_init_map_shared(mp_ctx** out, mp_ctx* src, const mp_params* p, void* cuda
         rc = mp_fail(c, MP_EINVAL, "mp_init_map_shared: the source context belongs to device %d, not %d", src->device,
                      c->device);
     if (rc) {
-        fprintf(stderr, "%s\n", c->err);
+        mp_fail_noctx(rc, "%s", c->err);
         destroy(c);
         return rc;
     }
@@ -498,7 +514,7 @@ int mp_init_map_shared(mp_ctx** out, mp_ctx* src, const mp_params* p, void* cuda
     src->map_refs->fetch_add(1);
     c->map_refs = src->map_refs;
     if ((rc = ctx_setup(c))) {
-        fprintf(stderr, "mp_init_map_shared: %s\n", c->err);
+        mp_fail_noctx(rc, "mp_init_map_shared: %s", c->err);
         destroy(c);
         return rc;
     }
@@ -507,6 +523,7 @@ int mp_init_map_shared(mp_ctx** out, mp_ctx* src, const mp_params* p, void* cuda
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         rc = mp_cuda_check(c, e, "mp_init_map_shared");
+        mp_fail_noctx(rc, "%s", c->err);
         destroy(c);
         return rc;
     }

@@ -110,8 +110,8 @@ void batch_free(mp_batch* b) {
 }
 
 int batch_err(cudaError_t e, const char* what) {
-    fprintf(stderr, "mp_batch: %s: %s\n", what, cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
+    return mp_fail_noctx(e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA, "mp_batch: %s: %s", what,
+                         cudaGetErrorString(e));
 }
 
 #define B_CUDA(x)                                        \
@@ -215,24 +215,20 @@ extern "C" {
 
 int mp_batch_create(mp_batch** out, mp_ctx* const* ctxs, int n, const int32_t* n_scan,
                     const float* const* tune_scans, void* cuda_stream) {
-    if (!out || !ctxs || n < 1 || !n_scan || !cuda_stream) return MP_EINVAL;
+    if (!out || !ctxs || n < 1 || !n_scan || !cuda_stream)
+        return mp_fail_noctx(MP_EINVAL, "mp_batch_create: NULL argument or no instance");
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         mp_ctx* c = ctxs[i];
-        if (!c || c->n == 0 || c->timing || n_scan[i] < 1 || n_scan[i] > c->p.max_scan) {
-            fprintf(stderr, "mp_batch_create: instance %d: uninitialised, timed, or a scan size outside "
-                            "[1, max_scan]\n", i);
-            return MP_EINVAL;
-        }
-        if (c->precision != MP_PREC_FP32) {
-            fprintf(stderr, "mp_batch_create: instance %d: batched instances use the FP32 likelihood\n", i);
-            return MP_EINVAL;
-        }
+        if (!c || c->n == 0 || c->timing || n_scan[i] < 1 || n_scan[i] > c->p.max_scan)
+            return mp_fail_noctx(MP_EINVAL, "mp_batch_create: instance %d: uninitialised, timed, or a scan size "
+                                            "outside [1, max_scan]", i);
+        if (c->precision != MP_PREC_FP32)
+            return mp_fail_noctx(MP_EINVAL, "mp_batch_create: instance %d: batched instances use the FP32 "
+                                            "likelihood", i);
         for (int k = 0; k < i; ++k)
-            if (ctxs[k] == c) {
-                fprintf(stderr, "mp_batch_create: instances %d and %d are the same context\n", k, i);
-                return MP_EINVAL;
-            }
+            if (ctxs[k] == c)
+                return mp_fail_noctx(MP_EINVAL, "mp_batch_create: instances %d and %d are the same context", k, i);
     }
     mp_batch* b = new mp_batch();
     b->n = n;
@@ -329,17 +325,15 @@ int mp_batch_create(mp_batch** out, mp_ctx* const* ctxs, int n, const int32_t* n
 }
 
 int mp_batch_step(mp_batch* b, const float* const* scans, const double* odom_T, const double* odom_cov) {
-    if (!b || !scans) return MP_EINVAL;
+    if (!b || !scans) return mp_fail_noctx(MP_EINVAL, "mp_batch_step: NULL batch or scans");
     const int p = (int)(b->steps & 1);
     B_CUDA(cudaEventSynchronize(b->done[p]));   // the launch that last read slot p
     int rc;
     for (int i = 0; i < b->n; ++i) {
         mp_ctx* c = b->G.ctx[i];
-        if (!scans[i]) return MP_EINVAL;
-        if (c->nbr_cur != (b->nbr_cur0[i] ^ p)) {
-            fprintf(stderr, "mp_batch_step: instance %d was stepped outside the batch\n", i);
-            return MP_EINVAL;
-        }
+        if (!scans[i]) return mp_fail_noctx(MP_EINVAL, "mp_batch_step: NULL scan of instance %d", i);
+        if (c->nbr_cur != (b->nbr_cur0[i] ^ p))
+            return mp_fail_noctx(MP_EINVAL, "mp_batch_step: instance %d was stepped outside the batch", i);
         memcpy(b->scans + p * b->scan_floats + b->G.scan_off[i], scans[i], sizeof(float) * 3 * (size_t)b->G.n_scan[i]);
         if ((rc = mp_set_odometry(c, odom_T ? odom_T + 16 * i : nullptr, odom_cov ? odom_cov + 36 * i : nullptr)))
             return rc;
@@ -364,13 +358,13 @@ int mp_batch_step(mp_batch* b, const float* const* scans, const double* odom_T, 
 }
 
 int mp_batch_split(mp_batch* b, int i, int* split) {
-    if (!b || !split || i < 0 || i >= b->n) return MP_EINVAL;
+    if (!b || !split || i < 0 || i >= b->n) return mp_fail_noctx(MP_EINVAL, "mp_batch_split: invalid argument");
     *split = b->G.ctx[i]->lk_split > 1 ? b->G.ctx[i]->lk_split : 1;
     return MP_OK;
 }
 
 int mp_stream_create(void** stream) {
-    if (!stream) return MP_EINVAL;
+    if (!stream) return mp_fail_noctx(MP_EINVAL, "mp_stream_create: invalid argument");
     cudaStream_t s = nullptr;
     B_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     *stream = (void*)s;
@@ -378,13 +372,13 @@ int mp_stream_create(void** stream) {
 }
 
 int mp_stream_destroy(void* stream) {
-    if (!stream) return MP_EINVAL;
+    if (!stream) return mp_fail_noctx(MP_EINVAL, "mp_stream_destroy: invalid argument");
     B_CUDA(cudaStreamDestroy((cudaStream_t)stream));
     return MP_OK;
 }
 
 int mp_batch_destroy(mp_batch* b) {
-    if (!b) return MP_EINVAL;
+    if (!b) return mp_fail_noctx(MP_EINVAL, "mp_batch_destroy: invalid argument");
     batch_free(b);
     return MP_OK;
 }

@@ -453,6 +453,8 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned expected, long l
 // host-side helpers
 // ---------------------------------------------------------------------------
 int mp_fail(mp_ctx* c, int code, const char* fmt, ...);
+// records the message of a failure without a context (mp_last_error(NULL))
+int mp_fail_noctx(int code, const char* fmt, ...);
 int mp_cuda_check(mp_ctx* c, cudaError_t e, const char* what);
 #define MP_CUDA(ctx, call)                                              \
     do {                                                                \

@@ -170,7 +170,7 @@ def mp_init_map(xyz, params: mp_params, cuda_stream=None):
     n = int(xyz.shape[0])
     rc = lib().mp_init_map(C.byref(ctx), ptr, n, C.byref(params), C.c_void_p(cuda_stream) if cuda_stream else None)
     if rc != MP_OK:
-        raise MPError(rc, "mp_init_map failed (details on stderr)")
+        raise MPError(rc, mp_last_error(None))
     return ctx
 
 
@@ -179,7 +179,7 @@ def mp_init_map_shared(src, params: mp_params, cuda_stream=None):
     ctx = C.c_void_p()
     rc = lib().mp_init_map_shared(C.byref(ctx), src, C.byref(params), C.c_void_p(cuda_stream) if cuda_stream else None)
     if rc != MP_OK:
-        raise MPError(rc, "mp_init_map_shared failed (details on stderr)")
+        raise MPError(rc, mp_last_error(None))
     return ctx
 
 
@@ -316,14 +316,32 @@ def mp_debug_set(ctx, what, value):
     _check(L.mp_debug_set(ctx, int(what), int(value)), ctx)
 
 
+def _device_tensor(x, name):
+    """x as a torch tensor on the current CUDA device, else TypeError: the
+    allocation-free entry point dereferences its pointers as device memory of
+    the current device (the library refuses anything else too)."""
+    if not (hasattr(x, "data_ptr") and hasattr(x, "is_cuda")):
+        raise TypeError(f"{name}: expected a CUDA tensor, got {type(x).__name__}")
+    if not x.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor, got one on {x.device}")
+    import torch
+    if x.device.index != torch.cuda.current_device():
+        raise TypeError(f"{name}: tensor on {x.device}, the current device is cuda:{torch.cuda.current_device()}")
+    return x
+
+
 def mp_posterior_init_noalloc(log_prior, loglik, post_out, best_out, cuda_stream=None):
-    """Device tensors in, device tensors out; allocates nothing (see the C header)."""
+    """Device tensors of the current device in, device tensors out; allocates
+    nothing (see the C header). log_prior may be None (uniform prior)."""
     L = lib()
     if not getattr(L, "_noalloc_declared", False):
         L.mp_posterior_init_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                                 C.c_void_p]
         L.mp_posterior_init_noalloc.restype = C.c_int
         L._noalloc_declared = True
+    for x, name in ((log_prior, "log_prior"), (loglik, "loglik"), (post_out, "post_out"), (best_out, "best_out")):
+        if x is not None or name != "log_prior":
+            _device_tensor(x, name)
     n = int(loglik.shape[0])
     lp, klp = _ptr(log_prior, np.float64, size=n)
     ll, kll = _ptr(loglik, np.float32, size=n)
@@ -331,7 +349,7 @@ def mp_posterior_init_noalloc(log_prior, loglik, post_out, best_out, cuda_stream
     bo, kbo = _ptr(best_out, np.int64, size=1, out=True)
     rc = L.mp_posterior_init_noalloc(lp, ll, n, po, bo, C.c_void_p(cuda_stream) if cuda_stream else None)
     if rc != MP_OK:
-        raise MPError(rc, "mp_posterior_init_noalloc failed (details on stderr)")
+        raise MPError(rc, mp_last_error(None))
 
 
 def mp_kernel_launches(ctx) -> int:
@@ -377,7 +395,7 @@ def _pn_lib():
 
 def _pn_check(rc, what):
     if rc != MP_OK:
-        raise MPError(rc, f"{what} failed (details on stderr)")
+        raise MPError(rc, f"{what} failed: {mp_last_error(None)}")
 
 
 def _dev(t, shape=None, numel=None):
@@ -519,7 +537,7 @@ def mp_batch_create(ctxs, n_scan, cuda_stream, tune_scans=None):
     rc = _batch_lib().mp_batch_create(C.byref(b), arr, n, ns.ctypes.data_as(C.c_void_p), tp,
                                       C.c_void_p(cuda_stream))
     if rc != MP_OK:
-        raise MPError(rc, "mp_batch_create failed (details on stderr)")
+        raise MPError(rc, mp_last_error(None))
     _batch_nscan[b.value] = [int(v) for v in ns]
     return b
 
@@ -551,14 +569,14 @@ def mp_batch_step(batch, scans, odom_T=None, odom_cov=None):
     rc = _batch_lib().mp_batch_step(batch, ptrs, None if T is None else T.ctypes.data_as(C.c_void_p),
                                     None if Q is None else Q.ctypes.data_as(C.c_void_p))
     if rc != MP_OK:
-        raise MPError(rc, "mp_batch_step failed (details on stderr)")
+        raise MPError(rc, mp_last_error(None))
 
 
 def mp_batch_split(batch, i) -> int:
     s = C.c_int()
     rc = _batch_lib().mp_batch_split(batch, int(i), C.byref(s))
     if rc != MP_OK:
-        raise MPError(rc, "mp_batch_split failed")
+        raise MPError(rc, mp_last_error(None))
     return int(s.value)
 
 
@@ -566,7 +584,7 @@ def mp_batch_destroy(batch):
     _batch_nscan.pop(batch.value if isinstance(batch, C.c_void_p) else batch, None)
     rc = _batch_lib().mp_batch_destroy(batch)
     if rc != MP_OK:
-        raise MPError(rc, "mp_batch_destroy failed")
+        raise MPError(rc, mp_last_error(None))
 
 
 def mp_stream_create() -> int:

@@ -44,7 +44,14 @@ def test_library_loads_and_reports_without_gpu(built):
     L = mp.lib()
     for n in declared():
         assert hasattr(L, n)
-    assert mp.mp_last_error(None) == "null context"
+    # a call without a context records its message for mp_last_error(NULL)
+    import ctypes as C
+    ctx = C.c_void_p()
+    assert L.mp_init_map(C.byref(ctx), None, 0, C.byref(mp.mp_default_params()), None) == mp.MP_EINVAL
+    assert "mp_init_map: empty map or NULL argument" in mp.mp_last_error(None)
+    L.mp_posterior_init_noalloc.argtypes = [C.c_void_p] * 2 + [C.c_int64] + [C.c_void_p] * 3
+    assert L.mp_posterior_init_noalloc(None, None, 4, None, None, None) == mp.MP_EINVAL
+    assert "NULL loglik" in mp.mp_last_error(None)
     p = mp.mp_default_params(mp.MP_PRESET_OUTDOOR, 1 << 20)
     assert p.n_buckets_log2 == 20 and p.K == 32 and abs(p.nnf_res - 0.2) < 1e-7
     with pytest.raises(mp.MPError):

@@ -56,12 +56,6 @@ def test_outputs_must_have_the_buffer_type_and_be_writeable_in_place():
         mp.mp_get_buffer(None, mp.MP_BUF_GN, out=np.zeros((4, 29), np.float64))
     with pytest.raises(TypeError):
         mp.mp_get_buffer(None, mp.MP_BUF_GN, out=np.zeros((29, 4), np.float32).T)   # not C-contiguous
-    with pytest.raises(TypeError):
-        mp.mp_posterior_init_noalloc(torch.zeros(4, dtype=torch.float64), torch.zeros(4, dtype=torch.float32),
-                                     torch.zeros(4, dtype=torch.float32), torch.zeros(1, dtype=torch.int64))
-    with pytest.raises(ValueError):
-        mp.mp_posterior_init_noalloc(torch.zeros(4, dtype=torch.float64), torch.zeros(4, dtype=torch.float32),
-                                     torch.zeros(3, dtype=torch.float64), torch.zeros(1, dtype=torch.int64))
 
 
 def test_batched_scans_match_the_batch():
@@ -98,3 +92,22 @@ def test_proposal_tensors_are_checked():
     with pytest.raises(ValueError):
         mp.mp_pn_sim_box_room(torch.zeros((3, 7)), 5.0, 3.0, torch.zeros((2, 7)), torch.zeros((8, 3)), 0.0, 0,
                               torch.zeros((2, 9, 3)))
+
+
+def test_noalloc_refuses_host_arrays_before_any_call():
+    """The allocation-free posterior dereferences its pointers as device
+    memory: numpy arrays and CPU tensors are refused by the binding (the C
+    entry point also refuses them, by cudaPointerGetAttributes)."""
+    n = 16
+    ll_np = np.zeros(n, np.float32)
+    post_np = np.zeros(n, np.float64)
+    best_np = np.zeros(1, np.int64)
+    with pytest.raises(TypeError):
+        mp.mp_posterior_init_noalloc(None, ll_np, post_np, best_np)
+    ll_t = torch.zeros(n, dtype=torch.float32)
+    post_t = torch.zeros(n, dtype=torch.float64)
+    best_t = torch.zeros(1, dtype=torch.int64)
+    with pytest.raises(TypeError):
+        mp.mp_posterior_init_noalloc(None, ll_t, post_t, best_t)
+    with pytest.raises(TypeError):
+        mp.mp_posterior_init_noalloc(torch.zeros(n, dtype=torch.float64), ll_t, post_t, best_t)
