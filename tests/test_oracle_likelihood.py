@@ -211,3 +211,42 @@ def test_gn_solve_matches_numpy(oracle):
             continue
         M = Hf[i] + P.lam * np.diag(np.diag(Hf[i])) + P.eps_damp * np.eye(6)
         assert np.allclose(psi[i], np.linalg.solve(M, -b[i]), rtol=1e-10, atol=1e-12)
+
+
+def test_ambiguity_band_bounds_the_other_decision(oracle, room_case):
+    """amb / ambabs: an inlier decision within amb_tol * c_max of the
+    threshold is ambiguous, and ambabs bounds how far each output moves if
+    the other decision is taken. Straddle one pair's cost c_j with two
+    thresholds c_j (1 +- d): the pair is an inlier under the first and an
+    outlier under the second, no other pair changes side (the band holds only
+    it), and the outputs of the two runs differ by exactly that pair's terms,
+    which both runs report in ambabs."""
+    c = room_case
+    pairs = oracle.likelihood_pairs(c["map"], c["pose"], c["scan"], c["sn"], c["sv"], c["P"])
+    costs = pairs["c"][pairs["m"] >= 0]
+    costs = np.sort(costs)
+    gaps = np.diff(costs)
+    # a pair whose cost is well separated from its neighbours and in the middle of the range
+    cand = [k for k in range(1, len(costs) - 1) if min(gaps[k - 1], gaps[k]) > 1e-3 * costs[k] and 0.5 < costs[k] < 50]
+    assert cand, "no isolated pair cost"
+    cj = costs[cand[len(cand) // 2]]
+    d = 1e-6
+    tol = 1e-4   # band half-width (relative to c_max): holds c_j under both thresholds, no other pair
+    out = {}
+    for side, cm in (("in", cj * (1 + d)), ("out", cj * (1 - d))):
+        P = oracle.Params(**{**c["P"].__dict__, "c_max": cm})
+        out[side] = oracle.likelihood(c["map"], c["pose"][None], c["scan"], c["sn"], c["sv"], P, amb_tol=tol)
+        assert out[side]["amb"][0] == 1
+    A, B = out["in"], out["out"]
+    assert A["n_in"][0] == B["n_in"][0] + 1
+    dH = np.abs(A["H"][0] - B["H"][0])
+    db = np.abs(A["b"][0] - B["b"][0])
+    for r in (A, B):
+        assert np.allclose(r["ambabs"][0, :21], dH, rtol=1e-9, atol=1e-12 * np.abs(A["H"]).max())
+        assert np.allclose(r["ambabs"][0, 21:27], db, rtol=1e-9, atol=1e-12 * np.abs(A["b"]).max())
+    assert dH.max() > 0 and db.max() > 0
+    # log p = -(sum of inlier costs) - c_max (outliers): with N_out outliers
+    # under the first threshold the two differ by -d c_j (2 N_out + 1)
+    n_out = int(c["sv"].sum()) - int(A["n_in"][0])
+    assert np.isclose(A["loglik"][0] - B["loglik"][0], -d * cj * (2 * n_out + 1), rtol=1e-6, atol=1e-9)
+    assert np.isclose(A["ambabs"][0, 27], d * cj, rtol=1e-6) and np.isclose(B["ambabs"][0, 27], d * cj, rtol=1e-6)

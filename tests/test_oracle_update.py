@@ -221,3 +221,17 @@ def test_uniform_init(oracle):
     full = oracle.init_uniform(n, [-1, -1, -1, -np.pi, -np.pi, -np.pi], [1, 1, 1, np.pi, np.pi, np.pi], 3)
     R = Rotation.from_quat(full[:, :4]).as_matrix().mean(0)
     assert np.abs(R).max() < 0.03            # Haar measure: E[R] = 0
+
+
+def test_philox_known_answers(oracle):
+    """Philox-4x32-10 against the known-answer vectors its authors publish
+    (tests/golden/philox4x32_10_kat.json): a swapped output word, a wrong
+    multiplier or key schedule fails here, which statistics would not show."""
+    import json
+    import os
+    kat = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.json")))
+    for v in kat["vectors"]:
+        ctr = [int(w, 16) for w in v["ctr"]]
+        key = [int(w, 16) for w in v["key"]]
+        out = [int(w) for w in oracle.philox(ctr, key)]
+        assert out == [int(w, 16) for w in v["out"]], v
