@@ -50,9 +50,8 @@ LK_FLOPS_PER_PAIR = 222
 # One random 32-byte NNF sector from DRAM per pair: the HBM bound of the
 # likelihood while particles are spread (the 0.5 GB grid does not fit in L2).
 LK_SECTOR_BYTES_PER_PAIR = 32
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 (non-tensor)
+# Localisation criterion of the representative state (as in the box-room trials)
+LOC_DIST_M, LOC_ANG_DEG = 0.3, 3.0
 
 
 def measured_peaks():
@@ -65,13 +64,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def stage_bounds_ms(n, K, pairs_per_step, hbm_gbs):
+def stage_bounds_ms(n, K, pairs_per_step, hbm_gbs, fp32_tflops, fp64_tflops):
     """Lower bound of each stage's time per step: max(bytes / HBM peak, flops /
     ALU peak) with the algorithmic bytes and flops of one step (per particle
-    unless stated). FP64 stages use the FP64 peak."""
+    unless stated). FP64 stages use the FP64 peak. Peaks: the measured copy
+    bandwidth and the measured FP32 / FP64 FMA rates."""
     bw = hbm_gbs * 1e9
-    f32 = ALU_PEAK_TFLOPS * 1e12
-    f64 = FP64_PEAK_TFLOPS * 1e12
+    f32 = fp32_tflops * 1e12
+    f64 = fp64_tflops * 1e12
     C = K
     b = {
         # pose in/out (2 x 32 B) + Philox noise
@@ -221,13 +221,14 @@ def traffic_from_profile():
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_setup(wl, n_sample):
+def oracle_setup(wl, n_sample, nthreads=0, svgd_precond=0):
     from oracle import oracle as O
     P = O.Params.outdoor(N_PARTICLES)
+    P.svgd_precond = int(svgd_precond)
     t = time.perf_counter()
-    om = O.OracleMap(wl.map_points, P)
+    om = O.OracleMap(wl.map_points, P, nthreads=nthreads)
     init_s = time.perf_counter() - t
-    f = O.OracleFilter(om, P, wl.particles[:n_sample].copy())
+    f = O.OracleFilter(om, P, wl.particles[:n_sample].copy(), nthreads=nthreads)
     return O, f, init_s
 
 
@@ -237,14 +238,39 @@ def oracle_step_time(f, wl, s):
     return time.perf_counter() - t
 
 
-def cpu_baseline(wl, n_sample=4096):
-    O, f, _ = oracle_setup(wl, n_sample)
-    dt = oracle_step_time(f, wl, 0)
+def cpu_baseline(wl, n_sample=4096, n_sample_one=512):
+    """The FP64 oracle as it stands on this host's cores, with all cores and
+    with one thread: one step of the paper-scale workload on a particle
+    sample (full scan and map), extrapolated linearly to 2^20 particles, and
+    the 4096-particle box-room workload (512-point scan, 10 steps) in full."""
+    from oracle import oracle as O
+    from paper_2404_16370_gb300 import synth
     cores = os.cpu_count()
-    steps_s = 1.0 / (dt * N_PARTICLES / n_sample)
-    return {"value": steps_s, "unit": "steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"one FP64 oracle step on {n_sample} of the 2^20 particles (full 8192-point scan, full 1M-point "
-                      f"map; {dt:.2f} s), extrapolated linearly to 2^20 particles"}
+    P = O.Params.outdoor(N_PARTICLES)
+    om = O.OracleMap(wl.map_points, P, nthreads=cores)
+    c2 = {}
+    for label, nt, ns in (("all_cores", cores, n_sample), ("one_thread", 1, n_sample_one)):
+        f = O.OracleFilter(om, P, wl.particles[:ns].copy(), nthreads=nt)
+        dt = oracle_step_time(f, wl, 0)
+        c2[label] = {"threads": nt, "sample_particles": ns, "s_per_sampled_step": round(dt, 3),
+                     "steps_per_s_extrapolated": 1.0 / (dt * N_PARTICLES / ns)}
+    box = synth.box_room_workload(n_particles=4096, n_steps=10)
+    Pb = O.Params.box_room(4096)
+    c1 = {}
+    for label, nt in (("all_cores", cores), ("one_thread", 1)):
+        f = O.OracleFilter(O.OracleMap(box.map_points, Pb, nthreads=nt), Pb, box.particles.copy(), nthreads=nt)
+        t = time.perf_counter()
+        for s in range(10):
+            f.step(box.scans[s], box.odom[s], box.odom_cov[s])
+        dt = time.perf_counter() - t
+        c1[label] = {"threads": nt, "steps": 10, "s": round(dt, 3), "steps_per_s": 10 / dt}
+    return {"value": c2["all_cores"]["steps_per_s_extrapolated"], "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"one FP64 oracle step of this workload on {n_sample} of the 2^20 particles with {cores} threads "
+                      f"(full 8192-point scan, full 1M-point map; {c2['all_cores']['s_per_sampled_step']} s), "
+                      f"extrapolated linearly to 2^20 particles",
+            "paper_scale_sampled": c2,
+            "box_room_full": {"workload": "10x10x3 m box room, 4096 particles, 512-point scan, K=16, 10 steps, "
+                                          "run in full", **c1}}
 
 
 def run_reference(args):
@@ -254,7 +280,7 @@ def run_reference(args):
     n_sample = args.sample
     n_steps = args.warmup + args.steps
     wl = make_workload(max(n_steps, KIDNAP_WINDOW[1]) if times_after_kidnap(args) else n_steps)
-    O, f, init_s = oracle_setup(wl, n_sample)
+    O, f, init_s = oracle_setup(wl, n_sample, nthreads=os.cpu_count(), svgd_precond=args.svgd_precond)
     for s in range(args.warmup):
         oracle_step_time(f, wl, s)
     times = [oracle_step_time(f, wl, args.warmup + k) for k in range(args.steps)]
@@ -262,37 +288,89 @@ def run_reference(args):
     value = 1.0 / (dt * N_PARTICLES / n_sample)
     sample = (f"{n_sample} of the 2^20 particles per step (full scan and map), {dt:.2f} s per sampled step, "
               f"extrapolated linearly to 2^20 particles")
+    extrap = (f"extrapolated: {args.steps} timed oracle steps on a {n_sample}-particle sample "
+              f"({dt:.3f} s each), scaled linearly by 2^20 / {n_sample}")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_desc(),
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "value_kind": extrap, "ms_per_step_kind": extrap,
+           "sampled": {"particles": n_sample, "s_per_step": dt, "steps": args.steps},
+           "config": {**workload_desc(), "svgd_reading": SVGD_READINGS[args.svgd_precond]},
            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
+SVGD_READINGS = {0: "Eq. 6 as printed", 1: "preconditioned repulsion (opt-in reading, not the printed update)"}
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def random_read_probe(torch, mp, n_words, stream):
-    """Context for the sector roofline: the rate of independent, uniformly
-    random 4-byte reads over a buffer the size of the NNF grid (each fetches
-    one 32-byte DRAM sector), outside the timed region. The likelihood's
-    lookups are not uniform (consecutive points of a particle fall in nearby
-    voxels, often in the same DRAM row), so this is a reference below it, not a
-    ceiling; the roofline's peak stays the measured copy bandwidth."""
+def device_ceilings(torch, mp, n_words, stream):
+    """Ceilings measured on this GPU, outside the timed region: SM count (device
+    query), FP32 and FP64 FMA rates (microbenchmark: 8 CTAs of 256 threads per
+    SM, 16 independent FMA chains per thread; FP32 scalar and packed pairs, the
+    larger taken) and the rate of random 32-byte sectors (independent random
+    4-byte reads over a buffer the size of the NNF grid, 16 in flight per
+    thread)."""
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    out = {"sm_count": sms, "l2_bytes": getattr(props, "L2_cache_size", None)}
+    cs = stream.cuda_stream
     try:
-        words = torch.zeros(int(n_words), dtype=torch.int32, device=torch.cuda.current_device())
-        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        blocks, reads = 8 * sms, 256
-        ms = mp.mp_probe_random_reads(words, blocks, reads, repeats=5, cuda_stream=stream.cuda_stream)
-        n_reads = blocks * 256 * reads
+        rates = {}
+        for name, kind, iters in (("fp32", mp.MP_FMA_FP32, 65536), ("fp32x2", mp.MP_FMA_FP32X2, 65536),
+                                  ("fp64", mp.MP_FMA_FP64, 2048)):
+            ms, flops = mp.mp_probe_fma_rate(kind, 8 * sms, iters, repeats=3, cuda_stream=cs)
+            rates[name] = flops / (ms * 1e-3) / 1e12
+        out["fma_tflops"] = rates
+        out["fp32_tflops"] = max(rates["fp32"], rates["fp32x2"])
+        out["fp64_tflops"] = rates["fp64"]
+    except Exception as e:   # no probe library: derived FP32 figure, nominal FP64
+        out["fma_error"] = str(e)
+        out["fp32_tflops"] = sms * 128 * 2 * 2.07e9 / 1e12
+        out["fp64_tflops"] = 1.25
+    try:
+        words = torch.zeros(int(n_words), dtype=torch.int32, device=dev)
+        ms, n_reads = mp.mp_probe_random_reads(words, 8 * sms, 2048, repeats=5, cuda_stream=cs)
         del words
-        return {"buffer_bytes": 4 * int(n_words), "reads_per_run": n_reads, "ms_per_run": ms,
-                "reads_per_s": n_reads / (ms / 1e3), "sector_gbs": n_reads * 32 / (ms / 1e3) / 1e9,
-                "method": "mp_probe_random_reads: independent LCG indices, 8 CTAs of 256 threads per SM"}
-    except Exception as e:   # a measurement aid only
-        return {"error": str(e)}
+        out["random_sectors"] = {"buffer_bytes": 4 * int(n_words), "reads_per_run": n_reads, "ms_per_run": ms,
+                                 "reads_per_s": n_reads / (ms / 1e3), "sector_gbs": n_reads * 32 / (ms / 1e3) / 1e9}
+    except Exception as e:
+        out["random_sectors"] = {"error": str(e)}
+    return out
+
+
+def accuracy_summary(errs, warmup, n_steps, after):
+    """Errors of the representative state against the ground truth, per step
+    ((rotation angle in rad, distance in m), as localise.pose_errors gives
+    them), summarised per timed window; a step is localised when both are
+    within 0.3 m and 3 degrees."""
+    ang = np.rad2deg(np.array([e[0] for e in errs]))
+    dist = np.array([e[1] for e in errs])
+    ok = (dist <= LOC_DIST_M) & (ang <= LOC_ANG_DEG)
+
+    def window(lo, hi):
+        hi = min(hi, len(errs))
+        if hi <= lo:
+            return None
+        return {"steps": f"{lo}-{hi - 1}", "localised_fraction": float(ok[lo:hi].mean()),
+                "median_dist_m": float(np.median(dist[lo:hi])), "median_angle_deg": float(np.median(ang[lo:hi]))}
+
+    def first(lo):
+        hit = np.nonzero(ok[lo:])[0]
+        return int(lo + hit[0]) if len(hit) else None
+
+    out = {"criterion": f"{LOC_DIST_M} m and {LOC_ANG_DEG} deg", "steps_run": len(errs), "first_localised_step": first(0),
+           "window_timed": window(warmup, n_steps), "last_step": {"step": len(errs) - 1, "dist_m": float(dist[-1]),
+                                                                  "angle_deg": float(ang[-1])}}
+    if after:
+        out["first_localised_after_kidnap"] = first(50)
+        out["window_after_kidnap"] = window(*KIDNAP_WINDOW)
+    return out
 
 
 def run_gpu(args):
@@ -300,13 +378,16 @@ def run_gpu(args):
     world, rank, local = dist_setup("nccl")
     torch.cuda.set_device(local)
     from paper_2404_16370_gb300 import mp
+    from paper_2404_16370_gb300.localise import pose_errors
 
     n_steps = args.warmup + args.steps
     after_kidnap = times_after_kidnap(args)
-    wl = make_workload(max(n_steps, KIDNAP_WINDOW[1]) if after_kidnap else n_steps, init=args.init)
+    n_traj = max(n_steps, KIDNAP_WINDOW[1]) if after_kidnap else n_steps
+    wl = make_workload(n_traj, init=args.init)
     stream = torch.cuda.Stream()
     params = mp.mp_default_params(mp.MP_PRESET_OUTDOOR, N_PARTICLES)
     params.seed = 4 + rank
+    params.svgd_precond = int(args.svgd_precond)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx = mp.mp_init_map(wl.map_points, params, cuda_stream=stream.cuda_stream)
@@ -315,13 +396,15 @@ def run_gpu(args):
     scans_dev = [torch.from_numpy(s).to(f"cuda:{local}") for s in wl.scans]
     scans_pin = [torch.from_numpy(s).pin_memory() for s in wl.scans]
     torch.cuda.synchronize()
+    errs = []
 
     def run_steps(lo, hi, host=False):
         for s in range(lo, hi):
             sc = scans_pin[s] if host else scans_dev[s]
             mp.mp_step(ctx, sc if len(sc) else None, wl.odom[s], wl.odom_cov[s])
             if host:
-                mp.mp_get_posterior(ctx)          # D2H of the step's result (best pose, its probability)
+                best, _ = mp.mp_get_posterior(ctx)   # D2H of the step's result (best pose, its probability)
+                errs.append(pose_errors(best, wl.gt[s]))
 
     def barrier():
         rank_barrier(world)
@@ -372,7 +455,10 @@ def run_gpu(args):
                      "ms_per_step": 1e3 * t_after / (hi - lo), "best_prob_last_step": best_p_after,
                      "note": "kidnap at step 50 (identity odometry, 100x covariance, 3 blackout steps)"}
 
-        # ---- end to end through host (pinned) buffers: same steps again
+        # ---- end to end through host (pinned) buffers: the same steps again from
+        # the same particles (the same trajectory); the best pose read back every
+        # step gives the accuracy of the representative state. Steps after the
+        # timed window run untimed to the end of the trajectory.
         mp.mp_init_particles(ctx, N_PARTICLES, poses=wl.particles)
         run_steps(0, args.warmup, host=True)
         torch.cuda.synchronize()
@@ -381,58 +467,75 @@ def run_gpu(args):
         run_steps(args.warmup, n_steps, host=True)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
+        if after_kidnap:
+            run_steps(n_steps, n_traj, host=True)
         nnf_voxels = int(np.prod(mp.mp_map_info(ctx)["dims"].astype(np.int64)))
     finally:
         mp.mp_destroy(ctx)
-    probe = random_read_probe(torch, mp, nnf_voxels, stream) if rank == 0 else None
+    ceil = device_ceilings(torch, mp, nnf_voxels, stream) if rank == 0 else None
 
     if rank != 0:
         return
     steps_total = args.steps * world
     value = job_value(args.steps, world, t_max)
-    pairs_rank = pairs
     lk_ms = stage_ms["likelihood"]
     lk_runs = max(stage_runs["likelihood"], 1)
-    lk_flops = LK_FLOPS_PER_PAIR * pairs_rank
-    achieved = lk_flops / (lk_ms / 1e3) / 1e12 if lk_ms > 0 else None
+    pairs_launch = pairs / lk_runs
+    lk_s = lk_ms / 1e3 / lk_runs
     traffic = traffic_from_profile() if args.precision == "fp32" else None
     n_timed_scans = [len(wl.scans[s]) for s in range(args.warmup, n_steps)]
     h2d = int(np.mean([n * 12 for n in n_timed_scans])) + 16 * 8 + 36 * 8
     d2h = 7 * 4 + 8
-    nvalid_mean = pairs_rank / N_PARTICLES / max(lk_runs, 1)
+    nvalid_mean = pairs / N_PARTICLES / lk_runs
     hbm_gbs, hbm_src = measured_peaks()
-    pairs_step = pairs_rank / lk_runs
-    lk_s = lk_ms / 1e3 / lk_runs
-    sector_gbs = pairs_step * LK_SECTOR_BYTES_PER_PAIR / lk_s / 1e9 if lk_s > 0 else None
+    fp32_tf, fp64_tf = ceil["fp32_tflops"], ceil["fp64_tflops"]
+    # the likelihood's two bounds; the larger one grades the kernel
+    alu_bound_s = pairs_launch * LK_FLOPS_PER_PAIR / (fp32_tf * 1e12)
+    hbm_bound_s = pairs_launch * LK_SECTOR_BYTES_PER_PAIR / (hbm_gbs * 1e9)
+    sector_gbs = pairs_launch * LK_SECTOR_BYTES_PER_PAIR / lk_s / 1e9 if lk_s > 0 else None
+    alu_tflops = pairs_launch * LK_FLOPS_PER_PAIR / lk_s / 1e12 if lk_s > 0 else None
+    rs = ceil.get("random_sectors", {})
+    roof_hbm = {"bound": "hbm", "kernel": "k_likelihood", "achieved": sector_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": (sector_gbs / hbm_gbs) if sector_gbs else None, "traffic": traffic,
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json copy bandwidth)",
+                "model": "one random 32-byte NNF sector from DRAM per (particle, scan point) pair",
+                "bytes_per_pair": LK_SECTOR_BYTES_PER_PAIR, "pairs_per_launch": pairs_launch,
+                "avg_launch_ms": 1e3 * lk_s, "bound_ms": 1e3 * hbm_bound_s,
+                "random_sector_ceiling_gbs": rs.get("sector_gbs"),
+                "frac_of_random_sector_ceiling": (sector_gbs / rs["sector_gbs"]) if sector_gbs and rs.get("sector_gbs")
+                else None}
+    roof_alu = {"bound": "alu", "kernel": "k_likelihood", "achieved": alu_tflops, "peak": fp32_tf, "unit": "TFLOP/s",
+                "frac": (alu_tflops / fp32_tf) if alu_tflops else None, "traffic": traffic,
+                "peak_source": "measured (FP32 FMA microbenchmark, libmp_probe.so)" if "fma_error" not in ceil
+                else "derived: SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (the probe library did not load)",
+                "flops_per_pair": LK_FLOPS_PER_PAIR, "pairs_per_launch": pairs_launch, "avg_launch_ms": 1e3 * lk_s,
+                "bound_ms": 1e3 * alu_bound_s}
+    graded, other = (roof_hbm, roof_alu) if hbm_bound_s >= alu_bound_s else (roof_alu, roof_hbm)
     stage_meas = {k: v / max(stage_runs[k], 1) for k, v in stage_ms.items()}
-    bounds = stage_bounds_ms(N_PARTICLES, 32, pairs_step, hbm_gbs)
+    bounds = stage_bounds_ms(N_PARTICLES, 32, pairs_launch, hbm_gbs, fp32_tf, fp64_tf)
     step_bound = sum(bounds.values())
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}[args.precision],
         "data": "synthetic",
-        "config": {**workload_desc(round(nvalid_mean, 1)), "init": args.init, "precision": args.precision},
-        "pair_evals_per_s": pairs_rank * world / t_max,
-        "roofline": {"bound": "alu", "kernel": "k_likelihood", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": (achieved / ALU_PEAK_TFLOPS) if achieved else None,
-                     "traffic": traffic,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz max SM clock",
-                     "flops_per_pair": LK_FLOPS_PER_PAIR, "pairs_per_launch": pairs_rank / lk_runs,
-                     "avg_launch_ms": lk_ms / lk_runs},
-        "roofline_hbm_sector": {"bound": "hbm", "kernel": "k_likelihood", "achieved": sector_gbs, "peak": hbm_gbs,
-                                "unit": "GB/s", "frac": (sector_gbs / hbm_gbs) if sector_gbs else None,
-                                "peak_source": hbm_src,
-                                "model": "one 32-byte NNF sector from DRAM per pair (spread particles)",
-                                "uniform_random_reads": probe},
+        "config": {**workload_desc(round(nvalid_mean, 1)), "init": args.init, "precision": args.precision,
+                   "svgd_reading": SVGD_READINGS[args.svgd_precond]},
+        "pair_evals_per_s": pairs * world / t_max,
+        "roofline": graded,
+        f"roofline_{other['bound']}": other,
         "roofline_step": {"bound_ms": step_bound, "measured_ms": 1e3 * t_max / args.steps,
                           "frac": step_bound / (1e3 * t_max / args.steps),
                           "stage_bound_ms": bounds,
-                          "model": "sum over stages of max(algorithmic bytes / HBM peak, flops / ALU peak)"},
+                          "model": "sum over stages of max(algorithmic bytes / HBM peak, flops / measured ALU peak)"},
         "stage_ms_per_step": stage_meas,
+        "device": ceil,
         "e2e": {"value": steps_total / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "after_kidnap": after,
+        "accuracy": {"reading": SVGD_READINGS[args.svgd_precond], "source": "the end-to-end pass (the same steps from "
+                     "the same particles), best pose read back every step",
+                     **accuracy_summary(errs, args.warmup, n_steps, after_kidnap)},
         "gpu_launches": launches,
         "clocks": clk,
         "init_map_s": round(init_map_s, 3),
@@ -458,6 +561,8 @@ def build_parser():
                     help="arithmetic of the likelihood stage (16-bit per-pair arithmetic, FP32 sums)")
     ap.add_argument("--after-kidnap", default="auto", choices=["auto", "on", "off"],
                     help="also time steps 60-99 (after the kidnap at step 50); auto: when >= 20 steps are timed")
+    ap.add_argument("--svgd-precond", type=int, default=0, choices=[0, 1],
+                    help="SVGD reading: 0 = Eq. 6 as printed (the benchmark), 1 = the opt-in preconditioned repulsion")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particle count (profiling runs of a smaller case; the benchmark is 2^20)")
     return ap

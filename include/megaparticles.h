@@ -372,22 +372,6 @@ int mp_debug_set(mp_ctx* ctx, int what, int64_t value);
 int mp_posterior_init_noalloc(const double* log_prior, const float* loglik, int64_t n, double* post_out,
                               int64_t* best_out, void* cuda_stream);
 
-/* ---- Measurement helper (no counterpart in the paper) -----------------
- * The rate of independent, uniformly random 4-byte reads over a device
- * buffer (each read fetches one 32-byte sector from DRAM when the buffer is
- * much larger than L2): a reference for the likelihood's NNF lookups while
- * particles are spread, which are random across particles but clustered
- * along a particle's scan. words: device buffer of n_words uint32 (contents
- * arbitrary, left unchanged); every thread of blocks x 256 makes
- * reads_per_thread reads at indices from its own linear congruential
- * sequence (independent of the data read), so many reads are in flight.
- * Runs once to warm up, then repeats times timed with CUDA events on
- * cuda_stream; *ms_out = mean milliseconds per run. Reads per run = blocks x
- * 256 x reads_per_thread. Errors: MP_EINVAL (NULL pointers, sizes < 1),
- * MP_ECUDA. */
-int mp_probe_random_reads(const uint32_t* words, int64_t n_words, int blocks, int reads_per_thread, int repeats,
-                          void* cuda_stream, float* ms_out);
-
 #ifdef __cplusplus
 }
 #endif

@@ -1,7 +1,9 @@
 """Builds libmp.so (the CUDA library behind include/megaparticles.h) in-tree
 for sm_103a: one nvcc job per translation unit, in parallel, then a shared
 link. Host code is compiled without floating-point contraction (the NNF
-geometry is an FP32 decision sequence).
+geometry is an FP32 decision sequence). The benchmark's measurement helpers
+(include/mp_probe.h, csrc/probe/) become a library of their own,
+libmp_probe.so, built by the same call.
 
 build(checked=True) (or `python -m paper_2404_16370_gb300.build --checked`)
 makes libmp_checked.so with -DMP_CHECKED instead: kernels bound-check the
@@ -22,6 +24,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmp.so")
 LIB_CHECKED = os.path.join(HERE, "libmp_checked.so")
+LIB_PROBE = os.path.join(HERE, "libmp_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", os.path.join(os.path.dirname(HERE), "include")]
@@ -49,13 +52,20 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked=False) -> str:
     """checked: False, True (printed checks) or "lite" (checks recorded by one
-    atomic, no printf; libmp_checked_lite.so)."""
+    atomic, no printf; libmp_checked_lite.so). The normal build also makes
+    libmp_probe.so."""
     suffix = "_checked_lite" if checked == "lite" else "_checked" if checked else ""
-    build_dir = BUILD + suffix
-    lib = os.path.join(HERE, f"libmp{suffix}.so")
+    lib = _build_lib(CSRC, BUILD + suffix, os.path.join(HERE, f"libmp{suffix}.so"), force, verbose, ptxas_info,
+                     checked)
+    if not checked:
+        _build_lib(os.path.join(CSRC, "probe"), BUILD + "_probe", LIB_PROBE, force, verbose, ptxas_info, False)
+    return lib
+
+
+def _build_lib(csrc, build_dir, lib, force, verbose, ptxas_info, checked) -> str:
     os.makedirs(build_dir, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
+    srcs = sorted(glob.glob(os.path.join(csrc, "*.cu")))
+    headers = sorted(glob.glob(os.path.join(csrc, "*.cuh"))) + sorted(
         glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
     objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DMP_CHECKED"] if checked else []) + \

@@ -646,19 +646,49 @@ def mp_step_gicp(ctx, scan, cov_scale=1.0):
 
 
 # ---------------------------------------------------------------------------
-# measurement helper
+# measurement helpers of the benchmark (include/mp_probe.h, libmp_probe.so)
+
+PROBE_PATH = os.path.join(_HERE, "libmp_probe.so")
+_probe = None
 
 
-def mp_probe_random_reads(words, blocks, reads_per_thread, repeats=5, cuda_stream=None) -> float:
-    """Mean ms of one run of blocks x 256 x reads_per_thread independent random
-    4-byte reads over `words` (a device uint32 tensor)."""
-    L = lib()
-    L.mp_probe_random_reads.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p,
-                                        C.POINTER(C.c_float)]
-    L.mp_probe_random_reads.restype = C.c_int
-    ms = C.c_float()
-    rc = L.mp_probe_random_reads(C.c_void_p(words.data_ptr()), int(words.numel()), int(blocks), int(reads_per_thread),
-                                 int(repeats), C.c_void_p(cuda_stream) if cuda_stream else None, C.byref(ms))
+def probe_lib():
+    global _probe
+    if _probe is None:
+        if not os.path.exists(PROBE_PATH):
+            raise ImportError(f"{PROBE_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(PROBE_PATH)
+        L.mp_probe_random_reads.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                            C.POINTER(C.c_float), C.POINTER(C.c_int64)]
+        L.mp_probe_fma_rate.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_float),
+                                        C.POINTER(C.c_double)]
+        for f in ("mp_probe_random_reads", "mp_probe_fma_rate"):
+            getattr(L, f).restype = C.c_int
+        _probe = L
+    return _probe
+
+
+def mp_probe_random_reads(words, blocks, reads_per_thread, repeats=5, cuda_stream=None):
+    """(mean ms of one run, reads per run) of independent random 4-byte reads
+    over `words` (a uint32/int32 tensor on the current CUDA device)."""
+    _device_tensor(words, "words")
+    ms, n = C.c_float(), C.c_int64()
+    rc = probe_lib().mp_probe_random_reads(C.c_void_p(words.data_ptr()), int(words.numel()), int(blocks),
+                                           int(reads_per_thread), int(repeats),
+                                           C.c_void_p(cuda_stream) if cuda_stream else None, C.byref(ms), C.byref(n))
     if rc != MP_OK:
-        raise MPError(rc, "mp_probe_random_reads failed")
-    return float(ms.value)
+        raise MPError(rc, "mp_probe_random_reads: invalid argument or CUDA failure")
+    return float(ms.value), int(n.value)
+
+
+MP_FMA_FP32, MP_FMA_FP32X2, MP_FMA_FP64 = 0, 1, 2
+
+
+def mp_probe_fma_rate(kind, blocks, iters, repeats=3, cuda_stream=None):
+    """(mean ms of one run, flops of one run) of the FMA throughput probe."""
+    ms, fl = C.c_float(), C.c_double()
+    rc = probe_lib().mp_probe_fma_rate(int(kind), int(blocks), int(iters), int(repeats),
+                                       C.c_void_p(cuda_stream) if cuda_stream else None, C.byref(ms), C.byref(fl))
+    if rc != MP_OK:
+        raise MPError(rc, "mp_probe_fma_rate: invalid argument or CUDA failure")
+    return float(ms.value), float(fl.value)

@@ -10,6 +10,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "megaparticles.h")
 HEADERS = [HEADER, os.path.join(ROOT, "include", "mp_proposal.h")]
+PROBE_HEADER = os.path.join(ROOT, "include", "mp_probe.h")
 
 
 def declared(headers=(HEADER,)):
@@ -32,11 +33,24 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
+def exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    return set(re.findall(r"\sT\s(mp_[a-z_0-9]+)$", out, flags=re.M))
+
+
 def test_library_exports_every_declared_symbol(built):
-    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\sT\s(mp_[a-z_0-9]+)$", out, flags=re.M))
-    missing = [n for n in declared(HEADERS) if n not in exported]
+    missing = [n for n in declared(HEADERS) if n not in exported(built)]
     assert not missing, missing
+
+
+def test_probe_library_is_apart_from_the_filter_library(built):
+    """The benchmark's measurement helpers (include/mp_probe.h) are exported by
+    libmp_probe.so and not by libmp.so."""
+    from paper_2404_16370_gb300 import build as B
+    probe = declared((PROBE_HEADER,))
+    assert set(probe) == {"mp_probe_random_reads", "mp_probe_fma_rate"}
+    assert set(probe) <= exported(B.LIB_PROBE)
+    assert not set(probe) & exported(built)
 
 
 def test_library_loads_and_reports_without_gpu(built):
