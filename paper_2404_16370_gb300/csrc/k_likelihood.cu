@@ -355,6 +355,7 @@ __device__ __forceinline__ void LkOp<SPLIT>::run(const LkArgs& A, unsigned bxi, 
         if (!MP_DCHECK(cc >= 0 && m > 0 && ((reinterpret_cast<uintptr_t>(A.scan) & 15) == 0), "scan chunk", cc))
             return;
         uint32_t bytes = (uint32_t)m * 48u;
+        fence_proxy_async_smem();   // the block's reads of dst (a reused buffer) before the copy's writes
         mbar_expect_tx(b, bytes + ((A.starve && cc == 0) ? 16u : 0u));
         bulk_g2s(dst, A.scan + 3 * (int64_t)cc * LK_CHUNK, bytes, b);
     };
@@ -638,6 +639,7 @@ __global__ void __launch_bounds__(LK_THREADS, MINB) k_likelihood_h(const LkArgs 
         if (!MP_DCHECK(cc >= 0 && m > 0 && ((reinterpret_cast<uintptr_t>(A.scan_h) & 15) == 0), "scan chunk", cc))
             return;
         uint32_t bytes = (uint32_t)m * 32u;
+        fence_proxy_async_smem();   // the block's reads of dst (a reused buffer) before the copy's writes
         mbar_expect_tx(b, bytes + ((A.starve && cc == 0) ? 16u : 0u));
         bulk_g2s(dst, A.scan_h + 2 * (int64_t)cc * LK_CHUNK, bytes, b);
     };

@@ -88,3 +88,54 @@ def test_filter_localises_16bit():
     assert res["fp32"]["success_rate"] >= 0.6
     for p in ("bf16", "fp16"):
         assert res[p]["success_rate"] >= res["fp32"]["success_rate"] - 0.2, p
+
+
+# bounds of the chained per-step errors against the FP64 oracle step taken
+# from the GPU's own state (median over particles of each step; translation in
+# m, rotation in rad, log-likelihood relative): a few times the measured values
+STEP_BOUNDS = {"fp32": (1e-5, 1e-5, 1e-6), "fp16": (5e-3, 5e-3, 5e-4), "bf16": (5e-2, 5e-2, 5e-3)}
+
+
+@pytest.mark.parametrize("name", ["fp32", "fp16", "bf16"])
+def test_chained_steps_against_oracle(room, oracle, name):
+    """The precision variant of the box-room workload (4096 particles, one
+    static 512-point scan, identity odometry): five chained GPU steps in the
+    given precision. Before each step the GPU state (poses, neighbour lists,
+    log prior) is read back and the FP64 oracle takes the same step from it;
+    the step's log-likelihood, SVGD update phi and updated poses are compared
+    particle by particle. The 16-bit forms' errors are reported per step and
+    bounded; the FP32 form stays at its own rounding scale."""
+    from gpu_util import pose_error
+    mp, P, w = room["mp"], room["P"], room["w"]
+    prec = {"fp32": 0, "fp16": 2, "bf16": 1}[name]
+    ctx = mp.mp_init_map(w.map_points, mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, N))
+    rows = []
+    try:
+        mp.mp_set_precision(ctx, prec)
+        mp.mp_init_particles(ctx, N, poses=w.particles)
+        for s in range(5):
+            poses_in = mp.mp_get_buffer(ctx, mp.MP_BUF_POSES)
+            ids = mp.mp_get_buffer(ctx, mp.MP_BUF_NBR_IDS, K=P.K)
+            logprior = mp.mp_get_buffer(ctx, mp.MP_BUF_LOG_PRIOR)
+            mp.mp_step(ctx, w.scans[s], w.odom[s], w.odom_cov[s])
+            gn = mp.mp_get_buffer(ctx, mp.MP_BUF_GN)
+            phi = mp.mp_get_buffer(ctx, mp.MP_BUF_PHI)
+            poses_out = mp.mp_get_buffer(ctx, mp.MP_BUF_POSES)
+            f = oracle.OracleFilter(room["om"], P, poses_in.copy(), ids=ids.copy(), logprior=logprior.copy(),
+                                    step_index=s)
+            out = f.step(w.scans[s], w.odom[s], w.odom_cov[s])
+            # log p = -sum_k min(c_k, c_max): every term has one sign, so |log p| is the sum of term magnitudes
+            ll_rel = np.abs(gn[:, 27] - out["loglik"]) / (np.abs(out["loglik"]) + 1e-6)
+            ang, dist = pose_error(poses_out, out["new_poses"])
+            dphi = np.abs(phi - out["phi"])
+            rows.append((s, np.median(ll_rel), np.quantile(ll_rel, 0.99), np.median(dphi[:, :3]),
+                         np.median(dphi[:, 3:]), np.median(ang), np.median(dist), np.quantile(dist, 0.99)))
+    finally:
+        mp.mp_destroy(ctx)
+    print(f"\n{name}: step | log-lik rel. err median p99 | phi err median rot trans | pose err median rad m | p99 m")
+    for r in rows:
+        print(f"{name}: {r[0]} | {r[1]:.2e} {r[2]:.2e} | {r[3]:.2e} {r[4]:.2e} | {r[5]:.2e} {r[6]:.2e} | {r[7]:.2e}")
+    b_t, b_r, b_ll = STEP_BOUNDS[name]
+    for r in rows:
+        assert r[1] < b_ll, (name, r)
+        assert r[5] < b_r and r[6] < b_t, (name, r)
