@@ -77,6 +77,15 @@ typedef struct mp_params {
      * paper's printed update); a particle without a step (fewer than 6
      * inliers or a non-positive pivot) gets no repulsion. */
     int32_t svgd_precond;
+    /* Floor of the initial posterior (Sec. III-D), in nats: p_i is evaluated
+     * as exp(max(l_i - max_j l_j, -post_floor)) with l = log prior +
+     * log-likelihood, so that no particle's posterior -- and so no particle's
+     * prior at the next step -- is an exact zero (without it, FP64 exp
+     * underflows for every particle more than ~745 nats below the best, and
+     * those particles could never become the representative state again,
+     * whatever their later likelihood). Default 700 (the range of FP64 exp);
+     * 0 = no floor (the plain exp(l - max l)). Not printed in the paper. */
+    float post_floor;
 } mp_params;
 
 #define MP_PRESET_BOX_ROOM 0   /* 0.1 m NNF, r_max 1 m, K = C = 16           */
@@ -341,9 +350,11 @@ int mp_debug_set(mp_ctx* ctx, int what, int64_t value);
  *
  * Computes, for n particles, p_i = exp(l_i - max l) / sum_j exp(l_j - max l)
  * with l_i = log_prior[i] + loglik[i] (log_prior NULL: 0), and the index of
- * the largest p_i (smallest index on ties). These equal the posterior stage's
- * initial posterior (MP_BUF_POST_INIT) up to the FP64 rounding of the sum,
- * whose summation order differs; the index is the same. log_prior (n
+ * the largest p_i (smallest index on ties): the plain definition, without
+ * the posterior stage's floor. These equal that stage's initial posterior
+ * (MP_BUF_POST_INIT) when its floor is off (mp_params.post_floor = 0), up to
+ * the FP64 rounding of the sum, whose summation order differs; the index is
+ * the same. log_prior (n
  * float64), loglik (n float32), post_out (n float64) and best_out (1 int64)
  * are DEVICE pointers of the current device, owned by the caller; host
  * memory (pageable or pinned) and other devices' memory are refused with

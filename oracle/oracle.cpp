@@ -1236,15 +1236,19 @@ void or_svgd(const float* poses, i64 np, const int32_t* ids, const double* kk, c
 // `iters` Jacobi sweeps p'_i = sum_j k_ij p_j / sum_j k_ij over the list of i,
 // and a final renormalisation. best = argmax p' (smallest index on ties).
 void or_posterior(const double* logprior, const double* loglik, i64 np, const int32_t* ids, const double* kk,
-                  int K, int iters, double* p_init, double* p_out, i64* best) {
+                  int K, int iters, double floor_nats, double* p_init, double* p_out, i64* best) {
   std::vector<double> l(np), p(np), q(np);
   double mx = -INFINITY;
   for (i64 i = 0; i < np; ++i) {
     l[i] = (logprior ? logprior[i] : 0.0) + (loglik ? loglik[i] : 0.0);
     if (l[i] > mx) mx = l[i];
   }
+  // the initial posterior relative to its largest value, exp(l - max l), is
+  // kept at or above exp(-floor_nats) (floor_nats = 0: no floor): no particle's
+  // posterior, and so no particle's prior at the next step, is an exact zero
+  const double lo = floor_nats > 0 ? -floor_nats : -INFINITY;
   double sum = 0;
-  for (i64 i = 0; i < np; ++i) { p[i] = std::exp(l[i] - mx); sum += p[i]; }
+  for (i64 i = 0; i < np; ++i) { p[i] = std::exp(std::max(l[i] - mx, lo)); sum += p[i]; }
   for (i64 i = 0; i < np; ++i) p[i] /= sum;
   if (p_init) for (i64 i = 0; i < np; ++i) p_init[i] = p[i];
   for (int it = 0; it < iters; ++it) {

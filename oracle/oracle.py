@@ -86,7 +86,7 @@ def _declare(L):
     L.or_svgd.argtypes = [_P, _I64, _P, _P, _P, _INT, _P, _D, _D, _P, _P, _P]
     L.or_gicp.argtypes = [_P, _P, _P, _I64, _P, _P, _P, _I64, _P, _D, _D, _D, _D, _INT, _D, _P, _P, _P, _P]
     L.or_gicp.restype = _INT
-    L.or_posterior.argtypes = [_P, _P, _I64, _P, _P, _INT, _INT, _P, _P, _P]
+    L.or_posterior.argtypes = [_P, _P, _I64, _P, _P, _INT, _INT, _D, _P, _P, _P]
     L.or_cholesky6.argtypes = [_P, _P]
     L.or_predict_noise.argtypes = [_I64, _U64, _U64, _P]
     L.or_predict.argtypes = [_P, _I64, _P, _P, _U64, _U64, _P, _P]
@@ -129,6 +129,7 @@ class Params:
     nb_log2: int = 12         # log2 of the number of LSH buckets
     seed: int = 4
     svgd_precond: int = 0     # 1: repulsion times (H + lambda diag H + eps I)^-1 (not the printed Eq. 6)
+    post_floor: float = 700.0  # floor of the initial posterior exp(l - max l) at exp(-post_floor); 0: none
 
     @staticmethod
     def box_room(n_particles: int = 4096) -> "Params":
@@ -373,12 +374,17 @@ def svgd_precond_matrices(H, ok, params: Params):
     return out
 
 
-def posterior(logprior, loglik, ids, kk, iters):
+def posterior(logprior, loglik, ids, kk, iters, floor=0.0):
+    """Sec. III-D: initial posterior p_i ~ prior_i p(P | x_i), evaluated as
+    exp(l_i - max l) with l = log prior + log-likelihood (floored at
+    exp(-floor) when floor > 0), normalised; `iters` Jacobi sweeps of Eq. 11;
+    renormalised. Returns (initial posterior, posterior, argmax)."""
     npart = len(loglik)
     K = np.asarray(ids).shape[1]
     p0 = np.zeros(npart); p = np.zeros(npart); best = np.zeros(1, np.int64)
     lib().or_posterior(_p(None if logprior is None else _c(logprior, np.float64)), _p(_c(loglik, np.float64)),
-                       npart, _p(_c(ids, np.int32)), _p(_c(kk, np.float64)), K, int(iters), _p(p0), _p(p), _p(best))
+                       npart, _p(_c(ids, np.int32)), _p(_c(kk, np.float64)), K, int(iters), float(floor), _p(p0),
+                       _p(p), _p(best))
     return p0, p, int(best[0])
 
 
@@ -488,7 +494,7 @@ class OracleFilter:
             loglik = np.zeros(n)
             out.update(loglik=loglik, new_poses=poses.astype(np.float64))
         # posterior probability update (Eq. 11)
-        p0, p, best = posterior(self.logprior, loglik, mg["ids"], mg["k"], P.post_iters)
+        p0, p, best = posterior(self.logprior, loglik, mg["ids"], mg["k"], P.post_iters, P.post_floor)
         out.update(post_init=p0, post=p, best=best)
         # the state is stored in FP32
         self.poses = out["new_poses"].astype(np.float32)

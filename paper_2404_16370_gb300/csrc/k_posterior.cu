@@ -57,6 +57,7 @@ struct PostArgs {
     int32_t* ids_t;       // the ids, slot-major: ids_t[l * n + i]
     double* invden;       // 1 / sum_j k_ij
     int iters;
+    double lfloor;        // lower bound of l - max l in the initial posterior (-post_floor; -inf: none)
     const float4* poses;
     float4* best_pose;
     int32_t* err;         // error bits (MP_ERR_WAIT when a grid barrier gives up)
@@ -96,13 +97,14 @@ __device__ __forceinline__ void reduce_max(const PostArgs& A) {
     }
 }
 
-// p = exp(l - max l) into post_init and post_tmp (the sweeps' input); block sums
+// p = exp(max(l - max l, floor)) into post_init and post_tmp (the sweeps'
+// input); block sums
 __device__ __forceinline__ void post_exp(const PostArgs& A, unsigned bx) {
     __shared__ double s[PB / 32];
     int64_t i = (int64_t)bx * PB + threadIdx.x;
     double v = 0.0;
     if (i < A.n) {
-        v = exp(A.post[i] - A.scalars[0]);
+        v = exp(fmax(A.post[i] - A.scalars[0], A.lfloor));
         A.post_init[i] = v;
         A.post_tmp[i] = v;
     }
@@ -407,6 +409,7 @@ PostArgs post_args(mp_ctx* c, int cur) {
     A.ids_t = c->post_ids;
     A.invden = c->post_invden;
     A.iters = c->p.post_iters;
+    A.lfloor = c->p.post_floor > 0.f ? -(double)c->p.post_floor : -INFINITY;
     A.poses = c->poses[c->cur];
     A.best_pose = c->best_pose;
     A.err = c->dev_error;

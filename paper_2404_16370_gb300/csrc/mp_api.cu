@@ -256,6 +256,8 @@ int check_params(mp_ctx* c, const mp_params* p) {
     if (p->n_buckets_log2 < 1 || p->n_buckets_log2 > 26) return mp_fail(c, MP_EINVAL, "n_buckets_log2 must lie in [1, 26]");
     if (p->max_scan < 1 || p->max_scan > (1 << 20)) return mp_fail(c, MP_EINVAL, "max_scan must lie in [1, 2^20]");
     if (p->svgd_precond != 0 && p->svgd_precond != 1) return mp_fail(c, MP_EINVAL, "svgd_precond must be 0 or 1");
+    if (!(p->post_floor >= 0.f && p->post_floor <= 700.f))
+        return mp_fail(c, MP_EINVAL, "post_floor must lie in [0, 700] nats (0: no floor)");
     return MP_OK;
 }
 
@@ -365,6 +367,7 @@ int mp_default_params(mp_params* p, int preset, int64_t n_particles) {
     p->post_iters = 10;
     p->max_scan = 16384;
     p->seed = 4;
+    p->post_floor = 700.0f;
     if (preset == MP_PRESET_BOX_ROOM) {
         p->nnf_res = 0.1f; p->r_max = 1.0f; p->r_cov = 1.0f; p->K = 16; p->C = 16;
     } else if (preset == MP_PRESET_OUTDOOR) {

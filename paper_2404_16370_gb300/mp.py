@@ -54,7 +54,7 @@ class mp_params(C.Structure):
                 ("lambda_", C.c_float), ("eps", C.c_float), ("eps_cov", C.c_float), ("r_cov", C.c_float),
                 ("K", C.c_int32), ("C", C.c_int32), ("cov_k", C.c_int32), ("cov_min", C.c_int32),
                 ("post_iters", C.c_int32), ("n_buckets_log2", C.c_int32), ("max_scan", C.c_int32),
-                ("seed", C.c_uint64), ("svgd_precond", C.c_int32)]
+                ("seed", C.c_uint64), ("svgd_precond", C.c_int32), ("post_floor", C.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

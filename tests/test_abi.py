@@ -81,7 +81,7 @@ def test_presets_match_oracle_readings(built, oracle, preset, n):
              ("sigma_t", "sigma_t"), ("alpha", "alpha"), ("lsh_sigma", "lsh_sigma"), ("lambda_", "lam"),
              ("eps", "eps_damp"), ("eps_cov", "eps_cov"), ("r_cov", "r_cov"), ("K", "K"), ("C", "C"),
              ("cov_k", "cov_k"), ("cov_min", "cov_min"), ("post_iters", "post_iters"),
-             ("n_buckets_log2", "nb_log2"), ("seed", "seed")]
+             ("n_buckets_log2", "nb_log2"), ("seed", "seed"), ("post_floor", "post_floor")]
     for gk, ok in pairs:
         assert abs(float(getattr(g, gk)) - float(getattr(o, ok))) <= 1e-7 * max(1.0, abs(float(getattr(o, ok)))), gk
 

@@ -236,7 +236,8 @@ def test_ragged_posterior_odd_sweeps(room, oracle):
         best, best_p = mp.mp_get_posterior(ctx)
     finally:
         mp.mp_destroy(ctx)
-    _, p_ref, b_ref = oracle.posterior(logprior, loglik.astype(np.float64), ids, kk.astype(np.float64), 7)
+    _, p_ref, b_ref = oracle.posterior(logprior, loglik.astype(np.float64), ids, kk.astype(np.float64), 7,
+                                       oracle.Params().post_floor)
     assert np.allclose(post, p_ref, rtol=1e-10, atol=1e-300)
     assert abs(post.sum() - 1) < 1e-12
     assert np.array_equal(best, room["w"].particles[b_ref]) and abs(best_p - p_ref[b_ref]) < 1e-12

@@ -220,7 +220,7 @@ def test_posterior_fullsize_matches_oracle(big, stepped, oracle):
     post = mp.mp_get_buffer(ctx, mp.MP_BUF_POST)
     best, best_p = mp.mp_get_posterior(ctx)
     _, p_ref, b_ref = oracle.posterior(logprior, loglik.astype(np.float64), ids, kk.astype(np.float64),
-                                       P.post_iters)
+                                       P.post_iters, P.post_floor)
     assert np.allclose(post, p_ref, rtol=1e-10, atol=1e-300)
     assert abs(post.sum() - 1) < 1e-12
     assert abs(best_p - p_ref[b_ref]) < 1e-12 and post[b_ref] == best_p

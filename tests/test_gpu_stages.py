@@ -329,7 +329,7 @@ def test_posterior(env, oracle):
     lp = mp.mp_get_buffer(ctx, mp.MP_BUF_LOG_PRIOR)
     best, best_p = mp.mp_get_posterior(ctx)
     p0_ref, p_ref, b_ref = oracle.posterior(logprior, loglik.astype(np.float64), ids, kk.astype(np.float64),
-                                            P.post_iters)
+                                            P.post_iters, P.post_floor)
     assert np.allclose(p0, p0_ref, rtol=1e-10, atol=1e-300)
     assert np.allclose(post, p_ref, rtol=1e-10, atol=1e-300)
     assert abs(post.sum() - 1) < 1e-12

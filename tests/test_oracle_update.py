@@ -235,3 +235,36 @@ def test_philox_known_answers(oracle):
         key = [int(w, 16) for w in v["key"]]
         out = [int(w) for w in oracle.philox(ctr, key)]
         assert out == [int(w, 16) for w in v["out"]], v
+
+
+def test_posterior_floor(oracle):
+    """The floor of the initial posterior (Sec. III-D prior; the reading that
+    keeps exp(l - max l) >= exp(-floor)): without it a particle far below the
+    best has an exact zero posterior, its log prior is -inf at the next step
+    and it can never win again; with it, its posterior is exp(-floor) relative
+    to the best, and a decisive likelihood at the next step makes it the
+    representative state."""
+    n = 4
+    ids = np.arange(n, dtype=np.int32)[:, None]          # lists = {self}: no smoothing
+    kk = np.ones((n, 1))
+    ll1 = np.array([0.0, -1e5, -50.0, -800.0])
+    for floor in (0.0, 700.0):
+        p0, p, best = oracle.posterior(None, ll1, ids, kk, 0, floor)
+        assert best == 0
+        if floor == 0.0:
+            assert p[1] == 0.0 and p[3] == 0.0
+        else:
+            # exp(max(l - max l, -floor)) / sum, term by term
+            w = np.exp(np.maximum(ll1 - 0.0, -floor))
+            assert np.allclose(p, w / w.sum(), rtol=1e-14, atol=0)
+            assert p[1] == p[3] > 0
+        with np.errstate(divide="ignore"):
+            prior2 = np.log(p)
+        # the next step: particle 1 now explains the scan, particle 0 does not
+        ll2 = np.array([-1000.0, 0.0, -2000.0, -900.0])
+        _, p2, best2 = oracle.posterior(prior2, ll2, ids, kk, 0, floor)
+        assert best2 == (0 if floor == 0.0 else 1)
+    # the floor is relative to the best particle, so it does not depend on an offset of l
+    a = oracle.posterior(None, ll1 + 1234.5, ids, kk, 0, 700.0)[1]
+    b = oracle.posterior(None, ll1, ids, kk, 0, 700.0)[1]
+    assert np.allclose(a, b, rtol=1e-12, atol=0)

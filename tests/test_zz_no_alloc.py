@@ -33,7 +33,8 @@ def test_noalloc_initial_posterior_matches_oracle_and_posterior_stage():
     from oracle import oracle as O
     from paper_2404_16370_gb300 import mp
     room = synth.box_room(1, n_map=5000)
-    params = mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, N, post_iters=0)
+    # the posterior stage without its floor: the entry point computes the plain exp(l - max l)
+    params = mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, N, post_iters=0, post_floor=0.0)
     ctx = mp.mp_init_map(room.map_points, params)
     try:
         poses = synth.box_room_particles(N, seed=5)
