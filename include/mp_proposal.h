@@ -81,6 +81,22 @@ int mp_pn_adam_step(mp_pn* net, float lr, float beta1, float beta2, float eps);
  * (particle index). */
 int mp_pn_sample(mp_pn* net, const float* mix, int64_t n, uint64_t seed, float* poses_out);
 
+/* Arithmetic of the shared per-point layers (the network's only dense
+ * contractions: 64 -> 128 and 128 -> 256 channels on every scan point).
+ * MP_PREC_BF16 (the default when n_points is a multiple of 128): one fused
+ * kernel on the tensor cores per forward pass -- layer 1 on the CUDA cores,
+ * layers 2 and 3 as tcgen05 MMAs with BF16 weights and activations and FP32
+ * accumulation, the max-pool in the same kernel; the FP32 parameters stay the
+ * master copy (their BF16 image is refreshed at every update), and the
+ * backward pass runs in FP32 on the activations the forward pass used.
+ * MP_PREC_FP32: every layer on the CUDA cores in FP32. Returns MP_EINVAL for
+ * another value, or for MP_PREC_BF16 when n_points is not a multiple of 128. */
+int mp_pn_set_precision(mp_pn* net, int precision);
+/* Waits for the network's stream; MP_ETIMEOUT if a bounded wait inside the
+ * fused kernel gave up since the last call (its outputs are then invalid),
+ * else MP_OK. */
+int mp_pn_status(mp_pn* net);
+
 #ifdef __cplusplus
 }
 #endif

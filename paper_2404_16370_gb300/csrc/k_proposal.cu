@@ -356,6 +356,9 @@ struct mp_pn {
     int* gi;
     float *dO, *dh4, *dg, *dh3, *dh2, *dh1;
     uint2 key;
+    int prec;          // MP_PREC_BF16: per-point layers on the tensor cores; MP_PREC_FP32: CUDA cores
+    uint8_t* wimg;     // BF16 image of W2^T and W3^T for the tensor-core kernel
+    int32_t* err;      // device error bits of the fused kernel
 };
 
 namespace {
@@ -395,15 +398,29 @@ void colsum(cudaStream_t s, const float* X, int64_t rows, int n, float* out) {
     k_colsum<<<grid, 128, 0, s>>>(X, rows, n, rpc, out);
 }
 
-int forward(mp_pn* net, const float* scans, int B) {
+// BF16 image of the per-point weights, refreshed after every parameter update
+int pack_weights(mp_pn* net) {
+    if (net->prec != MP_PREC_BF16) return MP_OK;
+    return mp_pn_tc_pack(net->param + OW2, net->param + OW3, net->wimg, net->stream);
+}
+
+// train: keep the per-point activations h1, h2 for the backward pass
+int forward(mp_pn* net, const float* scans, int B, bool train) {
     cudaStream_t s = net->stream;
     const int64_t rows = (int64_t)B * net->P;
     k_scale_points<<<grid_for(rows * 3, 256), 256, 0, s>>>(scans, rows * 3, 1.f / net->in_scale, net->xs);
     const float* W = net->param;
-    gemm<false, false, EPI_BIAS | EPI_RELU>(s, net->xs, W + OW1, net->h1, W + OB1, (int)rows, C1, 3, 3, C1, C1);
-    gemm<false, false, EPI_BIAS | EPI_RELU>(s, net->h1, W + OW2, net->h2, W + OB2, (int)rows, C2, C1, C1, C2, C2);
-    gemm<false, false, EPI_BIAS | EPI_RELU>(s, net->h2, W + OW3, net->h3, W + OB3, (int)rows, C3, C2, C2, C3, C3);
-    k_maxpool<<<dim3(C3 / 128, B), 128, 0, s>>>(net->h3, B, net->P, net->g, net->gi);
+    if (net->prec == MP_PREC_BF16) {
+        const int rc = mp_pn_tc_forward(net->xs, B, net->P, W + OW1, W + OB1, W + OB2, W + OB3, net->wimg, net->g,
+                                        net->gi, train ? net->h1 : nullptr, train ? net->h2 : nullptr, net->err,
+                                        MP_WAIT_BUDGET, s);
+        if (rc) return mp_fail_noctx(rc, "mp_pn: tensor-core forward launch failed");
+    } else {
+        gemm<false, false, EPI_BIAS | EPI_RELU>(s, net->xs, W + OW1, net->h1, W + OB1, (int)rows, C1, 3, 3, C1, C1);
+        gemm<false, false, EPI_BIAS | EPI_RELU>(s, net->h1, W + OW2, net->h2, W + OB2, (int)rows, C2, C1, C1, C2, C2);
+        gemm<false, false, EPI_BIAS | EPI_RELU>(s, net->h2, W + OW3, net->h3, W + OB3, (int)rows, C3, C2, C2, C3, C3);
+        k_maxpool<<<dim3(C3 / 128, B), 128, 0, s>>>(net->h3, B, net->P, net->g, net->gi);
+    }
     gemm<false, false, EPI_BIAS | EPI_RELU>(s, net->g, W + OW4, net->h4, W + OB4, B, C4, C3, C3, C4, C4);
     gemm<false, false, EPI_BIAS>(s, net->h4, W + OW5, net->o, W + OB5, B, NOUT, C4, C4, NOUT, NOUT);
     PN_CUDA(cudaGetLastError());
@@ -449,6 +466,7 @@ int mp_pn_create(mp_pn** netp, int n_points, int max_batch, float in_scale, cons
     A(&net->o, (size_t)max_batch * NOUT); A(&net->dO, (size_t)max_batch * NOUT);
     A(&net->dh4, (size_t)max_batch * C4); A(&net->dg, (size_t)max_batch * C3);
     A(&net->dh3, rows * C3); A(&net->dh2, rows * C2); A(&net->dh1, rows * C1);
+    A(&net->wimg, mp_pn_tc_image_bytes()); A(&net->err, 1);
     if (e != cudaSuccess) {
         mp_pn_destroy(net);
         return pn_fail("allocation", e);
@@ -459,8 +477,11 @@ int mp_pn_create(mp_pn** netp, int n_points, int max_batch, float in_scale, cons
     PN_CUDA(cudaMemsetAsync(net->am, 0, sizeof(float) * NPARAM, net->stream));
     PN_CUDA(cudaMemsetAsync(net->av, 0, sizeof(float) * NPARAM, net->stream));
     PN_CUDA(cudaMemsetAsync(net->grad, 0, sizeof(float) * NPARAM, net->stream));
+    PN_CUDA(cudaMemsetAsync(net->err, 0, sizeof(int32_t), net->stream));
     k_pn_init<<<grid_for(NPARAM, 256), 256, 0, net->stream>>>(net->param, net->key);
     PN_CUDA(cudaGetLastError());
+    net->prec = n_points % 128 == 0 ? MP_PREC_BF16 : MP_PREC_FP32;
+    if (pack_weights(net)) return pn_fail("weight image", cudaGetLastError());
     PN_CUDA(cudaStreamSynchronize(net->stream));
     return MP_OK;
 }
@@ -469,7 +490,7 @@ int mp_pn_destroy(mp_pn* net) {
     if (!net) return mp_fail_noctx(MP_EINVAL, "mp_pn_destroy: invalid argument");
     void* bufs[] = {net->scale, net->offset, net->param, net->grad, net->am, net->av, net->xs, net->h1,
                     net->h2, net->h3, net->g, net->gi, net->h4, net->o, net->dO, net->dh4, net->dg, net->dh3,
-                    net->dh2, net->dh1};
+                    net->dh2, net->dh1, net->wimg, net->err};
     for (void* p : bufs)
         if (p) cudaFree(p);
     delete net;
@@ -492,13 +513,14 @@ int mp_pn_get_params(mp_pn* net, float* out) {
 int mp_pn_set_params(mp_pn* net, const float* in) {
     if (!net || !in) return mp_fail_noctx(MP_EINVAL, "mp_pn_set_params: invalid argument");
     PN_CUDA(cudaMemcpyAsync(net->param, in, sizeof(float) * NPARAM, cudaMemcpyDefault, net->stream));
+    if (pack_weights(net)) return pn_fail("weight image", cudaGetLastError());
     PN_CUDA(cudaStreamSynchronize(net->stream));
     return MP_OK;
 }
 
 int mp_pn_forward(mp_pn* net, const float* scans, int B, float* out) {
     if (!net || !scans || !out || B < 1 || B > net->Bmax) return mp_fail_noctx(MP_EINVAL, "mp_pn_forward: invalid argument");
-    int rc = forward(net, scans, B);
+    int rc = forward(net, scans, B, false);
     if (rc) return rc;
     PN_CUDA(cudaMemcpyAsync(out, net->o, sizeof(float) * (size_t)B * NOUT, cudaMemcpyDefault, net->stream));
     return MP_OK;
@@ -506,7 +528,7 @@ int mp_pn_forward(mp_pn* net, const float* scans, int B, float* out) {
 
 int mp_pn_loss_grad(mp_pn* net, const float* scans, const float* targets, int B, float* loss_dev, float* grad_out) {
     if (!net || !scans || !targets || !loss_dev || B < 1 || B > net->Bmax) return mp_fail_noctx(MP_EINVAL, "mp_pn_loss_grad: invalid argument");
-    int rc = forward(net, scans, B);
+    int rc = forward(net, scans, B, true);
     if (rc) return rc;
     cudaStream_t s = net->stream;
     const int64_t rows = (int64_t)B * net->P;
@@ -552,6 +574,7 @@ int mp_pn_adam_step(mp_pn* net, float lr, float beta1, float beta2, float eps) {
     k_adam<<<grid_for(NPARAM, 256), 256, 0, net->stream>>>(net->param, net->grad, net->am, net->av, NPARAM, lr, beta1,
                                                            beta2, eps, c1, c2);
     PN_CUDA(cudaGetLastError());
+    if (pack_weights(net)) return pn_fail("weight image", cudaGetLastError());
     return MP_OK;
 }
 
@@ -561,6 +584,29 @@ int mp_pn_sample(mp_pn* net, const float* mix, int64_t n, uint64_t seed, float* 
     k_pn_sample<<<grid_for(n, 256), 256, 0, net->stream>>>(mix, n, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)),
                                                           net->scale, net->offset, poses_out);
     PN_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int mp_pn_set_precision(mp_pn* net, int precision) {
+    if (!net || (precision != MP_PREC_FP32 && precision != MP_PREC_BF16))
+        return mp_fail_noctx(MP_EINVAL, "mp_pn_set_precision: invalid argument");
+    if (precision == MP_PREC_BF16 && net->P % 128 != 0)
+        return mp_fail_noctx(MP_EINVAL, "mp_pn_set_precision: the tensor-core layers take scans of a multiple of "
+                                        "128 points, not %d", net->P);
+    net->prec = precision;
+    if (pack_weights(net)) return pn_fail("weight image", cudaGetLastError());
+    return MP_OK;
+}
+
+int mp_pn_status(mp_pn* net) {
+    if (!net) return mp_fail_noctx(MP_EINVAL, "mp_pn_status: invalid argument");
+    int32_t e = 0;
+    PN_CUDA(cudaMemcpyAsync(&e, net->err, sizeof(e), cudaMemcpyDeviceToHost, net->stream));
+    PN_CUDA(cudaStreamSynchronize(net->stream));
+    if (e) {
+        PN_CUDA(cudaMemsetAsync(net->err, 0, sizeof(int32_t), net->stream));
+        return mp_fail_noctx(MP_ETIMEOUT, "mp_pn: a bounded wait of the tensor-core forward pass gave up");
+    }
     return MP_OK;
 }
 

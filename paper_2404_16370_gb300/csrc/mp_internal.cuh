@@ -552,6 +552,12 @@ int mp_launch_unpack_poses(mp_ctx* c, const float4* src, float* dst7_dev);
 int mp_launch_gather_gn(mp_ctx* c, float* dst_dev);
 // k_posterior.cu
 int mp_launch_posterior(mp_ctx* c);
+// k_pn_tc.cu: the proposal network's fused per-point layers on the tensor cores
+size_t mp_pn_tc_image_bytes();
+int mp_pn_tc_pack(const float* W2, const float* W3, uint8_t* image, cudaStream_t s);
+int mp_pn_tc_forward(const float* xs, int B, int P, const float* W1, const float* b1, const float* b2,
+                     const float* b3, const uint8_t* image, float* g, int* gi, float* h1_out, float* h2_out,
+                     int32_t* err, long long budget, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // grouped launches (batched instances, mp_batch_*): one kernel over the blocks

@@ -386,8 +386,11 @@ def _pn_lib():
         L.mp_pn_loss_grad.argtypes = [V, P, P, C.c_int, P, P]
         L.mp_pn_adam_step.argtypes = [V, C.c_float, C.c_float, C.c_float, C.c_float]
         L.mp_pn_sample.argtypes = [V, P, I64, U64, P]
+        L.mp_pn_set_precision.argtypes = [V, C.c_int]
+        L.mp_pn_status.argtypes = [V]
         for f in ("mp_pn_sim_box_room", "mp_pn_create", "mp_pn_destroy", "mp_pn_num_params", "mp_pn_get_params",
-                  "mp_pn_set_params", "mp_pn_forward", "mp_pn_loss_grad", "mp_pn_adam_step", "mp_pn_sample"):
+                  "mp_pn_set_params", "mp_pn_forward", "mp_pn_loss_grad", "mp_pn_adam_step", "mp_pn_sample",
+                  "mp_pn_set_precision", "mp_pn_status"):
             getattr(L, f).restype = C.c_int
         L._pn_declared = True
     return L
@@ -482,6 +485,18 @@ def mp_pn_loss_grad(net, scans, targets, loss, grad=None):
 
 def mp_pn_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     _pn_check(_pn_lib().mp_pn_adam_step(net, float(lr), float(beta1), float(beta2), float(eps)), "mp_pn_adam_step")
+
+
+def mp_pn_set_precision(net, precision):
+    """MP_PREC_BF16: the per-point layers on the tensor cores (the default for
+    scans of a multiple of 128 points); MP_PREC_FP32: on the CUDA cores."""
+    _pn_check(_pn_lib().mp_pn_set_precision(net, int(precision)), "mp_pn_set_precision")
+
+
+def mp_pn_status(net):
+    """Waits for the network's stream; raises MPError (MP_ETIMEOUT) if a
+    bounded wait of the tensor-core forward pass gave up."""
+    _pn_check(_pn_lib().mp_pn_status(net), "mp_pn_status")
 
 
 def mp_pn_sample(net, mix, n, seed, out):

@@ -145,3 +145,134 @@ def test_trained_proposal_localises_faster(torch):
     assert q["trials_with_a_draw_within_tolerance"] > 0.8
     assert lrn["success_rate"] >= uni["success_rate"] - 0.1
     assert lrn["time_to_localise_median"] < uni["time_to_localise_median"]
+
+
+def bf16_round(a):
+    """Round FP32 values to the nearest BF16 (ties to even); returned as float64."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _exact_params(PN, rng):
+    """Parameters on a 1/8 grid in [-1, 1]: products with the inputs below are
+    exact in BF16 and their sums exact in FP32 up to layer 2."""
+    p = np.concatenate([rng.integers(-8, 9, int(np.prod(s))) / 8.0 for s in PN.SHAPES])
+    return p.astype(np.float64)
+
+
+def test_tensor_core_layers_on_exact_inputs(torch):
+    """The fused tensor-core kernel (tcgen05 MMAs from 128-byte-swizzled
+    shared memory, accumulators in TMEM, max-pool in the epilogue) against a
+    float64 evaluation of the same BF16 network: inputs on a 1/4 grid and
+    weights on a 1/8 grid make layer 1 and layer 2 exact in both, layer 2's
+    BF16 rounding is reproduced in numpy, and only layer 3's FP32 summation
+    order differs. A wrong operand layout, swizzle or descriptor would move
+    the outputs by O(1)."""
+    from oracle import proposal as PN
+    from paper_2404_16370_gb300 import mp, proposal as PR
+    B, P = 3, 384
+    net = mp.mp_pn_create(P, B, 1.0, PR.SCALE, PR.OFFSET, seed=3)
+    try:
+        rng = np.random.default_rng(17)
+        p = _exact_params(PN, rng)
+        mp.mp_pn_set_params(net, torch.tensor(p, dtype=torch.float32, device="cuda"))
+        scans = (rng.integers(-8, 9, (B, P, 3)) / 4.0).astype(np.float32)
+        o = torch.empty((B, mp.MP_PN_OUT), device="cuda")
+        mp.mp_pn_forward(net, torch.tensor(scans, device="cuda"), o)
+        mp.mp_pn_status(net)
+        o_tc = o.cpu().numpy().astype(np.float64)
+        W1, b1, W2, b2, W3, b3, W4, b4, W5, b5 = PN.unflatten(p)
+        x = scans.astype(np.float64)
+        h1 = np.maximum(x @ W1 + b1, 0.0)
+        assert np.array_equal(bf16_round(h1), h1)            # layer 1 exact in BF16
+        h2 = np.maximum(h1 @ W2 + b2, 0.0)                   # exact in FP32 accumulation
+        h3 = np.maximum(bf16_round(h2) @ W3 + b3, 0.0)
+        g = h3.max(axis=1)
+        o_ref = np.maximum(g @ W4 + b4, 0.0) @ W5 + b5
+        assert np.abs(o_tc - o_ref).max() <= 1e-5 * np.abs(o_ref).max(), np.abs(o_tc - o_ref).max()
+        # the CUDA-core FP32 path on the same parameters: layer 2 unrounded
+        mp.mp_pn_set_precision(net, mp.MP_PREC_FP32)
+        mp.mp_pn_forward(net, torch.tensor(scans, device="cuda"), o)
+        o32 = o.cpu().numpy().astype(np.float64)
+        g32 = np.maximum(h2 @ W3 + b3, 0.0).max(axis=1)
+        o32_ref = np.maximum(g32 @ W4 + b4, 0.0) @ W5 + b5
+        assert np.abs(o32 - o32_ref).max() <= 1e-5 * np.abs(o32_ref).max()
+    finally:
+        mp.mp_pn_destroy(net)
+
+
+def test_tensor_core_forward_and_gradient_against_oracle(torch):
+    """The BF16 tensor-core form of the per-point layers (FP32 master weights
+    and backward pass) against the FP64 oracle network: forward outputs,
+    loss and every parameter block's gradient within the BF16 tolerance (a
+    few times 2^-8 of each block's scale), on random parameters; and the
+    BF16 form beats the FP32 CUDA-core form on a training-size batch."""
+    import time
+    from oracle import proposal as PN
+    from paper_2404_16370_gb300 import mp, proposal as PR
+    B, P = 4, 256
+    net = mp.mp_pn_create(P, B, PR.IN_SCALE, PR.SCALE, PR.OFFSET, seed=3)
+    try:
+        n = mp.mp_pn_num_params(net)
+        rng = np.random.default_rng(11)
+        p = PN.init_params(5)
+        k = 0
+        for s in PN.SHAPES:
+            m = int(np.prod(s))
+            if len(s) == 1:
+                p[k:k + m] = rng.normal(0, 0.1, m)
+            k += m
+        mp.mp_pn_set_params(net, torch.tensor(p, dtype=torch.float32, device="cuda"))
+        p32 = torch.empty(n, device="cuda")
+        mp.mp_pn_get_params(net, p32)
+        p64 = p32.cpu().numpy().astype(np.float64)
+        scans = rng.normal(0, 3.0, (B, P, 3)).astype(np.float32)
+        y = np.concatenate([rng.normal(0, 1, (B, 3)), rng.uniform(-np.pi, np.pi, (B, 1)),
+                            rng.normal(0, 0.5, (B, 2))], 1).astype(np.float32)
+        xs, ys = torch.tensor(scans, device="cuda"), torch.tensor(y, device="cuda")
+        o = torch.empty((B, mp.MP_PN_OUT), device="cuda")
+        mp.mp_pn_forward(net, xs, o)
+        loss = torch.zeros(1, device="cuda")
+        grad = torch.empty(n, device="cuda")
+        mp.mp_pn_loss_grad(net, xs, ys, loss, grad)
+        mp.mp_pn_status(net)
+        ref = PN.forward(p64, scans.astype(np.float64), PR.IN_SCALE)
+        L_ref, g_ref = PN.loss_grad(p64, scans.astype(np.float64), y.astype(np.float64), PR.IN_SCALE)
+        o_gpu = o.cpu().numpy()
+        assert np.abs(o_gpu - ref["o"]).max() <= 2e-2 * max(1.0, np.abs(ref["o"]).max())
+        assert abs(float(loss.item()) - L_ref) <= 2e-2 * max(1.0, abs(L_ref))
+        g = grad.cpu().numpy()
+        k = 0
+        for s in PN.SHAPES:
+            m = int(np.prod(s))
+            gb, rb = g[k:k + m], g_ref[k:k + m]
+            rel = np.linalg.norm(gb - rb) / (np.linalg.norm(rb) + 1e-12)
+            print(f"grad block {s}: relative error {rel:.2e}")
+            assert rel <= 5e-2, (s, rel)
+            k += m
+    finally:
+        mp.mp_pn_destroy(net)
+    # speed on a training-size batch: 128 scans of 1024 points
+    B, P = 128, 1024
+    net = mp.mp_pn_create(P, B, PR.IN_SCALE, PR.SCALE, PR.OFFSET, seed=3)
+    try:
+        xs = torch.tensor(rng.normal(0, 3.0, (B, P, 3)).astype(np.float32), device="cuda")
+        o = torch.empty((B, mp.MP_PN_OUT), device="cuda")
+        ms = {}
+        for prec in (mp.MP_PREC_FP32, mp.MP_PREC_BF16):
+            mp.mp_pn_set_precision(net, prec)
+            for _ in range(3):
+                mp.mp_pn_forward(net, xs, o)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(20):
+                mp.mp_pn_forward(net, xs, o)
+            torch.cuda.synchronize()
+            ms[prec] = (time.perf_counter() - t0) / 20 * 1e3
+        mp.mp_pn_status(net)
+        print(f"forward of 128 x 1024 points: FP32 CUDA cores {ms[mp.MP_PREC_FP32]:.3f} ms, "
+              f"BF16 tensor cores {ms[mp.MP_PREC_BF16]:.3f} ms")
+        assert ms[mp.MP_PREC_BF16] < ms[mp.MP_PREC_FP32]
+    finally:
+        mp.mp_pn_destroy(net)
