@@ -12,6 +12,12 @@ include/mp_proposal.h:
 The gradient is the chain rule written out layer by layer (ReLU passes where
 its output is positive, max-pool to the first maximum). Its correctness is
 pinned by central finite differences of `loss`, not by itself.
+
+bf16=True gives the network the tensor-core form computes: the per-point
+activations h1 and h2 and the weights W2, W3 of the forward products rounded
+to BF16 (round to nearest, ties to even, from their FP32 values); the
+backward pass uses the FP32 weights and the rounded activations, as the GPU
+form does.
 """
 from __future__ import annotations
 
@@ -37,13 +43,21 @@ def wrap_pi(a):
     return np.where(a <= -np.pi, a + 2 * np.pi, a)
 
 
-def forward(p, scans, in_scale):
+def bf16(a):
+    """The nearest BF16 value (ties to even) of each value's FP32 rounding, as float64."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(p, scans, in_scale, bf16_form=False):
     """Layer outputs of B scans (B, P, 3)."""
     W1, b1, W2, b2, W3, b3, W4, b4, W5, b5 = unflatten(p)
+    r = bf16 if bf16_form else (lambda a: a)
     x = np.asarray(scans, np.float64) / in_scale
-    h1 = np.maximum(x @ W1 + b1, 0.0)
-    h2 = np.maximum(h1 @ W2 + b2, 0.0)
-    h3 = np.maximum(h2 @ W3 + b3, 0.0)
+    h1 = r(np.maximum(x @ W1 + b1, 0.0))
+    h2 = r(np.maximum(h1 @ r(W2) + b2, 0.0))
+    h3 = np.maximum(h2 @ r(W3) + b3, 0.0)
     gi = np.argmax(h3, axis=1)                        # first maximum
     g = np.take_along_axis(h3, gi[:, None, :], axis=1)[:, 0, :]
     h4 = np.maximum(g @ W4 + b4, 0.0)
@@ -74,10 +88,11 @@ def loss(p, scans, y, in_scale):
     return float(np.mean(nll(forward(p, scans, in_scale)["o"], y)))
 
 
-def loss_grad(p, scans, y, in_scale):
-    """(mean loss, gradient w.r.t. the flat parameter array)."""
+def loss_grad(p, scans, y, in_scale, bf16_form=False):
+    """(mean loss, gradient w.r.t. the flat parameter array); bf16_form: of the
+    tensor-core form (see the module docstring)."""
     W1, b1, W2, b2, W3, b3, W4, b4, W5, b5 = unflatten(p)
-    f = forward(p, scans, in_scale)
+    f = forward(p, scans, in_scale, bf16_form)
     o = f["o"]
     B = o.shape[0]
     a, m, r = _parts(o)

@@ -204,10 +204,13 @@ def test_tensor_core_layers_on_exact_inputs(torch):
 
 def test_tensor_core_forward_and_gradient_against_oracle(torch):
     """The BF16 tensor-core form of the per-point layers (FP32 master weights
-    and backward pass) against the FP64 oracle network: forward outputs,
-    loss and every parameter block's gradient within the BF16 tolerance (a
-    few times 2^-8 of each block's scale), on random parameters; and the
-    BF16 form beats the FP32 CUDA-core form on a training-size batch."""
+    and backward pass) against the oracle: element by element against the
+    oracle's BF16 form of the network (the same roundings; FP32 against FP64
+    sums), and against the plain FP64 network within the BF16 tolerance
+    stated here (outputs and loss 2e-2 of their scale; gradient blocks 0.25
+    in relative norm, where a BF16 rounding that moves a channel's max-pool to
+    another point moves that channel's whole gradient path); and the BF16
+    form beats the FP32 CUDA-core form on a training-size batch."""
     import time
     from oracle import proposal as PN
     from paper_2404_16370_gb300 import mp, proposal as PR
@@ -237,20 +240,24 @@ def test_tensor_core_forward_and_gradient_against_oracle(torch):
         grad = torch.empty(n, device="cuda")
         mp.mp_pn_loss_grad(net, xs, ys, loss, grad)
         mp.mp_pn_status(net)
-        ref = PN.forward(p64, scans.astype(np.float64), PR.IN_SCALE)
-        L_ref, g_ref = PN.loss_grad(p64, scans.astype(np.float64), y.astype(np.float64), PR.IN_SCALE)
-        o_gpu = o.cpu().numpy()
-        assert np.abs(o_gpu - ref["o"]).max() <= 2e-2 * max(1.0, np.abs(ref["o"]).max())
-        assert abs(float(loss.item()) - L_ref) <= 2e-2 * max(1.0, abs(L_ref))
-        g = grad.cpu().numpy()
-        k = 0
-        for s in PN.SHAPES:
-            m = int(np.prod(s))
-            gb, rb = g[k:k + m], g_ref[k:k + m]
-            rel = np.linalg.norm(gb - rb) / (np.linalg.norm(rb) + 1e-12)
-            print(f"grad block {s}: relative error {rel:.2e}")
-            assert rel <= 5e-2, (s, rel)
-            k += m
+        o_gpu, g = o.cpu().numpy(), grad.cpu().numpy()
+        s64, y64 = scans.astype(np.float64), y.astype(np.float64)
+        for form, o_tol, g_tol in ((True, 1e-5, 1e-5), (False, 2e-2, 0.25)):
+            ref = PN.forward(p64, s64, PR.IN_SCALE, bf16_form=form)
+            L_ref, g_ref = PN.loss_grad(p64, s64, y64, PR.IN_SCALE, bf16_form=form)
+            name = "BF16 form" if form else "plain FP64"
+            err_o = np.abs(o_gpu - ref["o"]).max() / max(1.0, np.abs(ref["o"]).max())
+            print(f"\n{name}: outputs {err_o:.2e}, loss {abs(float(loss.item()) - L_ref):.2e}")
+            assert err_o <= o_tol
+            assert abs(float(loss.item()) - L_ref) <= o_tol * max(1.0, abs(L_ref))
+            k = 0
+            for s in PN.SHAPES:
+                m = int(np.prod(s))
+                gb, rb = g[k:k + m], g_ref[k:k + m]
+                rel = np.linalg.norm(gb - rb) / (np.linalg.norm(rb) + 1e-12)
+                print(f"{name}: gradient block {s}: relative error {rel:.2e}")
+                assert rel <= g_tol, (name, s, rel)
+                k += m
     finally:
         mp.mp_pn_destroy(net)
     # speed on a training-size batch: 128 scans of 1024 points
