@@ -39,22 +39,30 @@ def pose_errors(a, b):
 
 
 def make_trials(n_trials, n_particles, seed0=100):
+    """Trials (true pose, its scan, the seed and size of the initial particle
+    set); the particles are drawn when a trial runs (trial_particles), so that
+    large sets are never held for every trial at once."""
     room = synth.box_room(1)
     dirs = synth.spherical_dirs(512)
     trials = []
     for t in range(n_trials):
         gt = synth.box_room_gt_pose(room, seed0 + t)
         sc = synth.scan(room, gt, dirs, 0.02, seed0 + t)
-        parts = synth.box_room_particles(n_particles, seed=10_000 + seed0 + t, half=room.half)
-        trials.append((gt, sc, parts))
+        trials.append((gt, sc, 10_000 + seed0 + t, n_particles))
     return room, trials
+
+
+def trial_particles(room, trial):
+    """The trial's uniform initial particle set (n x 7)."""
+    return synth.box_room_particles(trial[3], seed=trial[2], half=room.half)
 
 
 def run(room, trials, precision, max_steps, seeding=None, stream=None, svgd_precond=0):
     """Errors (trials, max_steps, 2) of the representative state per step.
-    seeding(trial_index, scan, particles) -> particles replaces the initial set;
-    svgd_precond selects the SVGD reading (mp_params.svgd_precond)."""
-    n = len(trials[0][2])
+    seeding(trial_index, scan, particles) -> particles (numpy or a CUDA
+    tensor) replaces the initial set; svgd_precond selects the SVGD reading
+    (mp_params.svgd_precond)."""
+    n = trials[0][3]
     params = mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, n)
     params.svgd_precond = int(svgd_precond)
     ctx = mp.mp_init_map(room.map_points, params, cuda_stream=stream)
@@ -62,7 +70,8 @@ def run(room, trials, precision, max_steps, seeding=None, stream=None, svgd_prec
     out = np.zeros((len(trials), max_steps, 2))
     try:
         mp.mp_set_precision(ctx, PRECISIONS[precision])
-        for t, (gt, sc, parts) in enumerate(trials):
+        for t, (gt, sc, _, _) in enumerate(trials):
+            parts = trial_particles(room, trials[t])
             p0 = parts if seeding is None else seeding(t, sc, parts)
             mp.mp_init_particles(ctx, n, poses=p0)
             mp.mp_set_step_index(ctx, 0)

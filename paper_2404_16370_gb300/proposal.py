@@ -130,15 +130,17 @@ class Proposal:
 
 def seeding_from(prop, sim, trials, frac=0.9, seed=0):
     """Seeding callback for localise.run: frac of the particles from the mixture
-    of the trial's 1024-ray scan, the rest kept from the uniform set."""
+    of the trial's 1024-ray scan, the rest kept from the uniform set (a CUDA
+    tensor: the drawn poses never leave the device)."""
+    import torch
+
     def seed_fn(t, _scan, parts):
         gt = trials[t][0]
         sc = sim.scans(gt[None], 0.02, seed + 7919 * (t + 1))
         mix = prop.mixture(sc)
         n_mix = int(round(frac * len(parts)))
-        drawn = prop.sample(mix[0], n_mix, seed + t).cpu().numpy()
-        out = parts.copy()
-        out[:n_mix] = drawn
+        out = torch.from_numpy(np.ascontiguousarray(parts)).to(sc.device)
+        out[:n_mix] = prop.sample(mix[0], n_mix, seed + t)
         return out
     return seed_fn
 
@@ -150,7 +152,8 @@ def proposal_quality(prop, sim, trials, n=4096, seed=0):
     of the same size reaches in a few per cent of trials)."""
     import torch
     best_d, best_a, hit = [], [], []
-    for t, (gt, _, _) in enumerate(trials):
+    for t, trial in enumerate(trials):
+        gt = trial[0]
         sc = sim.scans(gt[None], 0.02, seed + 7919 * (t + 1))
         mix = prop.mixture(sc)[0]
         c = int(torch.argmax(mix[:32]).item())
@@ -198,6 +201,8 @@ def main():
         del scans
         print(json.dumps({"train_samples": a.samples, "epochs": a.epochs, "batch": a.batch, "data_s": round(t_data, 2),
                           "train_s": round(t_train, 2), "loss_per_epoch": [round(h, 4) for h in hist]}), flush=True)
+        if a.trials <= 0:
+            return
         _, trials = localise.make_trials(a.trials, a.particles, seed0=100 + a.seed)
         print(json.dumps({"proposal_quality": proposal_quality(prop, sim, trials, a.particles, seed=a.seed)}),
               flush=True)
