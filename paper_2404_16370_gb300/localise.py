@@ -57,14 +57,17 @@ def trial_particles(room, trial):
     return synth.box_room_particles(trial[3], seed=trial[2], half=room.half)
 
 
-def run(room, trials, precision, max_steps, seeding=None, stream=None, svgd_precond=0):
+def run(room, trials, precision, max_steps, seeding=None, stream=None, svgd_precond=0, post_floor=None):
     """Errors (trials, max_steps, 2) of the representative state per step.
     seeding(trial_index, scan, particles) -> particles (numpy or a CUDA
     tensor) replaces the initial set; svgd_precond selects the SVGD reading
-    (mp_params.svgd_precond)."""
+    (mp_params.svgd_precond); post_floor (None: the default) the posterior
+    floor in nats (mp_params.post_floor; 0: none)."""
     n = trials[0][3]
     params = mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, n)
     params.svgd_precond = int(svgd_precond)
+    if post_floor is not None:
+        params.post_floor = float(post_floor)
     ctx = mp.mp_init_map(room.map_points, params, cuda_stream=stream)
     eye, zero = np.eye(4), np.zeros((6, 6))
     out = np.zeros((len(trials), max_steps, 2))
@@ -109,16 +112,19 @@ def main():
     ap.add_argument("--precision", default="fp32,bf16,fp16")
     ap.add_argument("--seed", type=int, default=100)
     ap.add_argument("--svgd-precond", default="0", help="comma list of mp_params.svgd_precond values")
+    ap.add_argument("--post-floor", default="700", help="comma list of mp_params.post_floor values (nats; 0: none)")
     a = ap.parse_args()
     room, trials = make_trials(a.trials, a.particles, a.seed)
-    for pre in (int(v) for v in a.svgd_precond.split(",")):
-        for prec in a.precision.split(","):
-            t0 = time.perf_counter()
-            errs = run(room, trials, prec, a.max_steps, svgd_precond=pre)
-            res = {"scene": "box_room", "precision": prec, "svgd_precond": pre, "seeding": "uniform",
-                   "particles": a.particles, "max_steps": a.max_steps, "wall_s": round(time.perf_counter() - t0, 2),
-                   **summarise(errs)}
-            print(json.dumps(res), flush=True)
+    for floor in (float(v) for v in a.post_floor.split(",")):
+        for pre in (int(v) for v in a.svgd_precond.split(",")):
+            for prec in a.precision.split(","):
+                t0 = time.perf_counter()
+                errs = run(room, trials, prec, a.max_steps, svgd_precond=pre, post_floor=floor)
+                res = {"scene": "box_room", "precision": prec, "svgd_precond": pre, "post_floor": floor,
+                       "seeding": "uniform", "particles": a.particles, "max_steps": a.max_steps,
+                       "wall_s": round(time.perf_counter() - t0, 2), **summarise(errs)}
+                res.pop("steps_to_localise")
+                print(json.dumps(res), flush=True)
 
 
 if __name__ == "__main__":
