@@ -184,31 +184,6 @@ __device__ __forceinline__ Lk2Look lk2_none() {
     return L;
 }
 
-// Points whose NNF sectors are prefetched into L2 ahead of the pipeline's own
-// loads (which fetch point k + 2's entries while point k is accumulated): the
-// voxel of point k + LK_PF is computed again and its sector requested with
-// prefetch.global.L2, which holds no register until the data arrives.
-constexpr int LK_PF = 6;
-
-__device__ __forceinline__ void lk2_prefetch(const LkArgs& A, const float2 R[9], float2 tx, float2 ty, float2 tz,
-                                             const float4* Pp) {
-    const float4 p0 = Pp[0], p1 = Pp[1];
-    const float2 mx = make_float2(p0.x, p0.y), my = make_float2(p0.z, p0.w), mz = make_float2(p1.x, p1.y);
-    const float2 qx = add2(fma2(R[2], mz, fma2(R[1], my, mul2(R[0], mx))), tx);
-    const float2 qy = add2(fma2(R[5], mz, fma2(R[4], my, mul2(R[3], mx))), ty);
-    const float2 qz = add2(fma2(R[8], mz, fma2(R[7], my, mul2(R[6], mx))), tz);
-    const float2 fx = __fadd2_rd(fma2(qx, A.inv2, A.offx2), A.magic2);
-    const float2 fy = __fadd2_rd(fma2(qy, A.inv2, A.offy2), A.magic2);
-    const float2 fz = __fadd2_rd(fma2(qz, A.inv2, A.offz2), A.magic2);
-    const unsigned vxa = __float_as_uint(fx.x) - 0x4B400000u, vxb = __float_as_uint(fx.y) - 0x4B400000u;
-    const unsigned vya = __float_as_uint(fy.x) - 0x4B400000u, vyb = __float_as_uint(fy.y) - 0x4B400000u;
-    const unsigned vza = __float_as_uint(fz.x) - 0x4B400000u, vzb = __float_as_uint(fz.y) - 0x4B400000u;
-    if (vxa < (unsigned)A.nx && vya < (unsigned)A.ny && vza < (unsigned)A.nz)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(A.nnf + (((int)vza * A.ny + (int)vya) * A.nx + (int)vxa)));
-    if (vxb < (unsigned)A.nx && vyb < (unsigned)A.ny && vzb < (unsigned)A.nz)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(A.nnf + (((int)vzb * A.ny + (int)vyb) * A.nx + (int)vxb)));
-}
-
 // One 32-byte map record (a 32-byte-aligned pair of float4, read-only in the
 // kernel) in one 256-bit load: (mu.xyz, w.x) and (w.y, w.z); the last two
 // words are padding.
@@ -425,7 +400,6 @@ __device__ __forceinline__ void LkOp<SPLIT>::run(const LkArgs& A, unsigned bxi, 
             lk2_record(A, sc.mb, rb0, rb1);
             if (m > 1) sb = lk2_lookup(A, R, tx, ty, tz, P + 3);
             for (int k = 0; k < m; ++k) {
-                if (k + LK_PF < m) lk2_prefetch(A, R, tx, ty, tz, P + 3 * (k + LK_PF));
                 const Lk2Look nb = (k + 2 < m) ? lk2_lookup(A, R, tx, ty, tz, P + 3 * (k + 2)) : lk2_none();
                 float4 na0, nb0;
                 float2 na1, nb1;
