@@ -4,10 +4,13 @@
 //
 // Layout: activations row-major [rows][channels] in FP32, rows = batch x
 // points for the shared per-point layers and = batch for the head. Every
-// dense layer is one tiled GEMM (64 x 64 output tile per CTA, 16-deep K
-// slices in shared memory, 4 x 4 outputs per thread) with the bias and ReLU
-// fused into the store; weight gradients reduce over the batch x points rows
-// with split-K CTAs adding into the gradient by atomics.
+// dense layer of the FP32 form is one tiled GEMM (64 x 64 output tile per
+// CTA, 16-deep K slices in shared memory, 4 x 4 outputs per thread) with the
+// bias and ReLU fused into the store; weight gradients reduce over rows with
+// split-K CTAs adding into the gradient by atomics. The BF16 form's forward
+// pass through the per-point layers is one tensor-core kernel (k_pn_tc.cu).
+// The backward pass through the per-point layers runs on the max-pooled rows
+// only (k_pool_rows).
 #include "mp_internal.cuh"
 #include "../../include/mp_proposal.h"
 
@@ -199,14 +202,40 @@ __global__ void k_maxpool(const float* __restrict__ h3, int B, int P, float* __r
     gi[b * C3 + c] = mi;
 }
 
-// dh3 (zeroed) gets dg at the pooled point of each channel; ReLU of layer 3
-// at that point passes it when g > 0
-__global__ void k_maxpool_back(const float* __restrict__ dg, const float* __restrict__ g, const int* __restrict__ gi,
-                               int B, int P, float* __restrict__ dh3) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
-    if (c >= C3 || b >= B) return;
-    if (g[b * C3 + c] > 0.f) dh3[((int64_t)b * P + gi[b * C3 + c]) * C3 + c] = dg[b * C3 + c];
+__global__ void k_pool_rows(const float* __restrict__ dg, const float* __restrict__ g, const int* __restrict__ gi,
+                            const float* __restrict__ xs, const float* __restrict__ h1, const float* __restrict__ h2,
+                            const float* __restrict__ W3, int B, int P, float* __restrict__ xc,
+                            float* __restrict__ h1c, float* __restrict__ h2c, float* __restrict__ dh2c) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // r = b * 256 + c
+    if (r >= (int64_t)B * C3) return;
+    const int64_t b = r / C3;
+    const int c = (int)(r % C3);
+    const float d = g[r] > 0.f ? dg[r] : 0.f;
+    const int64_t row = b * P + gi[r];
+    for (int k = 0; k < 3; ++k) xc[r * 3 + k] = xs[row * 3 + k];
+    for (int k = 0; k < C1; ++k) h1c[r * C1 + k] = h1[row * C1 + k];
+    for (int i = 0; i < C2; ++i) {
+        const float h = h2[row * C2 + i];
+        h2c[r * C2 + i] = h;
+        dh2c[r * C2 + i] = h > 0.f ? d * W3[i * C3 + c] : 0.f;
+    }
+}
+
+// dW3[i][c] += sum_b dg[b][c] h2[b, gi[b][c], i] (pooled, gated) and db3[c]
+__global__ void k_dw3(const float* __restrict__ dg, const float* __restrict__ g, const int* __restrict__ gi,
+                      const float* __restrict__ h2, int B, int P, float* __restrict__ dW3, float* __restrict__ db3) {
+    const int c = blockIdx.x;          // channel
+    const int i = threadIdx.x;         // input channel (C2 threads)
+    float acc = 0.f, bacc = 0.f;
+    for (int b = 0; b < B; ++b) {
+        const int64_t r = (int64_t)b * C3 + c;
+        if (!(g[r] > 0.f)) continue;
+        const float d = dg[r];
+        acc = fmaf(d, h2[((int64_t)b * P + gi[r]) * C2 + i], acc);
+        bacc += d;
+    }
+    dW3[i * C3 + c] += acc;
+    if (i == 0) db3[c] += bacc;
 }
 
 __device__ __forceinline__ float wrap_pi(float a) {
@@ -354,7 +383,8 @@ struct mp_pn {
     int64_t t;       // Adam step
     float *xs, *h1, *h2, *h3, *g, *h4, *o;
     int* gi;
-    float *dO, *dh4, *dg, *dh3, *dh2, *dh1;
+    float *dO, *dh4, *dg;
+    float *xc, *h1c, *h2c, *dh2c, *dh1c;   // compact rows (b, channel) of the backward pass
     uint2 key;
     int prec;          // MP_PREC_BF16: per-point layers on the tensor cores; MP_PREC_FP32: CUDA cores
     uint8_t* wimg;     // BF16 image of W2^T and W3^T for the tensor-core kernel
@@ -465,7 +495,9 @@ int mp_pn_create(mp_pn** netp, int n_points, int max_batch, float in_scale, cons
     A(&net->g, (size_t)max_batch * C3); A(&net->gi, (size_t)max_batch * C3); A(&net->h4, (size_t)max_batch * C4);
     A(&net->o, (size_t)max_batch * NOUT); A(&net->dO, (size_t)max_batch * NOUT);
     A(&net->dh4, (size_t)max_batch * C4); A(&net->dg, (size_t)max_batch * C3);
-    A(&net->dh3, rows * C3); A(&net->dh2, rows * C2); A(&net->dh1, rows * C1);
+    const int64_t rows_c = (int64_t)max_batch * C3;
+    A(&net->xc, rows_c * 3); A(&net->h1c, rows_c * C1); A(&net->h2c, rows_c * C2); A(&net->dh2c, rows_c * C2);
+    A(&net->dh1c, rows_c * C1);
     A(&net->wimg, mp_pn_tc_image_bytes()); A(&net->err, 1);
     if (e != cudaSuccess) {
         mp_pn_destroy(net);
@@ -489,8 +521,8 @@ int mp_pn_create(mp_pn** netp, int n_points, int max_batch, float in_scale, cons
 int mp_pn_destroy(mp_pn* net) {
     if (!net) return mp_fail_noctx(MP_EINVAL, "mp_pn_destroy: invalid argument");
     void* bufs[] = {net->scale, net->offset, net->param, net->grad, net->am, net->av, net->xs, net->h1,
-                    net->h2, net->h3, net->g, net->gi, net->h4, net->o, net->dO, net->dh4, net->dg, net->dh3,
-                    net->dh2, net->dh1, net->wimg, net->err};
+                    net->h2, net->h3, net->g, net->gi, net->h4, net->o, net->dO, net->dh4, net->dg, net->xc,
+                    net->h1c, net->h2c, net->dh2c, net->dh1c, net->wimg, net->err};
     for (void* p : bufs)
         if (p) cudaFree(p);
     delete net;
@@ -545,22 +577,19 @@ int mp_pn_loss_grad(mp_pn* net, const float* scans, const float* targets, int B,
     gemm<true, false, EPI_ATOMIC>(s, net->g, net->dh4, G + OW4, nullptr, C3, C4, B, C3, C4, C4);
     colsum(s, net->dh4, B, C4, G + OB4);
     gemm<false, true, 0>(s, net->dh4, W + OW4, net->dg, nullptr, B, C3, C4, C4, C4, C3);
-    // max-pool and the shared layers
-    PN_CUDA(cudaMemsetAsync(net->dh3, 0, sizeof(float) * rows * C3, s));
-    k_maxpool_back<<<dim3(C3 / 128, B), 128, 0, s>>>(net->dg, net->g, net->gi, B, net->P, net->dh3);
-    gemm<true, false, EPI_ATOMIC>(s, net->h2, net->dh3, G + OW3, nullptr, C2, C3, (int)rows, C2, C3, C3,
-                                  splits_for(rows, C2, C3));
-    colsum(s, net->dh3, rows, C3, G + OB3);
-    gemm<false, true, 0>(s, net->dh3, W + OW3, net->dh2, nullptr, (int)rows, C2, C3, C3, C3, C2);
-    k_relu_back<<<grid_for(rows * C2, 256), 256, 0, s>>>(net->dh2, net->h2, rows * C2);
-    gemm<true, false, EPI_ATOMIC>(s, net->h1, net->dh2, G + OW2, nullptr, C1, C2, (int)rows, C1, C2, C2,
-                                  splits_for(rows, C1, C2));
-    colsum(s, net->dh2, rows, C2, G + OB2);
-    gemm<false, true, 0>(s, net->dh2, W + OW2, net->dh1, nullptr, (int)rows, C1, C2, C2, C2, C1);
-    k_relu_back<<<grid_for(rows * C1, 256), 256, 0, s>>>(net->dh1, net->h1, rows * C1);
-    gemm<true, false, EPI_ATOMIC>(s, net->xs, net->dh1, G + OW1, nullptr, 3, C1, (int)rows, 3, C1, C1,
-                                  splits_for(rows, 3, C1));
-    colsum(s, net->dh1, rows, C1, G + OB1);
+    // max-pool and the shared layers, on the pooled rows (b, channel) only
+    const int64_t rows_c = (int64_t)B * C3;
+    k_dw3<<<C3, C2, 0, s>>>(net->dg, net->g, net->gi, net->h2, B, net->P, G + OW3, G + OB3);
+    k_pool_rows<<<grid_for(rows_c, 256), 256, 0, s>>>(net->dg, net->g, net->gi, net->xs, net->h1, net->h2, W + OW3, B,
+                                                      net->P, net->xc, net->h1c, net->h2c, net->dh2c);
+    gemm<true, false, EPI_ATOMIC>(s, net->h1c, net->dh2c, G + OW2, nullptr, C1, C2, (int)rows_c, C1, C2, C2,
+                                  splits_for(rows_c, C1, C2));
+    colsum(s, net->dh2c, rows_c, C2, G + OB2);
+    gemm<false, true, 0>(s, net->dh2c, W + OW2, net->dh1c, nullptr, (int)rows_c, C1, C2, C2, C2, C1);
+    k_relu_back<<<grid_for(rows_c * C1, 256), 256, 0, s>>>(net->dh1c, net->h1c, rows_c * C1);
+    gemm<true, false, EPI_ATOMIC>(s, net->xc, net->dh1c, G + OW1, nullptr, 3, C1, (int)rows_c, 3, C1, C1,
+                                  splits_for(rows_c, 3, C1));
+    colsum(s, net->dh1c, rows_c, C1, G + OB1);
     PN_CUDA(cudaGetLastError());
     if (grad_out) PN_CUDA(cudaMemcpyAsync(grad_out, G, sizeof(float) * NPARAM, cudaMemcpyDefault, s));
     return MP_OK;
