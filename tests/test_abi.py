@@ -97,3 +97,18 @@ def test_checked_build_exports_the_same_symbols(built):
     missing = [n for n in declared(HEADERS) if n not in exported]
     assert not missing, missing
     assert "mp_checked_sync" in out   # the host side of the checks is compiled in
+
+
+def test_post_floor_is_validated_before_any_device_work(built):
+    """mp_params.post_floor outside [0, 700] nats is refused by mp_init_map
+    (parameters are checked before anything touches the device)."""
+    import ctypes as C
+    from paper_2404_16370_gb300 import mp
+    L = mp.lib()
+    pts = (C.c_float * 3)(0.0, 0.0, 0.0)
+    for bad in (-1.0, 701.0, float("nan")):
+        p = mp.mp_default_params(mp.MP_PRESET_BOX_ROOM, 64, post_floor=bad)
+        ctx = C.c_void_p()
+        assert L.mp_init_map(C.byref(ctx), pts, 1, C.byref(p), None) == mp.MP_EINVAL
+        assert "post_floor" in mp.mp_last_error(None)
+    assert mp.mp_default_params(mp.MP_PRESET_OUTDOOR, 64).post_floor == 700.0
