@@ -34,5 +34,5 @@ def test_localisation_statistics_match_the_oracle(oracle, precond):
     assert abs(g["success_rate"] - o["success_rate"]) <= 0.15
     if g["localised"] >= 5 and o["localised"] >= 5:
         assert abs(g["time_to_localise_median"] - o["time_to_localise_median"]) <= 2
-    # the first steps are exact up to rounding, so most trials end alike
-    assert same >= 0.6
+    # the first steps are exact up to rounding, so most trials end alike (last run: all of them)
+    assert same >= 0.8
