@@ -166,7 +166,7 @@ const char* mp_last_error(const mp_ctx* ctx);
 #define MP_STAGE_PREDICT 0x001u      /* Eq. 1                                   */
 #define MP_STAGE_SCAN 0x002u         /* scan Gaussians + compaction             */
 #define MP_STAGE_LSH 0x004u          /* Eq. 9-10 keys (draws T^LSH, delta^LSH)  */
-#define MP_STAGE_SORT 0x008u         /* Algorithm 1 distribute: stable sort     */
+#define MP_STAGE_SORT 0x008u         /* Algorithm 1 distribute: stable sort (and the likelihood's visiting order) */
 #define MP_STAGE_MERGE 0x010u        /* Algorithm 1 gather + list refinement    */
 #define MP_STAGE_LIKELIHOOD 0x020u   /* Eq. 2-4 sums                            */
 #define MP_STAGE_SOLVE 0x040u        /* psi = GN step                           */
@@ -209,6 +209,11 @@ int mp_set_step_index(mp_ctx* ctx, uint64_t step);
 #define MP_BUF_MAP_VALID 18    /* n_map uint8              r                      */
 #define MP_BUF_LSH 19          /* 13 float64: T^LSH q (4), t (3), delta (6)  r    */
 #define MP_BUF_PHI 20          /* n x 6 float32 SVGD update r                     */
+#define MP_BUF_VISIT_ORDER 21  /* n int32 the likelihood's visiting order: particle ids by the Morton code
+                                  of their position's cell (cubes of 2^s NNF voxels, s the smallest
+                                  shift leaving at most 32 cubes along every NNF axis, positions
+                                  clamped to the grid), LSH order (MP_BUF_SORTED_IDS) within a cell.
+                                  Written by MP_STAGE_SORT; no result depends on it.  r */
 
 /* Element count of a buffer (0 if not allocated). */
 int mp_buffer_size(mp_ctx* ctx, int which, int64_t* count);

@@ -23,10 +23,14 @@
 // and add; each half rounds exactly as the scalar instruction, so the decision
 // sequences are unchanged and the per-pair instruction count roughly halves).
 // Every per-pair value is a float2 holding particle a in .x and particle b in
-// .y. Particles are visited in the order of the LSH sort (neighbouring poses
-// share CTAs, so their NNF and record gathers share L1 lines once the filter
-// has converged); a thread takes sorted slots p and p + 128, so each half of a
-// warp covers 32 consecutive slots. The scan streams through shared memory in
+// .y. Particles are visited in the order the sort stage leaves for this
+// kernel: by the cell of their position (a coarse Morton order), in LSH order
+// within a cell. The CTAs resident at one time then hold particles of one part
+// of the map, whose scans fall on a part of the NNF grid that stays in L2
+// (in LSH order they are spread over the whole map and most lookups miss L2),
+// and neighbouring poses share CTAs, so their NNF and record gathers share L1
+// lines once the filter has converged. A thread takes slots p and p + 128 of
+// that order, so each half of a warp covers 32 consecutive slots. The scan streams through shared memory in
 // chunks of 256 points stored as broadcast pairs (48 bytes a point), double-
 // buffered with 1-D bulk copies (TMA, cp.async.bulk) completing on mbarriers,
 // and every thread of a warp reads the same point. The two dependent gathers
@@ -722,7 +726,7 @@ namespace {
 LkArgs lk_args(mp_ctx* c) {
     LkArgs A;
     A.poses = c->poses[c->cur];
-    A.order = c->sorted_ids;
+    A.order = c->visit;
     A.n = c->n;
     A.scan = c->scan_pair;
     A.nvalid = c->scan_nvalid;

@@ -373,6 +373,65 @@ struct SegmentsOp {
 __global__ void __launch_bounds__(256) k_segments(const SortArgs A) { SegmentsOp::run(A, blockIdx.x, 0); }
 
 // ---------------------------------------------------------------------------
+// visiting order of the likelihood
+// ---------------------------------------------------------------------------
+// Every particle's sums (Eq. 2-4) are computed by one thread from its own pose
+// alone, so the order in which particles are assigned to threads changes no
+// result. It decides which NNF sectors the CTAs resident at one time touch:
+// in LSH order (Eq. 9-10 hashes pose cells to random buckets) those particles
+// are spread over the whole map and nearly every lookup misses L2, while in
+// the order of their position the resident particles share the part of the
+// grid their scans fall on. The key is the Morton code of the particle's cell
+// in a grid of cubes of 2^shift NNF voxels (at most 32 cubes along an axis,
+// positions outside the NNF grid clamped to its border); a stable radix sort
+// of (key, id) pairs that start in LSH order keeps LSH order within a cell.
+struct VisitKeyArgs {
+    const float4* poses;
+    const int32_t* lsh_order;
+    int64_t n;
+    float inv_res, off[3];
+    int dims[3];
+    int shift;
+    uint32_t* keys;
+    int32_t* ids;
+};
+
+// the low 5 bits of v moved to every third bit
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+struct VisitKeyOp {
+    using Args = VisitKeyArgs;
+    static constexpr int THREADS = 256, MINB = 1;
+    static __device__ __forceinline__ void run(const VisitKeyArgs& A, unsigned bx, unsigned) {
+        const int64_t p = (int64_t)bx * THREADS + threadIdx.x;
+        if (p >= A.n) return;
+        int32_t i = A.lsh_order[p];
+        if (!MP_DCHECK(i >= 0 && i < A.n, "LSH order entry", i)) i = 0;
+        const float4 t = A.poses[2 * (int64_t)i + 1];
+        const float x[3] = {t.x, t.y, t.z};
+        uint32_t key = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // voxel coordinate as a product and a sum (no contraction in this
+            // file); NaN and coordinates below the grid go to cell 0, those
+            // above it (the conversion saturates) to the last voxel's cell
+            const float f = x[a] * A.inv_res + A.off[a];
+            const int v = (f >= 0.f) ? min((int)f, A.dims[a] - 1) : 0;
+            key |= spread3((uint32_t)(v >> A.shift)) << a;
+        }
+        A.keys[p] = key;
+        A.ids[p] = i;
+    }
+};
+
+__global__ void __launch_bounds__(256) k_visit_keys(const VisitKeyArgs A) { VisitKeyOp::run(A, blockIdx.x, 0); }
+
+// ---------------------------------------------------------------------------
 // neighbour merge: one warp per particle, 64 candidate slots (2 per lane)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cand_eval(const float4* __restrict__ poses, int j, const Quat& qic, const float Rit[9],
@@ -600,6 +659,41 @@ SortArgs sort_args(mp_ctx* c) {
     return A;
 }
 
+// 32 cubes or fewer along the longest NNF axis
+int visit_shift(const mp_ctx* c) {
+    const int dmax = std::max(c->nnf_dims[0], std::max(c->nnf_dims[1], c->nnf_dims[2]));
+    int s = 0;
+    while ((dmax - 1) >> s >= 32) ++s;
+    return s;
+}
+
+VisitKeyArgs visit_key_args(mp_ctx* c) {
+    VisitKeyArgs A;
+    A.poses = c->poses[c->cur];
+    A.lsh_order = c->sorted_ids;
+    A.n = c->n;
+    A.inv_res = c->nnf_inv_res;
+    for (int a = 0; a < 3; ++a) {
+        A.off[a] = c->nnf_off[a];
+        A.dims[a] = c->nnf_dims[a];
+    }
+    A.shift = visit_shift(c);
+    A.keys = c->sort_keys[0];
+    A.ids = c->sort_ids[0];
+    return A;
+}
+
+// the radix passes over the 15-bit visiting keys; SortFinishOp writes the order
+SortArgs visit_sort_args(mp_ctx* c) {
+    SortArgs A = sort_args(c);
+    A.buckets = nullptr;
+    A.passes = 2;
+    A.sorted_ids = c->visit;
+    A.rank = nullptr;
+    A.blo = A.bhi = nullptr;
+    return A;
+}
+
 MergeArgs merge_args(mp_ctx* c, int cur) {
     MergeArgs A;
     A.poses = c->poses[c->cur];
@@ -653,6 +747,20 @@ int mp_launch_sort(mp_ctx* c) {
     // sort_keys[0] now holds the sorted buckets; seg[0..2^nb) / seg[2^nb..) hold bucket lo / hi
     k_segments<<<grid_for(n, 256), 256, 0, c->stream>>>(A);
     MP_LAUNCHED(c);
+    // the likelihood's visiting order, with the sort buffers free again
+    const SortArgs V = visit_sort_args(c);
+    k_visit_keys<<<grid_for(n, 256), 256, 0, c->stream>>>(visit_key_args(c));
+    MP_LAUNCHED(c);
+    for (int pss = 0; pss < V.passes; ++pss) {
+        k_radix_hist<<<V.nblocks, 256, 0, c->stream>>>(V, pss);
+        MP_LAUNCHED(c);
+        int rc = mp_launch_exclusive_scan(c, c->radix_counts, c->radix_counts, (int64_t)MP_RADIX * V.nblocks);
+        if (rc) return rc;
+        k_radix_scatter<<<V.nblocks, 256, 0, c->stream>>>(V, pss);
+        MP_LAUNCHED(c);
+    }
+    MP_CUDA(c, cudaMemcpyAsync(c->visit, c->sort_ids[V.passes & 1], sizeof(int32_t) * (size_t)n,
+                               cudaMemcpyDeviceToDevice, c->stream));
     return MP_OK;
 }
 
@@ -704,6 +812,30 @@ int mp_plan_lsh_sort(mp_group* G, int, std::vector<GOp>& plan) {
     }
     plan_kernel<SortFinishOp>(plan, stab, m256, n256);
     plan_kernel<SegmentsOp>(plan, stab, m256, n256);
+    // the likelihood's visiting order (two passes for every instance)
+    std::vector<VisitKeyArgs> vk;
+    std::vector<SortArgs> vs;
+    for (int i = 0; i < G->size(); ++i) {
+        vk.push_back(visit_key_args(G->ctx[i]));
+        vs.push_back(visit_sort_args(G->ctx[i]));
+    }
+    const VisitKeyArgs* vktab = G->upload(vk);
+    const SortArgs* vstab = G->upload(vs);
+    plan_kernel<VisitKeyOp>(plan, vktab, m256, n256);
+    for (int pss = 0; pss < 2; ++pss) {
+        std::vector<GBlk> hm, cm;
+        for (int i = 0; i < G->size(); ++i) {
+            for (int64_t b = 0; b < bsort[i]; ++b) hm.push_back(GBlk{i, (int32_t)b, pss, 0});
+            cm.push_back(GBlk{i, 0, pss, 0});
+        }
+        const unsigned nh = (unsigned)hm.size(), nc = (unsigned)cm.size();
+        const GBlk* hmap = G->upload(hm);
+        const GBlk* cmap = G->upload(cm);
+        plan_kernel<RadixHistOp>(plan, vstab, hmap, nh);
+        plan_kernel<CountScanOp>(plan, vstab, cmap, nc);
+        plan_kernel<RadixScatterOp>(plan, vstab, hmap, nh);
+    }
+    plan_kernel<SortFinishOp>(plan, vstab, m256, n256);
     return G->err;
 }
 

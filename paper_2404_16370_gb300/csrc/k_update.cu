@@ -373,7 +373,7 @@ SolveArgs solve_args(mp_ctx* c) {
     SolveArgs A;
     A.gn = c->gn;
     A.stride = c->cap;
-    A.order = c->sorted_ids;
+    A.order = c->visit;   // the likelihood's sums sit at its visiting slots
     A.n = c->n;
     A.lambda = (double)c->p.lambda;
     A.eps = (double)c->p.eps;
@@ -525,7 +525,7 @@ int mp_launch_unpack_poses(mp_ctx* c, const float4* src, float* dst7_dev) {
 }
 
 int mp_launch_gather_gn(mp_ctx* c, float* dst_dev) {
-    k_gather_gn<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->gn, c->cap, c->sorted_ids, c->n, dst_dev);
+    k_gather_gn<<<grid_for(c->n, 256), 256, 0, c->stream>>>(c->gn, c->cap, c->visit, c->n, dst_dev);
     MP_LAUNCHED(c);
     return MP_OK;
 }

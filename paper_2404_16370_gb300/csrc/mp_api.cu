@@ -168,7 +168,7 @@ void free_particles(mp_ctx* c) {
     dfree(c->poses[0]); dfree(c->poses[1]);
     dfree(c->logprior); dfree(c->post); dfree(c->post_tmp); dfree(c->post_init); dfree(c->post_invden); dfree(c->post_w);
     dfree(c->post_ids);
-    dfree(c->loglik); dfree(c->n_in); dfree(c->keys); dfree(c->buckets); dfree(c->sorted_ids); dfree(c->rank);
+    dfree(c->loglik); dfree(c->n_in); dfree(c->keys); dfree(c->buckets); dfree(c->sorted_ids); dfree(c->rank); dfree(c->visit);
     dfree(c->seg); dfree(c->sort_keys[0]); dfree(c->sort_keys[1]); dfree(c->sort_ids[0]); dfree(c->sort_ids[1]);
     dfree(c->radix_counts); dfree(c->scan_tmp);
     dfree(c->nbr_ids[0]); dfree(c->nbr_ids[1]); dfree(c->nbr_k); dfree(c->nbr_d);
@@ -195,7 +195,7 @@ int alloc_particles(mp_ctx* c, int64_t n) {
     A_(c->poses[0], 2 * n);
     A_(c->logprior, n); A_(c->post, n); A_(c->post_tmp, n); A_(c->post_init, n); A_(c->post_invden, n); A_(c->post_w, n * K);
     A_(c->post_ids, n * K);
-    A_(c->loglik, n); A_(c->n_in, n); A_(c->keys, n); A_(c->buckets, n); A_(c->sorted_ids, n); A_(c->rank, n);
+    A_(c->loglik, n); A_(c->n_in, n); A_(c->keys, n); A_(c->buckets, n); A_(c->sorted_ids, n); A_(c->rank, n); A_(c->visit, n);
     A_(c->seg, 2 * ((int64_t)1 << c->p.n_buckets_log2));
     A_(c->sort_keys[0], n); A_(c->sort_keys[1], n); A_(c->sort_ids[0], n); A_(c->sort_ids[1], n);
     A_(c->radix_counts, MP_RADIX * nb);
@@ -574,6 +574,7 @@ int mp_init_particles(mp_ctx* c, int64_t n, const float lo[6], const float hi[6]
     for (int64_t i = 0; i < n; ++i) iota[(size_t)i] = (int32_t)i;
     MP_CUDA(c, cudaMemcpyAsync(c->sorted_ids, iota.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
     MP_CUDA(c, cudaMemcpyAsync(c->rank, iota.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    MP_CUDA(c, cudaMemcpyAsync(c->visit, iota.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
     MP_CUDA(c, cudaMemsetAsync(c->loglik, 0, sizeof(float) * (size_t)n, c->stream));
     MP_CUDA(c, cudaMemsetAsync(c->psi, 0, sizeof(float) * 8 * (size_t)n, c->stream));
     MP_CUDA(c, cudaMemsetAsync(c->phi, 0, sizeof(float) * 8 * (size_t)n, c->stream));
@@ -712,6 +713,7 @@ int mp_buffer_size(mp_ctx* c, int which, int64_t* count) {
     switch (which) {
         case MP_BUF_POSES: *count = 7 * n; break;
         case MP_BUF_LOG_PRIOR: case MP_BUF_KEYS: case MP_BUF_BUCKETS: case MP_BUF_SORTED_IDS: case MP_BUF_POST:
+        case MP_BUF_VISIT_ORDER:
         case MP_BUF_POST_INIT: case MP_BUF_LOGLIK: *count = n; break;
         case MP_BUF_SEGMENTS: *count = 2 * n; break;
         case MP_BUF_NBR_IDS: case MP_BUF_NBR_K: *count = n * K; break;
@@ -758,6 +760,7 @@ int mp_get_buffer(mp_ctx* c, int which, void* dst, int64_t count) {
         case MP_BUF_KEYS: return copy(c->keys, sizeof(uint32_t) * n);
         case MP_BUF_BUCKETS: return copy(c->buckets, sizeof(uint32_t) * n);
         case MP_BUF_SORTED_IDS: return copy(c->sorted_ids, sizeof(int32_t) * n);
+        case MP_BUF_VISIT_ORDER: return copy(c->visit, sizeof(int32_t) * n);
         case MP_BUF_NBR_IDS: return copy(c->nbr_ids[c->nbr_cur], sizeof(int32_t) * n * c->p.K);
         case MP_BUF_NBR_K: return copy(c->nbr_k, sizeof(float) * n * c->p.K);
         case MP_BUF_NBR_D: return copy(c->nbr_d, sizeof(float) * n * c->p.K * 6);
@@ -835,8 +838,26 @@ int mp_set_buffer(mp_ctx* c, int which, const void* src, int64_t count) {
             return MP_OK;
         }
         case MP_BUF_LOG_PRIOR: return put(c->logprior, sizeof(double) * n);
-        case MP_BUF_SORTED_IDS: return put(c->sorted_ids, sizeof(int32_t) * n);
-        case MP_BUF_NBR_IDS: return put(c->nbr_ids[c->nbr_cur], sizeof(int32_t) * n * c->p.K);
+        case MP_BUF_SORTED_IDS: case MP_BUF_NBR_IDS: {
+            // kernels index particles by these entries: checked on the host first
+            const int64_t m = which == MP_BUF_SORTED_IDS ? n : n * c->p.K;
+            std::vector<int32_t> h((size_t)m);
+            MP_CUDA(c, cudaStreamSynchronize(c->stream));
+            MP_CUDA(c, cudaMemcpy(h.data(), src, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault));
+            if (which == MP_BUF_SORTED_IDS) {
+                std::vector<uint8_t> seen((size_t)n, 0);
+                for (int32_t v : h) {
+                    if (v < 0 || v >= n || seen[(size_t)v]) return mp_fail(c, MP_EINVAL, "sorted ids must be a permutation of [0, n)");
+                    seen[(size_t)v] = 1;
+                }
+            } else {
+                for (int32_t v : h)
+                    if (v < -1 || v >= n) return mp_fail(c, MP_EINVAL, "neighbour ids must lie in [-1, n)");
+            }
+            src = h.data();   // put() copies from src on the context stream
+            return put(which == MP_BUF_SORTED_IDS ? (void*)c->sorted_ids : (void*)c->nbr_ids[c->nbr_cur],
+                       sizeof(int32_t) * (size_t)m);
+        }
         case MP_BUF_NBR_K: return put(c->nbr_k, sizeof(float) * n * c->p.K);
         case MP_BUF_NBR_D: return put(c->nbr_d, sizeof(float) * n * c->p.K * 6);
         case MP_BUF_LOGLIK: return put(c->loglik, sizeof(float) * n);

@@ -76,6 +76,7 @@ struct mp_ctx {
     uint32_t* buckets;
     int32_t* sorted_ids;
     int32_t* rank;
+    int32_t* visit;         // the likelihood's visiting order (position cells, LSH order within a cell)
     int32_t* seg;           // 2 per particle
     uint32_t* sort_keys[2];
     int32_t* sort_ids[2];

@@ -35,6 +35,7 @@ MP_BUF_POSES, MP_BUF_LOG_PRIOR, MP_BUF_KEYS, MP_BUF_BUCKETS, MP_BUF_SORTED_IDS =
 MP_BUF_SEGMENTS, MP_BUF_NBR_IDS, MP_BUF_NBR_K, MP_BUF_NBR_D, MP_BUF_GN = 6, 7, 8, 9, 10
 MP_BUF_PSI, MP_BUF_POST, MP_BUF_POST_INIT, MP_BUF_LOGLIK, MP_BUF_SCAN_NORMALS = 11, 12, 13, 14, 15
 MP_BUF_SCAN_VALID, MP_BUF_MAP_NORMALS, MP_BUF_MAP_VALID, MP_BUF_LSH, MP_BUF_PHI = 16, 17, 18, 19, 20
+MP_BUF_VISIT_ORDER = 21
 
 # element type and trailing shape of each buffer
 _BUF = {
@@ -44,7 +45,7 @@ _BUF = {
     MP_BUF_GN: (np.float32, (29,)), MP_BUF_PSI: (np.float32, (6,)), MP_BUF_POST: (np.float64, ()),
     MP_BUF_POST_INIT: (np.float64, ()), MP_BUF_LOGLIK: (np.float32, ()), MP_BUF_SCAN_NORMALS: (np.float32, (3,)),
     MP_BUF_SCAN_VALID: (np.uint8, ()), MP_BUF_MAP_NORMALS: (np.float32, (3,)), MP_BUF_MAP_VALID: (np.uint8, ()),
-    MP_BUF_LSH: (np.float64, ()), MP_BUF_PHI: (np.float32, (6,)),
+    MP_BUF_LSH: (np.float64, ()), MP_BUF_PHI: (np.float32, (6,)), MP_BUF_VISIT_ORDER: (np.int32, ()),
 }
 
 

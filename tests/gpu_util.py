@@ -38,3 +38,28 @@ def check_sums(gn, ref, rel=1e-4, floor=1e-6):
     want = np.concatenate([ref["H"], ref["b"], ref["loglik"][:, None]], 1)
     tol = rel * ref["absum"] + ref["ambabs"] + floor
     return report("H/b/loglik", np.abs(got - want), tol)
+
+
+def visit_order(sorted_ids, t, info):
+    """The likelihood's visiting order as the library defines it: particles by
+    the Morton code of their position's cell (cubes of 2^s NNF voxels, s the
+    smallest shift leaving at most 32 cubes along every axis; positions clamped
+    to the grid, NaN to cell 0), stable over the LSH order. The voxel
+    coordinate is a float32 product and sum, as in the kernel."""
+    t = np.asarray(t, np.float32)
+    inv = np.float32(info["inv_res"])
+    off = np.asarray(info["off"], np.float32)
+    dims = np.asarray(info["dims"], np.int64)
+    s = 0
+    while (int(dims.max()) - 1) >> s >= 32:
+        s += 1
+    key = np.zeros(len(t), np.int64)
+    with np.errstate(invalid="ignore"):
+        for a in range(3):
+            f = t[:, a] * inv + off[a]
+            v = np.where(f >= 0, np.floor(np.minimum(f, np.float32(dims[a] - 1))), 0).astype(np.int64)
+            c = v >> s
+            for b in range(5):
+                key |= ((c >> b) & 1) << (3 * b + a)
+    sid = np.asarray(sorted_ids, np.int64)
+    return sid[np.argsort(key[sid], kind="stable")]

@@ -172,6 +172,22 @@ def test_invalid_arguments(room):
         assert e.value.code == mp.MP_EINVAL
         with pytest.raises(mp.MPError):
             mp.mp_set_buffer(ctx, mp.MP_BUF_KEYS, np.zeros(64, np.uint32))   # read-only buffer
+        with pytest.raises(mp.MPError):
+            mp.mp_set_buffer(ctx, mp.MP_BUF_VISIT_ORDER, np.arange(64, dtype=np.int32))
+        # index buffers the kernels gather through are checked before upload
+        dup = np.arange(64, dtype=np.int32)
+        dup[5] = 4
+        with pytest.raises(mp.MPError) as e:
+            mp.mp_set_buffer(ctx, mp.MP_BUF_SORTED_IDS, dup)
+        assert "permutation" in mp.mp_last_error(ctx)
+        K = mp.mp_buffer_size(ctx, mp.MP_BUF_NBR_IDS) // 64
+        ids = np.full((64, K), -1, np.int32)
+        ids[3, 1] = 64
+        with pytest.raises(mp.MPError) as e:
+            mp.mp_set_buffer(ctx, mp.MP_BUF_NBR_IDS, ids)
+        assert "[-1, n)" in mp.mp_last_error(ctx)
+        mp.mp_set_buffer(ctx, mp.MP_BUF_SORTED_IDS, np.arange(64, dtype=np.int32)[::-1].copy())
+        assert np.array_equal(mp.mp_get_buffer(ctx, mp.MP_BUF_SORTED_IDS), np.arange(64)[::-1])
         bad = np.eye(4)
         bad[0, 3] = np.nan
         with pytest.raises(mp.MPError):

@@ -12,7 +12,7 @@ argmax)."""
 import numpy as np
 import pytest
 
-from gpu_util import check_sums
+from gpu_util import check_sums, visit_order
 from paper_2404_16370_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -77,9 +77,9 @@ def stepped(big):
     names = {"keys": mp.MP_BUF_KEYS, "buckets": mp.MP_BUF_BUCKETS, "sid": mp.MP_BUF_SORTED_IDS,
              "seg": mp.MP_BUF_SEGMENTS, "ids": mp.MP_BUF_NBR_IDS, "k": mp.MP_BUF_NBR_K, "gn": mp.MP_BUF_GN,
              "post": mp.MP_BUF_POST, "psi": mp.MP_BUF_PSI, "poses": mp.MP_BUF_POSES, "d": mp.MP_BUF_NBR_D,
-             "phi": mp.MP_BUF_PHI}
+             "phi": mp.MP_BUF_PHI, "visit": mp.MP_BUF_VISIT_ORDER}
     out = {k: mp.mp_get_buffer(ctx, b) for k, b in names.items()}
-    out.update(best=best, best_p=best_p)
+    out.update(best=best, best_p=best_p, info=mp.mp_map_info(ctx))
     return out
 
 
@@ -99,6 +99,14 @@ def test_keys_and_order_fullsize(big, stepped, oracle):
         s = oracle.bucket_sort(ref["buckets"])
         assert np.array_equal(stepped["sid"], s["sorted_ids"])
         assert np.array_equal(stepped["seg"][:, 0], s["seg_lo"]) and np.array_equal(stepped["seg"][:, 1], s["seg_hi"])
+
+
+def test_visit_order_fullsize(big, stepped):
+    """The likelihood's visiting order: a permutation, equal to its definition
+    (position cells in Morton order, LSH order within a cell) at 2^20."""
+    v = stepped["visit"]
+    assert np.array_equal(np.sort(v), np.arange(N))
+    assert np.array_equal(v, visit_order(stepped["sid"], big["w"].particles[:, 4:7], stepped["info"]))
 
 
 def test_neighbour_lists_sampled_fullsize(big, stepped, oracle):

@@ -12,7 +12,7 @@ points, K = C = 16). Tolerances:
 import numpy as np
 import pytest
 
-from gpu_util import check_sums, pose_error
+from gpu_util import check_sums, pose_error, visit_order
 from paper_2404_16370_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -180,8 +180,12 @@ def test_sort_and_segments(env, oracle, alpha_scale):
         b = mp.mp_get_buffer(ctx, mp.MP_BUF_BUCKETS)
         sid = mp.mp_get_buffer(ctx, mp.MP_BUF_SORTED_IDS)
         seg = mp.mp_get_buffer(ctx, mp.MP_BUF_SEGMENTS)
+        visit = mp.mp_get_buffer(ctx, mp.MP_BUF_VISIT_ORDER)
+        info = mp.mp_map_info(ctx)
     finally:
         mp.mp_destroy(ctx)
+    # the likelihood's visiting order: position cells, LSH order within a cell
+    assert np.array_equal(visit, visit_order(sid, env["w"].particles[:, 4:7], info))
     om = env["om"]
     v = om.valid.astype(bool)
     q, t, d = oracle.lsh_draw(P.seed, 5, om.pts[v].min(0).astype(np.float64), om.pts[v].max(0).astype(np.float64),
