@@ -503,7 +503,10 @@ def run_gpu(args):
                 "avg_launch_ms": 1e3 * lk_s, "bound_ms": 1e3 * hbm_bound_s,
                 "random_sector_ceiling_gbs": rs.get("sector_gbs"),
                 "frac_of_random_sector_ceiling": (sector_gbs / rs["sector_gbs"]) if sector_gbs and rs.get("sector_gbs")
-                else None}
+                else None,
+                # DRAM bytes per pair measured by ncu (one full-size launch): below the model's 32 when the
+                # resident CTAs share NNF sectors through L2 (the likelihood's position visiting order)
+                "traffic_bytes_per_pair": (traffic / pairs_launch) if traffic and pairs_launch else None}
     roof_alu = {"bound": "alu", "kernel": "k_likelihood", "achieved": alu_tflops, "peak": fp32_tf, "unit": "TFLOP/s",
                 "frac": (alu_tflops / fp32_tf) if alu_tflops else None, "traffic": traffic,
                 "peak_source": "measured (FP32 FMA microbenchmark, libmp_probe.so)" if "fma_error" not in ceil
