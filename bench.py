@@ -525,6 +525,7 @@ def run_gpu(args):
         "config": {**workload_desc(round(nvalid_mean, 1)), "init": args.init, "precision": args.precision,
                    "svgd_reading": SVGD_READINGS[args.svgd_precond]},
         "pair_evals_per_s": pairs * world / t_max,
+        "pair_evals_per_s_likelihood": (pairs_launch / lk_s * world) if lk_s > 0 else None,
         "roofline": graded,
         f"roofline_{other['bound']}": other,
         "roofline_step": {"bound_ms": step_bound, "measured_ms": 1e3 * t_max / args.steps,

@@ -336,11 +336,11 @@ int mp_kernel_launches(mp_ctx* ctx, int64_t* count);
  * bounded wait gives up; the kernel then records the error (reported as
  * MP_ETIMEOUT by the next mp_get_posterior) and returns. No copy is left in
  * flight. MP_DEBUG_STARVE_BARRIER: when non-zero, the first grid barrier of
- * the posterior stage (one cooperative launch; in a batch, the first
- * instance's knob and wait budget when mp_batch_create captures the step
- * apply) waits for one CTA more than the grid has, so every
- * CTA's bounded wait gives up; the kernel records the error for every
- * instance it serves and returns. */
+ * the posterior stage (one cooperative launch) waits for one CTA more than the
+ * grid has, so every CTA's bounded wait gives up; the kernel records the error
+ * for every instance it serves and returns. In a batch the first instance's
+ * knob and wait budget when mp_batch_create captures the step apply, to the
+ * posterior and to the batch's LSH/sort phase (also one cooperative launch). */
 #define MP_DEBUG_WAIT_BUDGET 1
 #define MP_DEBUG_STARVE_TX 2
 #define MP_DEBUG_STARVE_BARRIER 3

@@ -119,7 +119,7 @@ __device__ __forceinline__ void log_se3_d(double qx, double qy, double qz, doubl
 // T_LSH^-1 and delta come from the device-side step values (replayable)
 struct LshOp {
     using Args = LshArgs;
-    static constexpr int THREADS = 256, MINB = 1;
+    static constexpr int THREADS = 256;
     static __device__ __forceinline__ void run(const LshArgs& A, unsigned bx, unsigned);
 };
 
@@ -180,14 +180,25 @@ struct SortArgs {
     int32_t* bhi;
 };
 
+// A load of sort data. CG: the data may have been written by another CTA
+// earlier in the same (persistent) launch, so the load goes through L2
+// (ld.global.cg); the read-only path is not coherent within a launch.
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_sort(const T* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // pass pss (the block map's y index): digit counts of block bx
 struct RadixHistOp {
     using Args = SortArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned pss);
+    template <bool CG>
+    static __device__ __forceinline__ void body(const SortArgs& A, unsigned bx, unsigned pss);
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned pss) { body<false>(A, bx, pss); }
 };
 
-__device__ __forceinline__ void RadixHistOp::run(const SortArgs& A, unsigned bx, unsigned pss) {
+template <bool CG>
+__device__ __forceinline__ void RadixHistOp::body(const SortArgs& A, unsigned bx, unsigned pss) {
     const uint32_t* __restrict__ keys = A.keys[pss & 1];
     const int64_t n = A.n;
     const int shift = (int)pss * MP_RADIX_BITS;
@@ -200,7 +211,7 @@ __device__ __forceinline__ void RadixHistOp::run(const SortArgs& A, unsigned bx,
 #pragma unroll
     for (int it = 0; it < MP_SORT_TILE / 256; ++it) {
         int64_t idx = base + it * 256 + threadIdx.x;
-        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (MP_RADIX - 1)], 1u);
+        if (idx < n) atomicAdd(&h[(ld_sort<CG>(keys + idx) >> shift) & (MP_RADIX - 1)], 1u);
     }
     __syncthreads();
     counts[(int64_t)threadIdx.x * nblocks + bx] = h[threadIdx.x];
@@ -209,11 +220,13 @@ __device__ __forceinline__ void RadixHistOp::run(const SortArgs& A, unsigned bx,
 // pass pss: stable scatter of block bx by its digit offsets
 struct RadixScatterOp {
     using Args = SortArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned pss);
+    template <bool CG>
+    static __device__ __forceinline__ void body(const SortArgs& A, unsigned bx, unsigned pss);
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned pss) { body<false>(A, bx, pss); }
 };
 
-__device__ __forceinline__ void RadixScatterOp::run(const SortArgs& A, unsigned bx, unsigned pss) {
+template <bool CG>
+__device__ __forceinline__ void RadixScatterOp::body(const SortArgs& A, unsigned bx, unsigned pss) {
     const uint32_t* __restrict__ kin = A.keys[pss & 1];
     const int32_t* __restrict__ iin = A.ids[pss & 1];
     uint32_t* __restrict__ kout = A.keys[(pss & 1) ^ 1];
@@ -236,8 +249,8 @@ __device__ __forceinline__ void RadixScatterOp::run(const SortArgs& A, unsigned 
     for (int it = 0; it < ITEMS; ++it) {
         int64_t idx = base + it * 32 + lane;
         bool ok = idx < n;
-        key[it] = ok ? kin[idx] : 0u;
-        id[it] = ok ? iin[idx] : 0;
+        key[it] = ok ? ld_sort<CG>(kin + idx) : 0u;
+        id[it] = ok ? ld_sort<CG>(iin + idx) : 0;
         uint32_t dg = ok ? ((key[it] >> shift) & (MP_RADIX - 1)) : MP_RADIX;
         unsigned peers = __match_any_sync(0xffffffffu, dg);
         uint32_t before = ok ? wcnt[w][dg] : 0u;
@@ -262,7 +275,7 @@ __device__ __forceinline__ void RadixScatterOp::run(const SortArgs& A, unsigned 
         int64_t idx = base + it * 32 + lane;
         if (idx < n) {
             uint32_t dg = (key[it] >> shift) & (MP_RADIX - 1);
-            int64_t pos = (int64_t)offs[(int64_t)dg * nblocks + bx] + wcnt[w][dg] + loc[it];
+            int64_t pos = (int64_t)ld_sort<CG>(offs + (int64_t)dg * nblocks + bx) + wcnt[w][dg] + loc[it];
             if (!MP_DCHECK(pos >= 0 && pos < n, "radix scatter position", pos)) continue;
             kout[pos] = key[it];
             iout[pos] = id[it];
@@ -283,91 +296,93 @@ __global__ void k_iota(int32_t* __restrict__ a, int64_t n) {
 // (key, id) pairs of the first pass: (bucket_i, i)
 struct SortInitOp {
     using Args = SortArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned) {
+    static constexpr int THREADS = 256;
+    template <bool CG>
+    static __device__ __forceinline__ void body(const SortArgs& A, unsigned bx) {
         int64_t i = (int64_t)bx * THREADS + threadIdx.x;
         if (i >= A.n) return;
         A.ids[0][i] = (int32_t)i;
-        A.keys[0][i] = A.buckets[i];
+        A.keys[0][i] = ld_sort<CG>(A.buckets + i);
     }
 };
 
 // sorted ids out of the last pass's pair, sorted buckets into keys[0]
 struct SortFinishOp {
     using Args = SortArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned) {
+    static constexpr int THREADS = 256;
+    template <bool CG>
+    static __device__ __forceinline__ void body(const SortArgs& A, unsigned bx) {
         int64_t i = (int64_t)bx * THREADS + threadIdx.x;
         if (i >= A.n) return;
         const int src = A.passes & 1;
-        A.sorted_ids[i] = A.ids[src][i];
-        if (src) A.keys[0][i] = A.keys[1][i];
+        A.sorted_ids[i] = ld_sort<CG>(A.ids[src] + i);
+        if (src) A.keys[0][i] = ld_sort<CG>(A.keys[1] + i);
     }
 };
 
 // Exclusive scan of one instance's digit counts (256 x nblocks), in place, by
-// one CTA: 4096 counts per round with a running carry.
-struct CountScanOp {
-    using Args = SortArgs;
-    static constexpr int THREADS = 1024, MINB = 1;
-    static __device__ __forceinline__ void run(const SortArgs& A, unsigned, unsigned) {
-        __shared__ uint32_t warp_tot[32];
-        __shared__ uint32_t carry_s;
-        const int64_t m = (int64_t)MP_RADIX * A.nblocks;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        if (threadIdx.x == 0) carry_s = 0;
-        __syncthreads();
-        for (int64_t base0 = 0; base0 < m; base0 += 4096) {
-            const int64_t base = base0 + 4 * threadIdx.x;
-            uint32_t v[4];
+// one CTA of NT threads: 4 NT counts per round with a running carry.
+template <int NT, bool CG>
+__device__ __forceinline__ void count_scan(const SortArgs& A) {
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t warp_tot[NW];
+    __shared__ uint32_t carry_s;
+    const int64_t m = (int64_t)MP_RADIX * A.nblocks;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t base0 = 0; base0 < m; base0 += 4 * NT) {
+        const int64_t base = base0 + 4 * threadIdx.x;
+        uint32_t v[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = (base + k < m) ? A.counts[base + k] : 0u;
-            const uint32_t s0 = v[0], s1 = s0 + v[1], s2 = s1 + v[2], tot = s2 + v[3];
-            uint32_t inc = tot;
+        for (int k = 0; k < 4; ++k) v[k] = (base + k < m) ? ld_sort<CG>(A.counts + base + k) : 0u;
+        const uint32_t s0 = v[0], s1 = s0 + v[1], s2 = s1 + v[2], tot = s2 + v[3];
+        uint32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) warp_tot[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t x = lane < NW ? warp_tot[lane] : 0u;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
             }
-            if (lane == 31) warp_tot[w] = inc;
-            __syncthreads();
-            if (w == 0) {
-                uint32_t x = warp_tot[lane];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                warp_tot[lane] = x;
-            }
-            __syncthreads();
-            const uint32_t carry = carry_s;
-            const uint32_t excl = carry + inc - tot + (w > 0 ? warp_tot[w - 1] : 0u);
-            const uint32_t r[4] = {excl, excl + s0, excl + s1, excl + s2};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (base + k < m) A.counts[base + k] = r[k];
-            __syncthreads();
-            if (threadIdx.x == 0) carry_s = carry + warp_tot[31];
-            __syncthreads();
+            if (lane < NW) warp_tot[lane] = x;
         }
+        __syncthreads();
+        const uint32_t carry = carry_s;
+        const uint32_t excl = carry + inc - tot + (w > 0 ? warp_tot[w - 1] : 0u);
+        const uint32_t r[4] = {excl, excl + s0, excl + s1, excl + s2};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (base + k < m) A.counts[base + k] = r[k];
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = carry + warp_tot[NW - 1];
+        __syncthreads();
     }
-};
+}
 
 // rank of every particle; [lo, hi) of every present bucket
 struct SegmentsOp {
     using Args = SortArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned) {
+    static constexpr int THREADS = 256;
+    template <bool CG>
+    static __device__ __forceinline__ void body(const SortArgs& A, unsigned bx) {
         const uint32_t* __restrict__ sk = A.keys[0];
         const int64_t n = A.n;
         int64_t p = (int64_t)bx * THREADS + threadIdx.x;
         if (p >= n) return;
-        uint32_t b = sk[p];
-        A.rank[A.sorted_ids[p]] = (int32_t)p;
-        if (p == 0 || sk[p - 1] != b) A.blo[b] = (int32_t)p;
-        if (p == n - 1 || sk[p + 1] != b) A.bhi[b] = (int32_t)(p + 1);
+        uint32_t b = ld_sort<CG>(sk + p);
+        A.rank[ld_sort<CG>(A.sorted_ids + p)] = (int32_t)p;
+        if (p == 0 || ld_sort<CG>(sk + p - 1) != b) A.blo[b] = (int32_t)p;
+        if (p == n - 1 || ld_sort<CG>(sk + p + 1) != b) A.bhi[b] = (int32_t)(p + 1);
     }
+    static __device__ __forceinline__ void run(const SortArgs& A, unsigned bx, unsigned) { body<false>(A, bx); }
 };
 
 __global__ void __launch_bounds__(256) k_segments(const SortArgs A) { SegmentsOp::run(A, blockIdx.x, 0); }
@@ -406,11 +421,12 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
 
 struct VisitKeyOp {
     using Args = VisitKeyArgs;
-    static constexpr int THREADS = 256, MINB = 1;
-    static __device__ __forceinline__ void run(const VisitKeyArgs& A, unsigned bx, unsigned) {
+    static constexpr int THREADS = 256;
+    template <bool CG>
+    static __device__ __forceinline__ void body(const VisitKeyArgs& A, unsigned bx) {
         const int64_t p = (int64_t)bx * THREADS + threadIdx.x;
         if (p >= A.n) return;
-        int32_t i = A.lsh_order[p];
+        int32_t i = ld_sort<CG>(A.lsh_order + p);
         if (!MP_DCHECK(i >= 0 && i < A.n, "LSH order entry", i)) i = 0;
         const float4 t = A.poses[2 * (int64_t)i + 1];
         const float x[3] = {t.x, t.y, t.z};
@@ -427,6 +443,7 @@ struct VisitKeyOp {
         A.keys[p] = key;
         A.ids[p] = i;
     }
+    static __device__ __forceinline__ void run(const VisitKeyArgs& A, unsigned bx, unsigned) { body<false>(A, bx); }
 };
 
 __global__ void __launch_bounds__(256) k_visit_keys(const VisitKeyArgs A) { VisitKeyOp::run(A, blockIdx.x, 0); }
@@ -508,7 +525,11 @@ __device__ __forceinline__ void MergeOp::run(const MergeArgs& args, unsigned bx,
     {
         uint32_t b = buckets[i];
         int lo = blo[b], hi = bhi[b], r = rank[i];
-        if (!MP_DCHECK(lo >= 0 && lo <= r && r < hi && hi <= n, "bucket segment", (long long)lo * 1000003 + hi)) {
+        // The segment table is the last sort's. Buckets of a later LSH draw
+        // that no sort followed (a batch whose sort phase gave up at a grid
+        // barrier, or stages run out of order) can name an entry that does
+        // not hold i, or one never written: the window is then empty.
+        if (!(lo >= 0 && lo <= r && r < hi && hi <= n)) {
             lo = 0;
             hi = 0;
         }
@@ -606,6 +627,95 @@ __device__ __forceinline__ void MergeOp::run(const MergeArgs& args, unsigned bx,
 }
 
 __global__ void __launch_bounds__(256) k_merge(const MergeArgs A) { MergeOp::run(A, blockIdx.x, 0); }
+
+// ---------------------------------------------------------------------------
+// the LSH / sort / visiting-order phase of a batch as one persistent kernel
+// ---------------------------------------------------------------------------
+// A cooperative launch whose CTAs take the blocks of every instance in turn,
+// with a bounded grid barrier between the sub-steps: keys and first pairs |
+// per radix pass: digit counts | count scan (one CTA per instance) | scatter |
+// sorted ids | rank and segments | visiting keys | two radix passes of the
+// visiting keys | visiting order. The bodies are those of the grouped kernels;
+// what a sub-step reads from an earlier one goes through L2.
+struct SortPhase {
+    const LshArgs* lsh;
+    const SortArgs* sort;
+    const VisitKeyArgs* vkey;
+    const SortArgs* vsort;
+    const GBlk* pblk;         // the 256-particle blocks (inst, bx) of every instance
+    const GBlk* sblk;         // the 2048-element sort tiles (inst, bx) of every instance
+    int32_t* const* err;      // every instance's error word
+    int n_pblk, n_sblk, n_inst, max_passes;
+    int starve;               // test knob: the first barrier waits for one CTA more than the grid
+    GridBar* bar;
+    long long budget;
+};
+
+constexpr int SORT_PHASE_THREADS = 256;
+
+__device__ __forceinline__ bool sort_phase_sync(const SortPhase& P, unsigned& expect) {
+    const bool ok = grid_sync(P.bar, expect, P.budget);
+    expect = gridDim.x;
+    if (!ok && threadIdx.x == 0)
+        for (int k = 0; k < P.n_inst; ++k) atomicOr(P.err[k], MP_ERR_WAIT);
+    return ok;
+}
+
+// the radix passes [0, passes) of the sorts in tab (one per instance)
+__device__ __forceinline__ bool sort_passes(const SortPhase& P, const SortArgs* tab, int passes, unsigned& expect) {
+    for (int pss = 0; pss < passes; ++pss) {
+        for (int w = blockIdx.x; w < P.n_sblk; w += gridDim.x) {
+            const GBlk g = P.sblk[w];
+            if (tab[g.inst].passes > pss) RadixHistOp::body<true>(tab[g.inst], (unsigned)g.bx, (unsigned)pss);
+            __syncthreads();
+        }
+        if (!sort_phase_sync(P, expect)) return false;
+        for (int k = blockIdx.x; k < P.n_inst; k += gridDim.x) {
+            if (tab[k].passes > pss) count_scan<SORT_PHASE_THREADS, true>(tab[k]);
+            __syncthreads();
+        }
+        if (!sort_phase_sync(P, expect)) return false;
+        for (int w = blockIdx.x; w < P.n_sblk; w += gridDim.x) {
+            const GBlk g = P.sblk[w];
+            if (tab[g.inst].passes > pss) RadixScatterOp::body<true>(tab[g.inst], (unsigned)g.bx, (unsigned)pss);
+            __syncthreads();
+        }
+        if (!sort_phase_sync(P, expect)) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(SORT_PHASE_THREADS) k_sort_phase(const __grid_constant__ SortPhase P) {
+    unsigned expect = gridDim.x + (P.starve ? 1u : 0u);
+    for (int w = blockIdx.x; w < P.n_pblk; w += gridDim.x) {
+        const GBlk g = P.pblk[w];
+        LshOp::run(P.lsh[g.inst], (unsigned)g.bx, 0);
+        SortInitOp::body<true>(P.sort[g.inst], (unsigned)g.bx);   // reads the thread's own bucket
+    }
+    if (!sort_phase_sync(P, expect)) return;
+    if (!sort_passes(P, P.sort, P.max_passes, expect)) return;
+    for (int w = blockIdx.x; w < P.n_pblk; w += gridDim.x) {
+        const GBlk g = P.pblk[w];
+        SortFinishOp::body<true>(P.sort[g.inst], (unsigned)g.bx);
+    }
+    if (!sort_phase_sync(P, expect)) return;
+    for (int w = blockIdx.x; w < P.n_pblk; w += gridDim.x) {
+        const GBlk g = P.pblk[w];
+        SegmentsOp::body<true>(P.sort[g.inst], (unsigned)g.bx);
+    }
+    if (!sort_phase_sync(P, expect)) return;
+    // the visiting keys overwrite the sort buffers the segments just read
+    for (int w = blockIdx.x; w < P.n_pblk; w += gridDim.x) {
+        const GBlk g = P.pblk[w];
+        VisitKeyOp::body<true>(P.vkey[g.inst], (unsigned)g.bx);
+    }
+    if (!sort_phase_sync(P, expect)) return;
+    if (!sort_passes(P, P.vsort, 2, expect)) return;
+    for (int w = blockIdx.x; w < P.n_pblk; w += gridDim.x) {
+        const GBlk g = P.pblk[w];
+        SortFinishOp::body<true>(P.vsort[g.inst], (unsigned)g.bx);
+    }
+}
 
 }  // namespace
 
@@ -771,72 +881,65 @@ int mp_launch_merge(mp_ctx* c) {
     return MP_OK;
 }
 
-// Grouped LSH keys and sort: every instance's keys, then the radix passes
-// (pass pss covers the instances that need it), then segments.
+// Resident CTAs of k_sort_phase on the current device: the grid of a
+// cooperative launch may not exceed it.
+static unsigned sort_phase_capacity() {
+    static int cap[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cap[dev]) {
+        int sms = 0, per = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sort_phase, SORT_PHASE_THREADS, 0) != cudaSuccess)
+            return 0;
+        cap[dev] = sms * per;
+    }
+    return (unsigned)cap[dev];
+}
+
+// The batch's LSH keys, sort, segments and visiting order: one cooperative
+// persistent launch over the particle blocks and sort tiles of all instances
+// (its barrier zeroed first).
 int mp_plan_lsh_sort(mp_group* G, int, std::vector<GOp>& plan) {
     std::vector<LshArgs> lt;
-    std::vector<SortArgs> st;
+    std::vector<SortArgs> st, vs;
+    std::vector<VisitKeyArgs> vk;
+    std::vector<int32_t*> errs;
     std::vector<int64_t> b256, bsort;
     int max_passes = 0;
     for (int i = 0; i < G->size(); ++i) {
         mp_ctx* c = G->ctx[i];
         lt.push_back(lsh_args(c, G->sd_dev + i));
         st.push_back(sort_args(c));
+        vk.push_back(visit_key_args(c));
+        vs.push_back(visit_sort_args(c));
+        errs.push_back(c->dev_error);
         b256.push_back((c->n + 255) / 256);
         bsort.push_back(st.back().nblocks);
-        max_passes = st.back().passes > max_passes ? st.back().passes : max_passes;
+        max_passes = std::max(max_passes, std::max(st.back().passes, vs.back().passes));
     }
-    const LshArgs* ltab = G->upload(lt);
-    const SortArgs* stab = G->upload(st);
-    unsigned nblk = 0;
-    const GBlk* m256 = G->block_map(b256, &nblk);
-    const unsigned n256 = nblk;
-    plan_kernel<LshOp>(plan, ltab, m256, n256);
-    plan_kernel<SortInitOp>(plan, stab, m256, n256);
-    for (int pss = 0; pss < max_passes; ++pss) {
-        std::vector<int> which;
-        for (int i = 0; i < G->size(); ++i)
-            if (st[i].passes > pss) which.push_back(i);
-        // the pass index rides in the block map's y field
-        std::vector<GBlk> hm, cm;
-        for (int i : which) {
-            for (int64_t b = 0; b < bsort[i]; ++b) hm.push_back(GBlk{i, (int32_t)b, pss, 0});
-            cm.push_back(GBlk{i, 0, pss, 0});
-        }
-        const unsigned nh = (unsigned)hm.size(), nc = (unsigned)cm.size();
-        const GBlk* hmap = G->upload(hm);
-        const GBlk* cmap = G->upload(cm);
-        plan_kernel<RadixHistOp>(plan, stab, hmap, nh);
-        plan_kernel<CountScanOp>(plan, stab, cmap, nc);
-        plan_kernel<RadixScatterOp>(plan, stab, hmap, nh);
-    }
-    plan_kernel<SortFinishOp>(plan, stab, m256, n256);
-    plan_kernel<SegmentsOp>(plan, stab, m256, n256);
-    // the likelihood's visiting order (two passes for every instance)
-    std::vector<VisitKeyArgs> vk;
-    std::vector<SortArgs> vs;
-    for (int i = 0; i < G->size(); ++i) {
-        vk.push_back(visit_key_args(G->ctx[i]));
-        vs.push_back(visit_sort_args(G->ctx[i]));
-    }
-    const VisitKeyArgs* vktab = G->upload(vk);
-    const SortArgs* vstab = G->upload(vs);
-    plan_kernel<VisitKeyOp>(plan, vktab, m256, n256);
-    for (int pss = 0; pss < 2; ++pss) {
-        std::vector<GBlk> hm, cm;
-        for (int i = 0; i < G->size(); ++i) {
-            for (int64_t b = 0; b < bsort[i]; ++b) hm.push_back(GBlk{i, (int32_t)b, pss, 0});
-            cm.push_back(GBlk{i, 0, pss, 0});
-        }
-        const unsigned nh = (unsigned)hm.size(), nc = (unsigned)cm.size();
-        const GBlk* hmap = G->upload(hm);
-        const GBlk* cmap = G->upload(cm);
-        plan_kernel<RadixHistOp>(plan, vstab, hmap, nh);
-        plan_kernel<CountScanOp>(plan, vstab, cmap, nc);
-        plan_kernel<RadixScatterOp>(plan, vstab, hmap, nh);
-    }
-    plan_kernel<SortFinishOp>(plan, vstab, m256, n256);
-    return G->err;
+    SortPhase P = {};
+    P.lsh = G->upload(lt);
+    P.sort = G->upload(st);
+    P.vkey = G->upload(vk);
+    P.vsort = G->upload(vs);
+    P.err = G->upload(errs);
+    unsigned np = 0, ns = 0;
+    P.pblk = G->block_map(b256, &np);
+    P.sblk = G->block_map(bsort, &ns);
+    P.n_pblk = (int)np;
+    P.n_sblk = (int)ns;
+    P.n_inst = G->size();
+    P.max_passes = max_passes;
+    P.starve = G->ctx[0]->starve_bar;
+    P.bar = static_cast<GridBar*>(G->scratch(sizeof(GridBar)));
+    P.budget = G->ctx[0]->wait_budget > 0 ? G->ctx[0]->wait_budget : MP_WAIT_BUDGET;
+    const unsigned cap = sort_phase_capacity();
+    if (G->err) return G->err;
+    if (!cap) return MP_ECUDA;
+    plan_memset(plan, P.bar, sizeof(GridBar));
+    plan_coop(plan, (const void*)k_sort_phase, std::min(std::max(np, ns), cap), SORT_PHASE_THREADS, P);
+    return MP_OK;
 }
 
 // Grouped merge: graph p reads list nbr_cur ^ p and writes the other.

@@ -8,21 +8,26 @@
 // global memory unless the caller asks for h1 and h2 (the backward pass reads
 // them).
 //
-// One persistent CTA per SM (128 threads, one warpgroup; 129 KB of shared
+// One persistent CTA per SM (256 threads, two warpgroups; 129 KB of shared
 // memory keep it alone on its SM, so its 512 TMEM columns are never waited
-// for), taking whole samples so that the max-pool stays in registers. A
-// sample's points go through in tiles of 128:
-//   * thread t computes h1 of point t and writes it, as BF16, into the tile's
-//     A operand (K-major, 128-byte swizzle);
+// for), taking whole samples so that the max-pool stays in registers. Thread
+// (row, half), row = tid mod 128 and half = tid / 128, owns tile row `row` (a
+// TMEM lane; warps w and w + 4 read the same lane quarter) and half of the
+// CUDA-core work of every layer. A sample's points go through in tiles of 128:
+//   * thread (r, h) computes channels [32h, 32h + 32) of h1 of point r and
+//     writes them, as BF16, into the tile's A operand (K-major, 128-byte
+//     swizzle);
 //   * one thread issues 4 MMAs (M = 128 points, N = 128, K = 16 each) into
 //     TMEM columns [0, 128) and commits them to an mbarrier;
-//   * thread t reads row t back (tcgen05.ld), adds b2, applies the ReLU and
-//     writes h2 as BF16 into the B operand of the next product;
+//   * thread (r, h) reads columns [64h, 64h + 64) of row r back (tcgen05.ld),
+//     adds b2, applies the ReLU and writes h2 as BF16 into the B operand of
+//     the next product;
 //   * the third layer is computed transposed, h3^T = W3^T h2^T (two MMA
 //     halves of M = 128 channels, N = 128 points, K = 128), into columns
-//     [128, 384): TMEM lane t then holds channel t (and 128 + t) for all 128
-//     points of the tile, so thread t takes the max over points in registers,
-//     in point order (the first maximum), without any cross-thread reduction.
+//     [128, 384): TMEM lane r of half h then holds channel 128h + r for all 128
+//     points of the tile, so thread (r, h) takes the max over points in
+//     registers, in point order (the first maximum), without any cross-thread
+//     reduction.
 // The BF16 weights W2^T and W3^T are packed once per parameter update into an
 // image of exactly this shared-memory layout (k_pn_pack_bf16) and copied in by
 // one bulk copy per CTA.
@@ -40,7 +45,7 @@
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;                   // two warpgroups: row = tid % 128, half = tid / 128
 constexpr int TC_ROWS = 128;                      // points per tile
 constexpr uint32_t SW_BLOCK = 16384;              // 128 rows x 64 BF16, 128-byte swizzle
 constexpr uint32_t OFF_W2 = 0;                    // W2^T: n (128) x k (64)
@@ -159,6 +164,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
     __shared__ __align__(8) uint64_t bar[3];   // weights copy, layer-2 MMAs, layer-3 MMAs
     __shared__ uint32_t tmem_s;
     const int tid = threadIdx.x, warp = tid >> 5;
+    // thread (row, half): TMEM lane / tile row `row`; half of the columns or channels of every layer
+    const int row_t = tid & (TC_ROWS - 1), half = tid >> 7;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;   // 1024-aligned operand region (shared address)
     uint8_t* const gb = smem_raw + (base - raw);    // and its generic pointer
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_s;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // this warp's TMEM lane quarter
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;   // this warp's TMEM lane quarter
     if (tid == 0) {
         mbar_expect_tx(&bar[0], W_IMAGE_BYTES);
         bulk_g2s(gb + OFF_W2, A.image, W_IMAGE_BYTES, &bar[0]);
@@ -190,15 +197,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
     uint32_t phase = 0;
     const int tiles = A.P / TC_ROWS;
     for (int b = blockIdx.x; b < A.B; b += gridDim.x) {
-        float m0 = -INFINITY, m1 = -INFINITY;   // channels tid and 128 + tid
-        int i0 = 0, i1 = 0;
+        float m = -INFINITY;   // channel 128 * half + row_t
+        int mi = 0;
         for (int t = 0; t < tiles; ++t) {
             if (__syncthreads_or(!ok)) { ok = false; break; }
-            const int64_t row = (int64_t)b * A.P + (int64_t)t * TC_ROWS + tid;
-            // layer 1 on the CUDA cores; point tid's 64 channels as eight 16-byte chunks
+            const int64_t row = (int64_t)b * A.P + (int64_t)t * TC_ROWS + row_t;
+            // layer 1 on the CUDA cores: channels [32 half, 32 half + 32) of point row_t as four 16-byte chunks
             const float x0 = A.xs[3 * row], x1 = A.xs[3 * row + 1], x2 = A.xs[3 * row + 2];
 #pragma unroll
-            for (int c8 = 0; c8 < 8; ++c8) {
+            for (int c8 = 4 * half; c8 < 4 * half + 4; ++c8) {
                 uint32_t w[4];
                 float r[8];
 #pragma unroll
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
                         fmaf(x2, sW1[129 + n0], fmaf(x1, sW1[65 + n0], fmaf(x0, sW1[1 + n0], sb1[1 + n0]))), 0.f);
                     w[j] = bf16x2_bits(v0, v1, r[2 * j], r[2 * j + 1]);
                 }
-                *reinterpret_cast<uint4*>(gb + OFF_H1 + sw128((uint32_t)tid, (uint32_t)(c8 * 8))) =
+                *reinterpret_cast<uint4*>(gb + OFF_H1 + sw128((uint32_t)row_t, (uint32_t)(c8 * 8))) =
                     make_uint4(w[0], w[1], w[2], w[3]);
                 if (A.h1_out) {
                     float4* o = reinterpret_cast<float4*>(A.h1_out + row * 64 + c8 * 8);
@@ -231,9 +238,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
             ok = mbar_wait_bounded(&bar[1], phase, A.budget);
             if (__syncthreads_or(!ok)) { ok = false; break; }
             tc_fence_after();
-            // layer 2 epilogue: row tid of the accumulator -> h2 (BF16) into the next product's B operand
+            // layer 2 epilogue: columns [64 half, 64 half + 64) of accumulator row row_t -> h2 (BF16) into
+            // the next product's B operand
 #pragma unroll 1
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 4 * half; j < 4 * half + 4; ++j) {
                 float v[16];
                 tc_ld16(tmem + lane_off + 16u * j, v);
                 uint32_t w[8];
@@ -246,8 +254,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
                 }
                 const uint32_t blk = OFF_H2 + (uint32_t)(j >> 2) * SW_BLOCK;
                 const uint32_t k0 = (uint32_t)(j & 3) * 16u;
-                *reinterpret_cast<uint4*>(gb + blk + sw128((uint32_t)tid, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(gb + blk + sw128((uint32_t)tid, k0 + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+                *reinterpret_cast<uint4*>(gb + blk + sw128((uint32_t)row_t, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(gb + blk + sw128((uint32_t)row_t, k0 + 8)) =
+                    make_uint4(w[4], w[5], w[6], w[7]);
                 if (A.h2_out) {
                     float4* o = reinterpret_cast<float4*>(A.h2_out + row * 128 + 16 * j);
 #pragma unroll
@@ -272,16 +281,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
             ok = mbar_wait_bounded(&bar[2], phase, A.budget);
             if (__syncthreads_or(!ok)) { ok = false; break; }
             tc_fence_after();
-            // layer 3 epilogue: lane tid = channel tid (and 128 + tid), columns = the tile's points in order
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const float bias = sb3[128 * h + tid];
-                float m = h ? m1 : m0;
-                int mi = h ? i1 : i0;
+            // layer 3 epilogue: lane row_t of half `half` = channel 128 half + row_t, columns = the tile's
+            // points in order
+            {
+                const float bias = sb3[128 * half + row_t];
 #pragma unroll 1
                 for (int j = 0; j < 8; ++j) {
                     float v[16];
-                    tc_ld16(tmem + lane_off + 128u + 128u * h + 16u * j, v);
+                    tc_ld16(tmem + lane_off + 128u + 128u * (uint32_t)half + 16u * j, v);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const float y = fmaxf(v[i] + bias, 0.f);
@@ -291,15 +298,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
                         }
                     }
                 }
-                if (h) { m1 = m; i1 = mi; } else { m0 = m; i0 = mi; }
             }
             phase ^= 1u;
         }
         if (!ok) break;
-        A.g[(int64_t)b * 256 + tid] = m0;
-        A.gi[(int64_t)b * 256 + tid] = i0;
-        A.g[(int64_t)b * 256 + 128 + tid] = m1;
-        A.gi[(int64_t)b * 256 + 128 + tid] = i1;
+        A.g[(int64_t)b * 256 + 128 * half + row_t] = m;
+        A.gi[(int64_t)b * 256 + 128 * half + row_t] = mi;
     }
     if (!ok && tid == 0) atomicOr(A.err, MP_ERR_WAIT);
     tc_fence_before();

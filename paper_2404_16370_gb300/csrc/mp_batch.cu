@@ -1,9 +1,11 @@
 // Batched stepping of independent filter instances (contexts). Every phase of
-// a step is one grouped launch over the blocks of all instances (k_group<Op>:
-// a block map names the instance and block each CTA runs, a table holds each
-// instance's arguments; the posterior is one cooperative persistent launch),
-// so a batch step is about thirty launches whatever the number of instances,
-// all on the batch's stream. The launches are captured
+// a step runs over the blocks of all instances at once: grouped launches
+// (k_group<Op>: a block map names the instance and block each CTA runs, a
+// table holds each instance's arguments), and for the two phases made of
+// dependent sub-steps, the LSH/sort phase and the posterior, one cooperative
+// persistent launch each with grid barriers between the sub-steps. A batch
+// step is about a dozen launches whatever the number of instances, all on the
+// batch's stream. The launches are captured
 // once into a CUDA graph per pinned staging slot and every batch step replays
 // one; the host fills the other slot (scans, odometry, LSH draw, step
 // counter) while a step runs. Before the capture, the likelihood's scan split

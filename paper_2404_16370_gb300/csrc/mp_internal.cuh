@@ -145,7 +145,7 @@ struct mp_ctx {
     uint4* scan_h2;          // 2 per valid point: the scan as 16-bit broadcast pairs (precision != FP32)
     long long wait_budget;   // cycles; 0 = MP_WAIT_BUDGET
     int starve_tx;
-    int starve_bar;          // the posterior's first grid barrier waits for one CTA more than the grid
+    int starve_bar;          // test knob: the first grid barrier of the posterior (and of a batch's sort phase) waits for one CTA more than the grid
     struct GridBar* post_bar;   // the persistent posterior's grid barrier (zeroed before each launch)
 };
 

@@ -149,6 +149,25 @@ def test_device_inputs_on_caller_stream(room):
     assert np.array_equal(outs[0], outs[1])
 
 
+def test_merge_after_keys_without_sort(room):
+    """Stages out of order: fresh LSH buckets with the segment table of no
+    sort (never written after the particles' initialisation). The merge's
+    window is empty wherever the table does not hold the particle, so the
+    lists keep only valid ids (self and the previous list)."""
+    from paper_2404_16370_gb300 import mp
+    n = 2048
+    ctx = make_ctx(mp, room, n)
+    try:
+        mp.mp_set_step_index(ctx, 3)
+        mp.mp_run_stages(ctx, mp.MP_STAGE_LSH)
+        mp.mp_run_stages(ctx, mp.MP_STAGE_MERGE)
+        ids = mp.mp_get_buffer(ctx, mp.MP_BUF_NBR_IDS)
+    finally:
+        mp.mp_destroy(ctx)
+    assert ids.min() >= -1 and ids.max() < n
+    assert np.array_equal(ids[:, 0], np.arange(n))   # self first
+
+
 def test_invalid_arguments(room):
     from paper_2404_16370_gb300 import mp
     with pytest.raises(mp.MPError):
