@@ -102,18 +102,42 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
+// 64 consecutive FP32 columns of this thread's TMEM lane: four loads in
+// flight, one wait. The wait names the destination registers, so that no use
+// of them is scheduled before it.
+__device__ __forceinline__ void tc_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_wait_ld16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, float v[64]) {
+    uint32_t r0[16], r1[16], r2[16], r3[16];
+    tc_ld16_issue(taddr, r0);
+    tc_ld16_issue(taddr + 16u, r1);
+    tc_ld16_issue(taddr + 32u, r2);
+    tc_ld16_issue(taddr + 48u, r3);
+    tc_wait_ld16(r0);   // waits for all four; the next three only tie their registers to a wait
+    tc_wait_ld16(r1);
+    tc_wait_ld16(r2);
+    tc_wait_ld16(r3);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) {
+        v[i] = __uint_as_float(r0[i]);
+        v[16 + i] = __uint_as_float(r1[i]);
+        v[32 + i] = __uint_as_float(r2[i]);
+        v[48 + i] = __uint_as_float(r3[i]);
+    }
 }
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi, float& rlo, float& rhi) {
@@ -199,11 +223,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
     for (int b = blockIdx.x; b < A.B; b += gridDim.x) {
         float m = -INFINITY;   // channel 128 * half + row_t
         int mi = 0;
+        // the tile's points; the next tile's are loaded while the layer-3 MMAs run
+        const int64_t row0 = (int64_t)b * A.P + row_t;
+        float x0 = A.xs[3 * row0], x1 = A.xs[3 * row0 + 1], x2 = A.xs[3 * row0 + 2];
         for (int t = 0; t < tiles; ++t) {
             if (__syncthreads_or(!ok)) { ok = false; break; }
             const int64_t row = (int64_t)b * A.P + (int64_t)t * TC_ROWS + row_t;
             // layer 1 on the CUDA cores: channels [32 half, 32 half + 32) of point row_t as four 16-byte chunks
-            const float x0 = A.xs[3 * row], x1 = A.xs[3 * row + 1], x2 = A.xs[3 * row + 2];
 #pragma unroll
             for (int c8 = 4 * half; c8 < 4 * half + 4; ++c8) {
                 uint32_t w[4];
@@ -240,10 +266,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
             tc_fence_after();
             // layer 2 epilogue: columns [64 half, 64 half + 64) of accumulator row row_t -> h2 (BF16) into
             // the next product's B operand
-#pragma unroll 1
-            for (int j = 4 * half; j < 4 * half + 4; ++j) {
-                float v[16];
-                tc_ld16(tmem + lane_off + 16u * j, v);
+            float v2[64];
+            tc_ld64(tmem + lane_off + 64u * (uint32_t)half, v2);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = 4 * half + jj;
+                const float* v = v2 + 16 * jj;
                 uint32_t w[8];
                 float r[16];
 #pragma unroll
@@ -278,6 +306,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
                     }
                 tc_commit(&bar[2]);
             }
+            if (t + 1 < tiles) {
+                const int64_t nrow = row + TC_ROWS;
+                x0 = A.xs[3 * nrow];
+                x1 = A.xs[3 * nrow + 1];
+                x2 = A.xs[3 * nrow + 2];
+            }
             ok = mbar_wait_bounded(&bar[2], phase, A.budget);
             if (__syncthreads_or(!ok)) { ok = false; break; }
             tc_fence_after();
@@ -286,15 +320,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
             {
                 const float bias = sb3[128 * half + row_t];
 #pragma unroll 1
-                for (int j = 0; j < 8; ++j) {
-                    float v[16];
-                    tc_ld16(tmem + lane_off + 128u + 128u * (uint32_t)half + 16u * j, v);
+                for (int q = 0; q < 2; ++q) {
+                    float v[64];
+                    tc_ld64(tmem + lane_off + 128u + 128u * (uint32_t)half + 64u * (uint32_t)q, v);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
+                    for (int i = 0; i < 64; ++i) {
                         const float y = fmaxf(v[i] + bias, 0.f);
                         if (y > m) {
                             m = y;
-                            mi = t * TC_ROWS + 16 * j + i;
+                            mi = t * TC_ROWS + 64 * q + i;
                         }
                     }
                 }
