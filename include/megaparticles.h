@@ -213,7 +213,8 @@ int mp_set_step_index(mp_ctx* ctx, uint64_t step);
                                   of their position's cell (cubes of 2^s NNF voxels, s the smallest
                                   shift leaving at most 32 cubes along every NNF axis, positions
                                   clamped to the grid), LSH order (MP_BUF_SORTED_IDS) within a cell.
-                                  Written by MP_STAGE_SORT; no result depends on it.  r */
+                                  Written by MP_STAGE_SORT; no result depends on it (a
+                                  permutation set here lasts until the next sort).  rw */
 
 /* Element count of a buffer (0 if not allocated). */
 int mp_buffer_size(mp_ctx* ctx, int which, int64_t* count);

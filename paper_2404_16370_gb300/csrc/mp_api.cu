@@ -838,16 +838,19 @@ int mp_set_buffer(mp_ctx* c, int which, const void* src, int64_t count) {
             return MP_OK;
         }
         case MP_BUF_LOG_PRIOR: return put(c->logprior, sizeof(double) * n);
-        case MP_BUF_SORTED_IDS: case MP_BUF_NBR_IDS: {
+        case MP_BUF_SORTED_IDS: case MP_BUF_VISIT_ORDER: case MP_BUF_NBR_IDS: {
             // kernels index particles by these entries: checked on the host first
-            const int64_t m = which == MP_BUF_SORTED_IDS ? n : n * c->p.K;
+            const bool perm = which != MP_BUF_NBR_IDS;
+            const int64_t m = perm ? n : n * c->p.K;
             std::vector<int32_t> h((size_t)m);
             MP_CUDA(c, cudaStreamSynchronize(c->stream));
             MP_CUDA(c, cudaMemcpy(h.data(), src, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault));
-            if (which == MP_BUF_SORTED_IDS) {
+            if (perm) {
                 std::vector<uint8_t> seen((size_t)n, 0);
                 for (int32_t v : h) {
-                    if (v < 0 || v >= n || seen[(size_t)v]) return mp_fail(c, MP_EINVAL, "sorted ids must be a permutation of [0, n)");
+                    if (v < 0 || v >= n || seen[(size_t)v])
+                        return mp_fail(c, MP_EINVAL, "%s must be a permutation of [0, n)",
+                                       which == MP_BUF_SORTED_IDS ? "sorted ids" : "the visiting order");
                     seen[(size_t)v] = 1;
                 }
             } else {
@@ -855,8 +858,9 @@ int mp_set_buffer(mp_ctx* c, int which, const void* src, int64_t count) {
                     if (v < -1 || v >= n) return mp_fail(c, MP_EINVAL, "neighbour ids must lie in [-1, n)");
             }
             src = h.data();   // put() copies from src on the context stream
-            return put(which == MP_BUF_SORTED_IDS ? (void*)c->sorted_ids : (void*)c->nbr_ids[c->nbr_cur],
-                       sizeof(int32_t) * (size_t)m);
+            void* dst = which == MP_BUF_SORTED_IDS ? (void*)c->sorted_ids
+                        : which == MP_BUF_VISIT_ORDER ? (void*)c->visit : (void*)c->nbr_ids[c->nbr_cur];
+            return put(dst, sizeof(int32_t) * (size_t)m);
         }
         case MP_BUF_NBR_K: return put(c->nbr_k, sizeof(float) * n * c->p.K);
         case MP_BUF_NBR_D: return put(c->nbr_d, sizeof(float) * n * c->p.K * 6);

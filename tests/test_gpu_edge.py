@@ -192,7 +192,9 @@ def test_invalid_arguments(room):
         with pytest.raises(mp.MPError):
             mp.mp_set_buffer(ctx, mp.MP_BUF_KEYS, np.zeros(64, np.uint32))   # read-only buffer
         with pytest.raises(mp.MPError):
-            mp.mp_set_buffer(ctx, mp.MP_BUF_VISIT_ORDER, np.arange(64, dtype=np.int32))
+            mp.mp_set_buffer(ctx, mp.MP_BUF_VISIT_ORDER, np.zeros(64, np.int32))   # not a permutation
+        mp.mp_set_buffer(ctx, mp.MP_BUF_VISIT_ORDER, np.arange(64, dtype=np.int32)[::-1].copy())
+        assert np.array_equal(mp.mp_get_buffer(ctx, mp.MP_BUF_VISIT_ORDER), np.arange(64)[::-1])
         # index buffers the kernels gather through are checked before upload
         dup = np.arange(64, dtype=np.int32)
         dup[5] = 4
