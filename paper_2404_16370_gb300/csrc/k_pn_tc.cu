@@ -140,6 +140,13 @@ __device__ __forceinline__ void tc_ld64(uint32_t taddr, float v[64]) {
     }
 }
 
+// eight floats from a 16-byte-aligned shared-memory address (two 16-byte loads)
+__device__ __forceinline__ void ld8_shared(const float* p, float v[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi, float& rlo, float& rhi) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);   // .x = lo (low half), .y = hi
     const float2 f = __bfloat1622float2(h);
@@ -184,7 +191,7 @@ struct MlpArgs {
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ float sW1[3 * 64], sb1[64], sb2[128], sb3[256];
+    __shared__ __align__(16) float sW1[3 * 64], sb1[64], sb2[128], sb3[256];   // read 4 at a time
     __shared__ __align__(8) uint64_t bar[3];   // weights copy, layer-2 MMAs, layer-3 MMAs
     __shared__ uint32_t tmem_s;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -234,12 +241,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
             for (int c8 = 4 * half; c8 < 4 * half + 4; ++c8) {
                 uint32_t w[4];
                 float r[8];
+                float w0[8], w1[8], w2[8], b0[8];
+                ld8_shared(sW1 + c8 * 8, w0);
+                ld8_shared(sW1 + 64 + c8 * 8, w1);
+                ld8_shared(sW1 + 128 + c8 * 8, w2);
+                ld8_shared(sb1 + c8 * 8, b0);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int n0 = c8 * 8 + 2 * j;
-                    const float v0 = fmaxf(fmaf(x2, sW1[128 + n0], fmaf(x1, sW1[64 + n0], fmaf(x0, sW1[n0], sb1[n0]))), 0.f);
-                    const float v1 = fmaxf(
-                        fmaf(x2, sW1[129 + n0], fmaf(x1, sW1[65 + n0], fmaf(x0, sW1[1 + n0], sb1[1 + n0]))), 0.f);
+                    const int e = 2 * j;
+                    const float v0 = fmaxf(fmaf(x2, w2[e], fmaf(x1, w1[e], fmaf(x0, w0[e], b0[e]))), 0.f);
+                    const float v1 = fmaxf(fmaf(x2, w2[e + 1], fmaf(x1, w1[e + 1], fmaf(x0, w0[e + 1], b0[e + 1]))), 0.f);
                     w[j] = bf16x2_bits(v0, v1, r[2 * j], r[2 * j + 1]);
                 }
                 *reinterpret_cast<uint4*>(gb + OFF_H1 + sw128((uint32_t)row_t, (uint32_t)(c8 * 8))) =
@@ -273,13 +284,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
                 const int j = 4 * half + jj;
                 const float* v = v2 + 16 * jj;
                 uint32_t w[8];
-                float r[16];
+                float r[16], bb[16];
+                ld8_shared(sb2 + 16 * j, bb);
+                ld8_shared(sb2 + 16 * j + 8, bb + 8);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int n0 = 16 * j + 2 * i;
-                    w[i] = bf16x2_bits(fmaxf(v[2 * i] + sb2[n0], 0.f), fmaxf(v[2 * i + 1] + sb2[n0 + 1], 0.f), r[2 * i],
+                for (int i = 0; i < 8; ++i)
+                    w[i] = bf16x2_bits(fmaxf(v[2 * i] + bb[2 * i], 0.f), fmaxf(v[2 * i + 1] + bb[2 * i + 1], 0.f), r[2 * i],
                                        r[2 * i + 1]);
-                }
                 const uint32_t blk = OFF_H2 + (uint32_t)(j >> 2) * SW_BLOCK;
                 const uint32_t k0 = (uint32_t)(j & 3) * 16u;
                 *reinterpret_cast<uint4*>(gb + blk + sw128((uint32_t)row_t, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -323,14 +334,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pn_mlp_tc(const MlpArgs A) {
                 for (int q = 0; q < 2; ++q) {
                     float v[64];
                     tc_ld64(tmem + lane_off + 128u + 128u * (uint32_t)half + 64u * (uint32_t)q, v);
+                    // the first maximum of each run of 16 points (four independent chains), then of
+                    // the runs in point order: a later value replaces an earlier one only if greater
+                    float cm[4];
+                    int ci[4];
 #pragma unroll
-                    for (int i = 0; i < 64; ++i) {
-                        const float y = fmaxf(v[i] + bias, 0.f);
-                        if (y > m) {
-                            m = y;
-                            mi = t * TC_ROWS + 64 * q + i;
+                    for (int c = 0; c < 4; ++c) {
+                        cm[c] = -INFINITY;
+                        ci[c] = 0;
+#pragma unroll
+                        for (int i = 16 * c; i < 16 * c + 16; ++i) {
+                            const float y = fmaxf(v[i] + bias, 0.f);
+                            if (y > cm[c]) {
+                                cm[c] = y;
+                                ci[c] = i;
+                            }
                         }
                     }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (cm[c] > m) {
+                            m = cm[c];
+                            mi = t * TC_ROWS + 64 * q + ci[c];
+                        }
                 }
             }
             phase ^= 1u;
