@@ -124,6 +124,30 @@ def test_likelihood_near_ground_truth(env, oracle):
     check_gn(gn, ref)
 
 
+def test_likelihood_sums_do_not_depend_on_the_visiting_order(env):
+    """Each particle's sums come from one thread in scan order, so any
+    visiting order gives the same bits per particle: identity, reversed,
+    a random permutation and the sort stage's position order; the solve reads
+    the sums through the same order, so psi agrees too."""
+    mp, ctx = env["mp"], env["ctx"]
+    reset(env)
+    mp.mp_set_scan(ctx, env["w"].scans[0])
+    mp.mp_set_step_index(ctx, 2)
+    mp.mp_run_stages(ctx, mp.MP_STAGE_SCAN | mp.MP_STAGE_LSH | mp.MP_STAGE_SORT)
+    orders = {"position": mp.mp_get_buffer(ctx, mp.MP_BUF_VISIT_ORDER).copy(),
+              "identity": np.arange(N, dtype=np.int32), "reversed": np.arange(N, dtype=np.int32)[::-1].copy(),
+              "random": np.random.default_rng(5).permutation(N).astype(np.int32)}
+    res = {}
+    for name, order in orders.items():
+        mp.mp_set_buffer(ctx, mp.MP_BUF_VISIT_ORDER, order)
+        mp.mp_run_stages(ctx, mp.MP_STAGE_LIKELIHOOD | mp.MP_STAGE_SOLVE)
+        res[name] = (mp.mp_get_buffer(ctx, mp.MP_BUF_GN), mp.mp_get_buffer(ctx, mp.MP_BUF_PSI))
+    ref_gn, ref_psi = res["position"]
+    for name, (gn, psi) in res.items():
+        assert np.array_equal(gn.view(np.uint32), ref_gn.view(np.uint32)), name
+        assert np.array_equal(psi.view(np.uint32), ref_psi.view(np.uint32)), name
+
+
 def test_gn_step_solves_the_reference_system(env, oracle):
     mp, ctx = env["mp"], env["ctx"]
     gn, ref = likelihood_case(env, oracle, env["w"].particles, env["w"].scans[0])
