@@ -324,7 +324,9 @@ __device__ __forceinline__ const PostArgs& phase_item(const PostPhase& P, int w,
     return P.tab[g.inst];
 }
 
-__global__ void __launch_bounds__(PB, 8) k_post_phase(const __grid_constant__ PostPhase P) {
+// 4 CTAs of 256 threads per SM: 64 registers, no spill (fewer registers and
+// more CTAs spill the sub-steps' FP64 values and measured slower)
+__global__ void __launch_bounds__(PB, 4) k_post_phase(const __grid_constant__ PostPhase P) {
     // the test knob: the first barrier waits for one CTA more than the grid
     unsigned expect = gridDim.x + (P.starve ? 1u : 0u);
     auto sync = [&]() {
