@@ -1,4 +1,4 @@
-"""Multi-step parity, judged on statistics: trajectories of the filter
+"""Multi-step parity, compared on statistics: trajectories of the filter
 diverge chaotically between the GPU (FP32) and the FP64 oracle once an LSH
 floor or a neighbour tie falls the other way, so over many steps the two are
 compared by what the filter is for -- whether and when its representative
