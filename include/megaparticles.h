@@ -220,7 +220,10 @@ int mp_set_step_index(mp_ctx* ctx, uint64_t step);
 int mp_buffer_size(mp_ctx* ctx, int which, int64_t* count);
 /* Copy a buffer out (synchronises the stream). count must equal its size. */
 int mp_get_buffer(mp_ctx* ctx, int which, void* dst, int64_t count);
-/* Overwrite a writable buffer (synchronises the stream). */
+/* Overwrite a writable buffer (synchronises the stream). Index buffers the
+ * kernels gather through are checked on the host first: MP_BUF_SORTED_IDS and
+ * MP_BUF_VISIT_ORDER must be permutations of [0, n), MP_BUF_NBR_IDS entries
+ * must lie in [-1, n); otherwise MP_EINVAL and nothing is written. */
 int mp_set_buffer(mp_ctx* ctx, int which, const void* src, int64_t count);
 
 /* NNF values of m voxels (m x 3 int32 integer coordinates; outside the grid:
